@@ -1,0 +1,391 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test names the passage it follows.  A plausible mistake in the oracle (a
+sign of the y or z coupling, a wrong neighbour, a mass on the wrong
+component, the time-average on the wrong term, a link phase of the wrong sign
+or place) fails at least one of them:
+
+* conservation of the functional E (Lemma, Sect. 2 Eq. EPM; Lemma, Sect. 3)
+  holds only for the Hermitian sign pattern of the scheme;
+* a lattice plane wave advances by exactly the phase of Eq. pwdsip;
+* the full spectrum of the one-step map equals the closed form (single cone);
+* stability below/above r_max (Sect. 2.2, Sect. 3);
+* the light cone of the nearest-neighbour stencil (Eq. 3+3Ddis);
+* the (3+1)D -> (2+1)D reduction (Sect. 3, opening paragraph);
+* gauge covariance of the Peierls substitution (Sect. 4).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1309_3452_gb300 import workloads as W
+from tests import closed_forms as CF
+
+
+def prob2(N=(12, 10), r=0.9, m=0.3, dx=(1.0, 1.0)):
+    dt = r * W.stability_limit(2) * min(dx)
+    return W.Problem(2, (N[0], N[1], 1), (dx[0], dx[1], 1.0), dt, m)
+
+
+def prob3(N=(6, 5, 7), r=0.9, m=0.7, dx=(1.0, 1.0, 1.0)):
+    dt = r * W.stability_limit(3) * min(dx)
+    return W.Problem(3, tuple(N), tuple(dx), dt, m)
+
+
+def rel_drift(prob, psi0, nsteps, t0=0.0):
+    e0 = O.observables(prob, psi0, t0)
+    psi = O.step(prob, psi0, nsteps, t0)
+    e1 = O.observables(prob, psi, t0 + nsteps * prob.dt)
+    return (e1["E"] - e0["E"]) / e0["E"], e0, e1, psi
+
+
+# ---------------------------------------------------------------- T1
+@pytest.mark.parametrize("dims", [2, 3])
+def test_conservation_random_static_potential(dims):
+    """Lemma of Sect. 2 (Eq. EPM) and of Sect. 3: E is conserved exactly for
+    arbitrary real V(x); the naive norm is not (Sect. 3)."""
+    prob = prob2() if dims == 2 else prob3()
+    prob = prob.with_fields(V_static=W.random_potential(prob, 11, 0.8))
+    psi0 = W.random_state(prob, 5)
+    d, e0, e1, _ = rel_drift(prob, psi0, 400 if dims == 2 else 200)
+    assert abs(d) < 2e-14
+    # the naive norm oscillates (not conserved), as the paper states
+    assert abs(e1["naive"] - e0["naive"]) > 1e-3
+    # upper and lower forms agree for static fields (summation by parts)
+    assert abs(e1["E"] - e1["E_upper"]) < 1e-13
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_conservation_time_dependent_potential_and_anisotropic_grid(dims):
+    """E is conserved for space- and time-dependent V (Prop. 3 / Prop. 5 hold
+    'for arbitrary space- and time-dependent mass and potential'), with
+    r_x != r_y != r_z."""
+    if dims == 2:
+        dx = (1.0, 1.3)
+        prob = W.Problem(2, (10, 9, 1), (1.0, 1.3, 1.0), 0.5, 0.4)
+    else:
+        dx = (1.0, 1.2, 0.9)
+        prob = W.Problem(3, (5, 6, 4), dx, 0.45, 0.4)
+    r2 = sum((prob.dt / prob.dx[a]) ** 2 for a in range(dims))
+    assert r2 < 1.0
+    prob = prob.with_fields(V_static=W.random_potential(prob, 3, 1.0), Vmod_amp=0.7,
+                            Vmod_omega=1.3, V0=0.2, step_axis=0, step_x0=2.6, step_V=0.9,
+                            sc_Z=0.5, sc_a=1.0, sc_center=(2.0, 3.0, 1.5))
+    psi0 = W.random_state(prob, 9)
+    d, _, _, _ = rel_drift(prob, psi0, 300, t0=0.37)
+    assert abs(d) < 2e-14
+
+
+@pytest.mark.parametrize("dims,kaxis", [(2, 1), (3, 2), (2, 0), (3, 0)])
+def test_conservation_static_vector_potential(dims, kaxis):
+    """Sect. 4: the Peierls-substituted scheme keeps the norm: E (with link
+    factors) is conserved for a static vector potential, constant or a
+    static (omega = 0) plane wave that is periodic on the box.  With k along
+    the polarisation the link factor varies along its own link, so only a
+    phase taken at the same point from both ends (the link midpoint) keeps
+    the hopping Hermitian."""
+    prob = prob2(N=(8, 8)) if dims == 2 else prob3(N=(4, 6, 8))
+    L = [prob.N[a] * prob.dx[a] for a in range(dims)]
+    k = [0.0, 0.0, 0.0]
+    k[kaxis] = 2 * math.pi / L[kaxis]
+    prob = prob.with_fields(A_const=(0.31, -0.2, 0.15), Apw_amp=0.6, Apw_k=tuple(k),
+                            Apw_omega=0.0, Apw_phase=0.4, Apw_pol=0,
+                            V_static=W.random_potential(prob, 2, 0.5))
+    psi0 = W.random_state(prob, 4)
+    d, e0, e1, _ = rel_drift(prob, psi0, 300)
+    assert abs(d) < 2e-14
+    assert abs(e1["E"] - e1["E_upper"]) < 1e-13
+
+
+def _paper_2d_cross(prob, psi, sign):
+    """r Re sum_v conj(v) (delta_x u + sign*i delta_y u), restated on the
+    canonical planes (u0,u1,v0,v1) of Sect. 3: v0 at (j+1/2, j) has x
+    neighbours u0[j+1], u0[j] and y neighbours u1[j], u1[j-1]; v1 at
+    (j, j+1/2) has x neighbours u1[j], u1[j-1] and y neighbours u0[j+1], u0[j]."""
+    u0, u1, v0, v1 = (psi[i, 0] for i in range(4))
+    r = prob.dt / prob.dx[0]
+    sx = lambda a: np.roll(a, -1, axis=1)  # a[j+1] along x
+    sy = lambda a: np.roll(a, -1, axis=0)
+    mx = lambda a: np.roll(a, 1, axis=1)   # a[j-1] along x
+    my = lambda a: np.roll(a, 1, axis=0)
+    d0 = (sx(u0) - u0) + sign * 1j * (u1 - my(u1))
+    d1 = (u1 - mx(u1)) + sign * 1j * (sy(u0) - u0)
+    return r * np.real(np.sum(np.conj(v0) * d0) + np.sum(np.conj(v1) * d1))
+
+
+def test_2d_functional_sign_reading():
+    """Sect. 3 Lemma prints the cross term with delta_- u; the scheme as
+    printed (Eqs. scheme2ndline, scheme4thline) updates v with
+    delta_x u + i delta_y u = delta_+ u, and only the delta_+ form is
+    conserved.  The oracle's E equals the delta_+ form."""
+    prob = W.Problem(2, (10, 10, 1), (1.0, 1.0, 1.0), 0.9 * W.stability_limit(2), 0.2)
+    psi0 = W.random_state(prob, 21)
+    psi1 = O.step(prob, psi0, 150)
+    naive = lambda s: float(np.sum(np.abs(s) ** 2))
+    Ep = [naive(s) + _paper_2d_cross(prob, s, +1) for s in (psi0, psi1)]
+    Em = [naive(s) + _paper_2d_cross(prob, s, -1) for s in (psi0, psi1)]
+    assert abs(Ep[1] - Ep[0]) / Ep[0] < 1e-13
+    assert abs(Em[1] - Em[0]) / Em[0] > 1e-3
+    assert abs(O.observables(prob, psi1, 150 * prob.dt)["E"] - Ep[1]) < 1e-13
+
+
+# ---------------------------------------------------------------- T2
+@pytest.mark.parametrize("dims,m,modes", [(2, 0.0, (5, 3)), (2, 0.5, (5, 3)), (2, 0.5, (-2, 7)),
+                                          (3, 0.0, (2, -1, 3)), (3, 1.0, (2, -1, 3)),
+                                          (3, 1.0, (0, 0, 0))])
+def test_plane_wave_phase(dims, m, modes):
+    """Eq. pwdsip with the eigenspinor of Sect. 2.1: a lattice plane wave is
+    an exact eigenmode and advances by exp(-i w n dt)."""
+    if dims == 2:
+        prob = W.Problem(2, (16, 12, 1), (1.0, 1.0, 1.0), 0.9 * W.stability_limit(2), m)
+        n = 200
+    else:
+        prob = W.Problem(3, (8, 6, 10), (1.0, 1.0, 1.0), 0.9 * W.stability_limit(3), m)
+        n = 100
+    psi0, w = CF.plane_wave_state(prob, modes)
+    psi = O.step(prob, psi0, n)
+    ref = psi0 * np.exp(-1j * w * n * prob.dt)
+    err = np.linalg.norm(psi - ref) / np.linalg.norm(ref)
+    assert err < 1e-12
+
+
+def test_plane_wave_negative_energy_3d():
+    prob = W.Problem(3, (6, 6, 6), (1.0, 1.0, 1.0), 0.9 * W.stability_limit(3), 0.6)
+    psi0, w = CF.plane_wave_state(prob, (1, 2, -1), positive=False)
+    assert w < 0
+    psi = O.step(prob, psi0, 60)
+    err = np.linalg.norm(psi - psi0 * np.exp(-1j * w * 60 * prob.dt)) / np.linalg.norm(psi0)
+    assert err < 1e-12
+
+
+# ---------------------------------------------------------------- T3 / T4
+def one_step_matrix(prob):
+    n = int(np.prod(prob.shape))
+    G = np.zeros((n, n), complex)
+    for i in range(n):
+        e = np.zeros(n, complex)
+        e[i] = 1.0
+        G[:, i] = O.step(prob, e.reshape(prob.shape), 1).reshape(-1)
+    return G
+
+
+@pytest.mark.parametrize("dims,N,m", [(2, (4, 4), 0.3), (2, (4, 4), 0.0), (3, (2, 2, 2), 0.5)])
+def test_exact_spectrum(dims, N, m):
+    """Single cone (Sect. 2.1, Fig. 2; Sect. 3): the eigen-phases of the
+    one-step map are exactly -+ w(k) dt over the reduced zone, each with the
+    multiplicity of the staggered copy, and all have modulus one."""
+    prob = W.Problem(dims, tuple(N) + ((1,) if dims == 2 else ()), (1.0, 1.0, 1.0),
+                     0.9 * W.stability_limit(dims), m)
+    lam = np.linalg.eigvals(one_step_matrix(prob))
+    assert np.max(np.abs(np.abs(lam) - 1.0)) < 1e-12
+    got = np.sort(np.angle(lam))
+    want = np.sort(-CF.reduced_spectrum(prob))  # exp(-i w dt)
+    assert got.shape == want.shape
+    assert np.max(np.abs(got - want)) < 1e-10
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_stability_bound(dims):
+    """Stability condition r_x^2 + r_y^2 (+ r_z^2) <= 1 (Sect. 2.2, Sect. 3):
+    |lambda| = 1 at 0.9 r_max, also with a random real potential (Prop. 3 /
+    Prop. 5); |lambda| > 1 at 1.1 r_max."""
+    N = (4, 4, 1) if dims == 2 else (2, 2, 2)
+    for r, stable in ((0.9, True), (1.1, False)):
+        prob = W.Problem(dims, N, (1.0, 1.0, 1.0), r * W.stability_limit(dims), 0.3)
+        for V in (None, W.random_potential(prob, 1, 0.7)):
+            lam = np.linalg.eigvals(one_step_matrix(prob.with_fields(V_static=V)))
+            if stable:
+                assert np.max(np.abs(lam)) - 1.0 < 1e-12
+            else:
+                assert np.max(np.abs(lam)) > 1.05
+
+
+def test_functional_positive_definite_3d():
+    """Appendix A / Prop. 3: at r <= 1/sqrt(3) the functional E is a norm;
+    above the bound it is indefinite (its Hermitian form gets a negative
+    eigenvalue)."""
+    def min_eig(r):
+        prob = W.Problem(3, (2, 2, 2), (1.0, 1.0, 1.0), r * W.stability_limit(3), 0.0)
+        n = int(np.prod(prob.shape))
+        Ed = [O.observables(prob, np.eye(n)[i].reshape(prob.shape))["E"] for i in range(n)]
+        M = np.diag(np.array(Ed, complex))
+        for i in range(n):
+            for j in range(i + 1, n):
+                ei, ej = np.eye(n)[i], np.eye(n)[j]
+                a = O.observables(prob, (ei + ej).reshape(prob.shape))["E"] - Ed[i] - Ed[j]
+                b = O.observables(prob, (ei + 1j * ej).reshape(prob.shape))["E"] - Ed[i] - Ed[j]
+                M[i, j] = 0.5 * (a - 1j * b)
+                M[j, i] = np.conj(M[i, j])
+        return np.min(np.linalg.eigvalsh(M))
+    assert min_eig(0.99) > 0.0
+    assert min_eig(1.05) < 0.0
+
+
+# ---------------------------------------------------------------- T7
+@pytest.mark.parametrize("dims", [2, 3])
+def test_light_cone(dims):
+    """Nearest-neighbour stencil (Eq. 3+3Ddis): after n steps a single
+    nonzero value spreads at most 2n half-lattice steps per axis (one per
+    half-step); everything outside is exactly zero."""
+    N = (15, 13, 11)
+    prob = W.Problem(dims, N if dims == 3 else (15, 13, 1), (1.0, 1.0, 1.0),
+                     0.9 * W.stability_limit(dims), 0.5)
+    src_cell = (7, 6, 5)
+    n = 2
+    _, offs, _, _ = W.plane_tables(dims)
+    for plane in range(prob.n_planes):
+        psi = O.step(prob, W.delta_state(prob, plane, src_cell), n)
+        so = [2 * src_cell[a] + offs[plane][a] for a in range(dims)]
+        for pl in range(prob.n_planes):
+            xyz = W.site_positions(prob, pl)
+            dist = sum(np.abs(2 * xyz[a] - so[a]) for a in range(dims))  # half-lattice L1
+            outside = dist > 2 * n
+            assert np.all(psi[pl][outside] == 0.0)
+        assert np.count_nonzero(psi) > 1
+
+
+# ---------------------------------------------------------------- T6
+def test_3d_reduces_to_2d_bitwise():
+    """Sect. 3: with z-independent data and B = C = 0 the (3+1)D scheme
+    carries A, D exactly like u, v of the (2+1)D scheme (the z differences
+    vanish), for any V(x, y)."""
+    N = (9, 7)
+    Nz = 4
+    p2 = W.Problem(2, (N[0], N[1], 1), (1.0, 1.0, 1.0), 0.5, 0.35)
+    p3 = W.Problem(3, (N[0], N[1], Nz), (1.0, 1.0, 1.0), 0.5, 0.35)
+    V2 = W.random_potential(p2, 7, 0.6)
+    V3 = np.zeros(p3.shape)
+    psi2 = W.random_state(p2, 8)
+    psi3 = np.zeros(p3.shape, complex)
+    for z in range(Nz):  # A0,A1 <- u0,u1 ; D0,D1 <- v0,v1
+        psi3[0, z], psi3[1, z], psi3[6, z], psi3[7, z] = psi2[0, 0], psi2[1, 0], psi2[2, 0], psi2[3, 0]
+        V3[0, z], V3[1, z], V3[6, z], V3[7, z] = V2[0, 0], V2[1, 0], V2[2, 0], V2[3, 0]
+    out2 = O.step(p2.with_fields(V_static=V2), psi2, 37)
+    out3 = O.step(p3.with_fields(V_static=V3), psi3, 37)
+    for z in range(Nz):
+        assert np.array_equal(out3[0, z], out2[0, 0]) and np.array_equal(out3[1, z], out2[1, 0])
+        assert np.array_equal(out3[6, z], out2[2, 0]) and np.array_equal(out3[7, z], out2[3, 0])
+        assert not np.any(out3[2:6, z])
+
+
+# ---------------------------------------------------------------- T9
+@pytest.mark.parametrize("dims", [2, 3])
+def test_gauge_covariance_constant_vector_potential(dims):
+    """Sect. 4 (Peierls substitution): a constant A with q A_a L_a = 2 pi n_a
+    is a pure gauge; psi_A(t) = exp(i q A.x) psi_0(t) at every site."""
+    N = (8, 6, 5)
+    prob = W.Problem(dims, N if dims == 3 else (8, 6, 1), (1.0, 1.0, 1.0),
+                     0.9 * W.stability_limit(dims), 0.4)
+    prob = prob.with_fields(V_static=W.random_potential(prob, 5, 0.5))
+    q = 0.7
+    A = [2 * math.pi * n / (q * prob.N[a] * prob.dx[a]) for a, n in zip(range(dims), (1, -2, 3))]
+    A += [0.0] * (3 - dims)
+    psi0 = W.random_state(prob, 3)
+    gauge = np.zeros(prob.shape, complex)
+    for pl in range(prob.n_planes):
+        xyz = W.site_positions(prob, pl)
+        gauge[pl] = np.exp(1j * q * sum(A[a] * xyz[a] for a in range(dims)))
+    out0 = O.step(prob, psi0, 40)
+    outA = O.step(prob.with_fields(q=q, A_const=tuple(A)), gauge * psi0, 40)
+    assert np.max(np.abs(outA - gauge * out0)) < 1e-12
+
+
+def test_uniform_time_dependent_vector_potential_2d():
+    """Sect. 4 with a spatially uniform A(t): a lattice plane wave stays a
+    plane wave whose momentum is shifted, P_a = (2/dx) sin((k_a - q A_a(t))
+    dx/2) (the link factor multiplies exp(i k h) by exp(-i q A h)).  The
+    oracle must agree with this per-mode 2x2 recursion, each half-step at the
+    time sheet of its neighbours."""
+    N = (8, 8)
+    dt = 0.9 * W.stability_limit(2)
+    amp, om, q, m = 0.4, 0.3, 1.0, 0.25
+    prob = W.Problem(2, (N[0], N[1], 1), (1.0, 1.0, 1.0), dt, m,
+                     W.Fields(q=q, Apw_amp=amp, Apw_k=(0.0, 0.0, 0.0), Apw_omega=om, Apw_phase=0.2,
+                              Apw_pol=1))
+    k = (2 * math.pi * 1 / N[0], 2 * math.pi * 2 / N[1])
+    u, v = 0.6 + 0.1j, -0.3 + 0.7j
+    # state: u at t=-dt/2, v at t=0, amplitudes times exp(i k.x)
+    psi0 = np.zeros(prob.shape, complex)
+    for pl in range(4):
+        xyz = W.site_positions(prob, pl)
+        psi0[pl] = (u if pl < 2 else v) * np.exp(1j * (k[0] * xyz[0] + k[1] * xyz[1]))
+    n = 30
+    t = 0.0
+    for _ in range(n):
+        # upper half-step: A at time t
+        Ay = amp * math.cos(-om * t + 0.2)
+        Px, Py = 2 * math.sin(k[0] / 2), 2 * math.sin((k[1] - q * Ay) / 2)
+        th = dt * m / 2
+        S = dt * 1j * (Px - 1j * Py) * v   # r(delta_x - i delta_y) v with delta -> 2i sin
+        u = ((1 - 1j * th) * u - S) / (1 + 1j * th)
+        Ay = amp * math.cos(-om * (t + dt / 2) + 0.2)
+        Py = 2 * math.sin((k[1] - q * Ay) / 2)
+        th = -dt * m / 2
+        S = dt * 1j * (Px + 1j * Py) * u
+        v = ((1 - 1j * th) * v - S) / (1 + 1j * th)
+        t += dt
+    out = O.step(prob, psi0, n)
+    ref = np.zeros(prob.shape, complex)
+    for pl in range(4):
+        xyz = W.site_positions(prob, pl)
+        ref[pl] = (u if pl < 2 else v) * np.exp(1j * (k[0] * xyz[0] + k[1] * xyz[1]))
+    assert np.max(np.abs(out - ref)) < 1e-12
+
+
+# ---------------------------------------------------------------- T10
+def test_proposition_2_bound():
+    """Prop. 2: for r_x + r_y + r_z < 1 the naive norm stays below
+    E0 / (1 - r_x - r_y - r_z) for all time, for arbitrary V(x,t)."""
+    prob = W.Problem(3, (5, 4, 6), (1.0, 1.0, 1.0), 0.3, 0.2)
+    prob = prob.with_fields(V_static=W.random_potential(prob, 4, 2.0), Vmod_amp=0.5, Vmod_omega=0.9)
+    psi = W.random_state(prob, 6)
+    E0 = O.observables(prob, psi)["E"]
+    bound = E0 / (1 - 3 * 0.3)
+    t = 0.0
+    for _ in range(40):
+        psi = O.step(prob, psi, 5, t)
+        t += 5 * prob.dt
+        assert O.observables(prob, psi, t)["naive"] <= bound
+
+
+def test_proposition_5_averaged_norm_2d():
+    """Prop. 5 (Sect. 3): at r = 1/sqrt(2) the grid-averaged norm of u stays
+    below E0 (so ||u~||^2 + ||v~||^2 <= 2 E0) for arbitrary V.  With the
+    delta_+ reading of the (2+1)D functional the averaging carries +i:
+    ||u~||^2 = sum_j |(u_{j+(1,0)} + i u_{j+(1/2,1/2)} + u_j + i u_{j+(1/2,-1/2)}) / (2 sqrt 2)|^2
+    over j in Z^2 u (Z+1/2)^2; the proof's auxiliary E~ then expands to the
+    conserved E (the u-u cross terms telescope for either sign)."""
+    N = 8
+    prob = W.Problem(2, (N, N, 1), (1.0, 1.0, 1.0), 1.0 / math.sqrt(2.0), 0.3)
+    prob = prob.with_fields(V_static=W.random_potential(prob, 1, 1.5))
+    psi = W.random_state(prob, 2)
+    E0 = O.observables(prob, psi)["E"]
+
+    def unorm(s):
+        u0, u1 = s[0, 0], s[1, 0]
+        sx = lambda a: np.roll(a, -1, axis=1)
+        sy = lambda a: np.roll(a, -1, axis=0)
+        my = lambda a: np.roll(a, 1, axis=0)
+        # j on u0 sites (integer): j+(1,0) -> u0[x+1], j+(1/2,1/2) -> u1[j], j+(1/2,-1/2) -> u1[y-1]
+        a0 = (sx(u0) + 1j * u1 + u0 + 1j * my(u1)) / (2 * math.sqrt(2))
+        # j on u1 sites (half-integer): j+(1,0) -> u1[x+1], j+(1/2,1/2) -> u0[x+1,y+1], j+(1/2,-1/2) -> u0[x+1]
+        a1 = (sx(u1) + 1j * sx(sy(u0)) + u1 + 1j * sx(u0)) / (2 * math.sqrt(2))
+        return float(np.sum(np.abs(a0) ** 2) + np.sum(np.abs(a1) ** 2))
+
+    t = 0.0
+    for _ in range(30):
+        psi = O.step(prob, psi, 7, t)
+        t += 7 * prob.dt
+        assert unorm(psi) <= E0 * (1 + 1e-12)
+
+
+def test_partial_density_splits_naive_norm():
+    prob = W.Problem(2, (12, 8, 1), (1.0, 1.0, 1.0), 0.5, 0.1)
+    psi = W.random_state(prob, 1)
+    x0 = 5.25
+    right = O.partial_density(prob, psi, 0, x0)
+    xs = [W.site_positions(prob, pl)[0] for pl in range(4)]
+    want = sum(float(np.sum(np.abs(psi[pl][xs[pl] > x0]) ** 2)) for pl in range(4))
+    assert abs(right - want) < 1e-14
