@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the staggered leap-frog Dirac stepper on GB300.
+
+One benchmark step = one pass of the whole hot path over one workload: set
+up nothing, advance the resident state by the workload's number of time steps
+(both half-steps each) and evaluate the conserved functional E (FP64
+reduction).  Default workload: (3+1)D 128^3 periodic grid, m = 1, seeded
+Gaussian packet (sigma = 10), 1000 time steps, FP32 stencil with FP64
+reductions.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun: one independent replica per GPU (the method is
+advanced per simulation; replicas need no data exchange), timing is the max
+over ranks, value = total site updates / time.
+
+Prints ONE JSON line (rank 0).  GLUPS = cells x time steps / s / 1e9 (one
+site update = one unit cell advanced one full time step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spinor site-updates/s (GLUPS) & % HBM roofline; served p50/p99 latency"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def workload(name):
+    from paper_1309_3452_gb300 import workloads as W
+    if name == "3d128":
+        prob, psi, n = W.workload_3d(N=128, steps=1000)
+        desc = ("(3+1)D 128^3 periodic, m=1, no fields, Gaussian packet sigma=10 at the centre, "
+                "seeded k0 (|k0|<=1), dt=0.9/sqrt(3), 1000 time steps + E per step")
+    elif name == "3d512":
+        prob, psi, n = W.workload_3d(N=512, steps=200, sigma=24.0)
+        desc = "(3+1)D 512^3 periodic, m=1, no fields, packet sigma=24, 200 time steps + E per step"
+    elif name == "2d4096":
+        prob, psi, n = W.workload_klein(N=4096, steps=500)
+        desc = ("(2+1)D 4096^2 Klein step (V0 = 2E+m at x0 = N/2+1/4), m=0.2, packet sigma=40, "
+                "500 time steps + E per step")
+    elif name == "2d64":
+        prob, psi, n = W.workload_2d64(0.5)
+        desc = "(2+1)D 64^2, m=0.5, packet sigma=6, 200 time steps + E per step"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return prob, psi, n, desc
+
+
+def bytes_per_lup(dims, precision):
+    """Algorithmic HBM bytes per site update: every value read once and
+    written once per full step (8 complex values per (3+1)D cell, 4 per
+    (2+1)D cell)."""
+    vals = 8 if dims == 3 else 4
+    return 2 * vals * (8 if precision == "fp32" else 16)
+
+
+class Clocks:
+    """Samples nvidia-smi during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.f:
+            return None
+        try:
+            rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+            os.unlink(self.f.name)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha1()
+    for name in sorted(os.listdir(os.path.join(ROOT, "paper_1309_3452_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_1309_3452_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kernel, workload_name):
+    """DRAM bytes per launch from a committed ncu summary, valid only while
+    the kernel sources are unchanged since the capture."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    e = d.get(f"{kernel}@{workload_name}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(prob, psi, budget_s=15.0):
+    """The FP64 oracle as it stands, on a bounded sample of the workload."""
+    from oracle import oracle as O
+    O.build()
+    t = time.perf_counter()
+    st = O.step(prob, psi, 1)
+    t1 = time.perf_counter() - t
+    k = max(1, min(200, int(budget_s / max(t1, 1e-3))))
+    t = time.perf_counter()
+    O.step(prob, st, k)
+    dt = time.perf_counter() - t
+    return {"value": prob.cells * k / dt / 1e9, "unit": "GLUPS", "cores": O.threads(), "kind": "oracle",
+            "sample": f"{k} time steps of the same {'x'.join(map(str, prob.N[:prob.dims]))} "
+                      f"workload (FP64, {dt:.1f} s)"}
+
+
+def run_reference(args, prob, psi, n, desc, rank, world):
+    from oracle import oracle as O
+    if rank != 0:
+        return
+    O.build()
+    t = time.perf_counter()
+    O.step(prob, psi, 1)
+    t1 = time.perf_counter() - t
+    per_step = max(1, min(20, int(8.0 / max(t1, 1e-3))))  # each step: ~8 s of CPU work
+    st = psi
+    for _ in range(args.warmup):
+        st = O.step(prob, st, per_step)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        st = O.step(prob, st, per_step)
+        times.append(time.perf_counter() - t)
+    total = sum(times)
+    value = prob.cells * per_step * args.steps / total / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": desc, "grid": list(prob.N[:prob.dims]),
+                      "time_steps_per_step": per_step, "precision": "fp64 (CPU oracle)",
+                      "parallelism": "oracle, rank 0 only"},
+           "cpu_baseline": {"kind": "oracle", "cores": O.threads(), "value": value, "unit": "GLUPS",
+                            "sample": f"{per_step} time steps per step of the {desc} workload"},
+           "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="3d128", choices=["3d128", "3d512", "2d4096", "2d64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison line")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    prob, psi, n, desc = workload(args.workload)
+
+    if args.impl == "reference":
+        return run_reference(args, prob, psi, n, desc, rank, world)
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1309_3452_gb300 import dirac as D
+
+    stream = torch.cuda.Stream()
+    prec = D.FP32 if args.precision == "fp32" else D.FP64
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        sim = D.Sim(prob, prec, stream=stream.cuda_stream)
+    sim.set_spinor(psi)
+    E_start, _ = sim.norm()
+
+    def one_step():
+        sim.step(n)
+        return sim.norm()
+
+    for _ in range(args.warmup):
+        one_step()
+    launches0 = sim.launches
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    norm_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+    barrier()
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))  # evict the state from L2 between timed steps
+            torch.cuda.synchronize()
+            ev[i][0].record(stream)
+            sim.step(n)
+            norm_ev[i][0].record(stream)
+            E_end, _ = sim.norm()
+            norm_ev[i][1].record(stream)
+            ev[i][1].record(stream)
+        barrier()
+    launches = sim.launches - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    norm_ms = [a.elapsed_time(b) for a, b in norm_ev]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    lups = prob.cells * n
+    value = world * lups / (ms_per_step / 1e3) / 1e9
+
+    # dominant kernel: the time-step kernels; per launch = one full time step
+    stencil_ms = (sum(step_ms) - sum(norm_ms)) / args.steps / n
+    bpl = bytes_per_lup(prob.dims, args.precision)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    achieved = bpl * prob.cells / (stencil_ms / 1e3) / 1e9
+    kname = "step_fp32" if args.precision == "fp32" else "step_fp64"
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": ncu_traffic(kname, args.workload),
+                "peak_source": peak_src, "kernel": "one full time step (all launches of a step)",
+                "algorithmic_bytes_per_lup": bpl, "time_step_us": stencil_ms * 1e3}
+
+    # end to end through the C ABI with host buffers
+    nbytes = int(np.prod(prob.shape)) * 16
+    h_in = torch.from_numpy(psi.view(np.float64).reshape(-1).copy()).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    e2e_ms = []
+    for i in range(max(1, min(3, args.steps))):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.set_spinor_ptr(h_in.data_ptr())
+        sim.step(n)
+        sim.norm()
+        sim.get_spinor_ptr(h_out.data_ptr())
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_ms_step = statistics.median(e2e_ms)
+    if dist is not None:
+        tt = torch.tensor([e2e_ms_step], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms_step = float(tt.item())
+    e2e = {"value": world * lups / (e2e_ms_step / 1e3) / 1e9, "unit": "GLUPS",
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 8 * 5,
+           "ms_per_step": e2e_ms_step}
+
+    # the plain FP64 one-simulation-per-launch path on the same workload
+    fp64 = None
+    if not args.no_fp64 and args.precision == "fp32":
+        with D.Sim(prob, D.FP64, stream=stream.cuda_stream) as s64:
+            s64.set_spinor(psi)
+            n64 = max(1, n // 10)
+            s64.step(n64)
+            s64.norm()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s64.step(n64)
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b)
+            fp64 = {"value": prob.cells * n64 / (ms / 1e3) / 1e9, "unit": "GLUPS",
+                    "time_steps": n64, "ms": ms}
+    E_drift = abs(E_end - E_start) / abs(E_start)
+    sim.close()
+
+    clocks = clk.summary()
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(prob, psi)
+    out = {"metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+           "config": {"workload": desc, "grid": list(prob.N[:prob.dims]), "time_steps_per_step": n,
+                      "precision": args.precision + (" stencil, fp64 reductions"
+                                                     if args.precision == "fp32" else ""),
+                      "l2": f"flushed between timed steps (write of {2 * L2_BYTES >> 20} MiB); "
+                            f"state {D.state_bytes(prob.dims, prob.N, prec) >> 20} MiB",
+                      "parallelism": f"replicas x{world}"},
+           "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+           "gpu_launches": launches, "clocks": clocks, "fp64_plain": fp64,
+           "E_rel_drift": E_drift}
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * libdirac -- GB300 (sm_103a) CUDA implementation of the single-cone
+ * staggered space-time leap-frog scheme for the time-dependent Dirac equation
+ * (R. Hammer, W. Poetz, A. Arnold, arXiv:1309.3452).
+ *
+ * The scheme (Sect. 2, Eqs. sbegin-send, compact form Eq. 3+3Ddis and
+ * Eqs. ss1-ss4; Sect. 3, Eqs. scheme2Deq-scheme4thline) places each spinor
+ * component on its own sublattice of a grid staggered in space and time and
+ * advances it explicitly:  the "upper" components (A, B in (3+1)D; u in
+ * (2+1)D) go from t - dt/2 to t + dt/2 using centred differences of the
+ * "lower" ones (C, D; v) at t, then the lower components go from t to t + dt
+ * using the new upper values.  Mass and scalar potential enter through the
+ * time average of Eq. 3+3Ddis (a per-site Cayley factor), the vector
+ * potential through Peierls link factors (Sect. 4).
+ *
+ * Units: hbar = c = 1.  Lengths dx[a] = Delta_a, time step dt = Delta_t,
+ * r_a = dt / dx[a].  Periodic boundaries in units of the cell.
+ *
+ * ---------------------------------------------------------------------------
+ * Canonical host layout (dirac_set_spinor / dirac_get_spinor)
+ *   double[P][Nz][Ny][Nx][2]   (complex128, re then im; x fastest)
+ *   (3+1)D: P = 8 planes  A0 A1 B0 B1 C0 C1 D0 D1
+ *   (2+1)D: P = 4 planes  u0 u1 v0 v1  (Nz = 1)
+ * For cell j = (jx, jy, jz) the planes hold the values at positions
+ * (grid definitions of Sect. 2; fcr-u / fcr-v of Sect. 3)
+ *   A0  j dx                 A1  (j + (1/2,1/2,0)) dx
+ *   B0  (j + (1/2,0,1/2)) dx B1  (j + (0,1/2,1/2)) dx
+ *   C0  (j + (0,0,1/2)) dx   C1  (j + (1/2,1/2,1/2)) dx
+ *   D0  (j + (1/2,0,0)) dx   D1  (j + (0,1/2,0)) dx
+ *   u0 = A0, u1 = A1, v0 = D0, v1 = D1 without z.
+ * Upper planes (A, B, u) hold their values at time t - dt/2, lower planes
+ * (C, D, v) at time t, where t is the simulation time (dirac_get_time).
+ * One real per site (the optional static potential) uses the same layout
+ * without the trailing [2].
+ *
+ * Ownership: the library allocates and owns all device memory of a
+ * simulation; host buffers belong to the caller, are only read or written
+ * during the call, and are never retained.
+ *
+ * Errors: every call returns a dirac_status; no exception or abort crosses
+ * the ABI.  On failure dirac_last_error() describes the cause.  A CUDA error
+ * leaves the simulation in an unspecified state (destroy it).
+ *
+ * Streams: all device work of a simulation runs on the stream given at
+ * creation (NULL = the legacy default stream).  dirac_step only enqueues
+ * work; dirac_norm, dirac_partial_density, dirac_get_spinor synchronise the
+ * stream before returning.
+ * ---------------------------------------------------------------------------
+ */
+#ifndef DIRAC_H
+#define DIRAC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dirac_sim dirac_sim;
+
+typedef enum {
+  DIRAC_OK = 0,
+  DIRAC_ERR_INVALID = 1,     /* bad argument (NULL pointer, dims, N < 2, dx <= 0, ...) */
+  DIRAC_ERR_UNSTABLE = 2,    /* r_x^2 + r_y^2 (+ r_z^2) > 1 (Sect. 2.2 / Sect. 3 bound) */
+  DIRAC_ERR_OOM = 3,         /* device allocation failed */
+  DIRAC_ERR_CUDA = 4,        /* a CUDA call or kernel launch failed */
+  DIRAC_ERR_DIVERGED = 5,    /* the conserved functional became non-finite or grew */
+  DIRAC_ERR_TIMEOUT = 6,     /* a bounded device wait gave up */
+  DIRAC_ERR_UNSUPPORTED = 7  /* valid request this build does not implement */
+} dirac_status;
+
+typedef enum {
+  DIRAC_FP64 = 0, /* complex128 state, FP64 arithmetic (validation mode) */
+  DIRAC_FP32 = 1  /* complex64 state, FP32 stencil with compensated (hi+lo)
+                     coefficients; FP64 reductions */
+} dirac_precision;
+
+/* flags for dirac_create */
+#define DIRAC_FLAG_ALLOW_UNSTABLE 0x1u /* accept r beyond the stability bound */
+
+/*
+ * External fields (Sect. 2: V in Eq. 3+3D; Sect. 4: vector potential).
+ * Scalar potential, evaluated at every site's own position x:
+ *   V(x,t) = V0
+ *          + step_V * H(x[step_axis] - step_x0)        (Klein step, Sect. 5;
+ *                                                        step_axis < 0: none)
+ *          - sc_Z / sqrt(|x - sc_center|^2 + sc_a^2)    (soft core; sc_Z = 0: none)
+ *          + V_static(x) * (1 + Vmod_amp * cos(Vmod_omega * t))
+ * Vector potential, coupled with charge q through link factors:
+ *   A(x,t) = A_const + e_{Apw_pol} * Apw_amp * cos(Apw_k . x - Apw_omega t + Apw_phase)
+ * A must be periodic on the box for the link factors at the wrap to be
+ * consistent.  The upper half-step uses the fields at time t, the lower
+ * half-step at t + dt/2 (the time sheets of Eqs. ss1-ss4).
+ * V_static: NULL, or a host array of one real per site (canonical layout);
+ * it is copied during dirac_create.
+ */
+typedef struct {
+  double V0;
+  int step_axis;
+  double step_x0, step_V;
+  double sc_Z, sc_a, sc_center[3];
+  const double* V_static;
+  double Vmod_amp, Vmod_omega;
+  double q;
+  double A_const[3];
+  double Apw_amp, Apw_k[3], Apw_omega, Apw_phase;
+  int Apw_pol;
+} dirac_fields;
+
+/* Zero fields: everything 0 except q = 1, step_axis = -1, sc_a = 1. */
+void dirac_fields_default(dirac_fields* f);
+
+/*
+ * Create a simulation of the (dims+1)D scheme on an N[0] x N[1] (x N[2])
+ * periodic grid of unit cells (each cell carries two sites of every
+ * component), lattice constants dx[], time step dt, mass m.  fields may be
+ * NULL (free particle).  Rejects N[a] < 2, dx[a] <= 0, dt <= 0 and (unless
+ * DIRAC_FLAG_ALLOW_UNSTABLE) sum_a (dt/dx[a])^2 > 1.  cuda_stream is a
+ * cudaStream_t (may be NULL).  The state starts at zero with t = 0.
+ * On success *out owns the simulation; free it with dirac_destroy.
+ */
+dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], const double dx[3], double dt,
+                          double m, const dirac_fields* fields, dirac_precision precision,
+                          unsigned flags, void* cuda_stream);
+
+/* Copy a full state in the canonical host layout (complex128) into the
+   simulation (converted to the simulation's precision on the device). */
+dirac_status dirac_set_spinor(dirac_sim* sim, const double* host);
+
+/* Copy the current state out in the canonical host layout (complex128);
+   synchronises the stream. */
+dirac_status dirac_get_spinor(dirac_sim* sim, double* host);
+
+/* Enqueue nsteps full time steps (both half-steps each; Eq. 3+3Ddis);
+   t advances by nsteps*dt.  nsteps >= 0. */
+dirac_status dirac_step(dirac_sim* sim, long nsteps);
+
+/*
+ * Conserved functional of the stored state (Lemma of Sect. 2, Eq. EPM, and
+ * Lemma of Sect. 3), written with every lower value G paired with the
+ * difference part S_G of its own update:
+ *   E = sum |psi|^2 + Re sum_{lower sites} conj(G) S_G(upper),
+ *   S_G = r_x dx(G) + s_y r_y dy(G) + s_z r_z dz(G)   (Eqs. ss3, ss4),
+ * with link factors at the upper sheet's time t - dt/2.  Equal to Eq. EPM by
+ * summation by parts for time-independent A.  In (2+1)D this is
+ * ||u||^2 + ||v||^2 + r Re (delta_+ u, v); Sect. 3 prints delta_- u, which
+ * the scheme as printed does not conserve.
+ * *naive (may be NULL) receives sum |psi|^2 over all values (Sect. 3: the
+ * naive norm, conserved only on average).  Accumulated in FP64 in a fixed
+ * order (deterministic).  Synchronises the stream.
+ * Returns DIRAC_ERR_DIVERGED if E is not finite.
+ */
+dirac_status dirac_norm(dirac_sim* sim, double* E, double* naive);
+
+/* sum of |psi|^2 over the values whose position along axis exceeds x0
+   (transmitted probability for the Klein step, Sect. 5).  Synchronises. */
+dirac_status dirac_partial_density(dirac_sim* sim, int axis, double x0, double* out);
+
+/* simulation time t of the lower sheet (upper planes are at t - dt/2) */
+dirac_status dirac_get_time(const dirac_sim* sim, double* t);
+dirac_status dirac_set_time(dirac_sim* sim, double t);
+
+/* number of CUDA kernels this simulation has launched since creation
+   (every launch of every call counts once) */
+long long dirac_kernel_launches(const dirac_sim* sim);
+
+/* device bytes a simulation of this shape and precision allocates */
+size_t dirac_state_bytes(int dims, const int N[3], dirac_precision precision);
+
+/* human-readable description of the last failure on sim (or of the last
+   failed dirac_create when sim is NULL) */
+const char* dirac_last_error(const dirac_sim* sim);
+
+/* free all device memory of sim (NULL is ignored); synchronises its stream */
+void dirac_destroy(dirac_sim* sim);
+
+/* ABI version of this header */
+int dirac_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DIRAC_H */

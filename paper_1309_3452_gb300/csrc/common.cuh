@@ -1,0 +1,259 @@
+// Shared device definitions of libdirac: precision traits, the staggered grid
+// geometry and the per-value update of the leap-frog scheme (arXiv:1309.3452).
+//
+// Device layout: one array per plane (A0,A1,B0,B1,C0,C1,D0,D1 in (3+1)D;
+// u0,u1,v0,v1 in (2+1)D), each [z][y][x] with x fastest, complex values
+// interleaved (float2 / double2).  Plane k starts at base + k*pstride
+// elements; pstride is a multiple of 64 elements.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dirac {
+
+// ------------------------------------------------------------------ geometry
+// Half-lattice offsets (units of dx/2) of each plane inside its cell: the grid
+// definitions of Sect. 2 (A,B,C,D) and Sect. 3 (u,v).
+//   plane:    A0      A1      B0      B1      C0      C1      D0      D1
+__host__ __device__ constexpr int off3(int plane, int axis) {
+  // bit 0 = x, bit 1 = y, bit 2 = z
+  return (((plane == 0) ? 0 : (plane == 1) ? 3 : (plane == 2) ? 5 : (plane == 3) ? 6
+         : (plane == 4) ? 4 : (plane == 5) ? 7 : (plane == 6) ? 1 : 2) >> axis) & 1;
+}
+//   plane:    u0      u1      v0      v1
+__host__ __device__ constexpr int off2(int plane, int axis) {
+  return axis == 2 ? 0 : ((((plane == 0) ? 0 : (plane == 1) ? 3 : (plane == 2) ? 1 : 2) >> axis) & 1);
+}
+template <int DIMS>
+__host__ __device__ constexpr int plane_off(int plane, int axis) {
+  return DIMS == 3 ? off3(plane, axis) : off2(plane, axis);
+}
+template <int DIMS>
+__host__ __device__ constexpr int nplanes() { return DIMS == 3 ? 8 : 4; }
+// upper planes (A,B / u) come first
+template <int DIMS>
+__host__ __device__ constexpr bool is_upper(int plane) { return plane < (DIMS == 3 ? 4 : 2); }
+
+// The plane whose offset differs from `plane` only along `axis`: the
+// neighbours at +-dx_a/2 of a value on `plane` live there.
+template <int DIMS>
+__host__ __device__ constexpr int partner(int plane, int axis) {
+  // search the plane table for the flipped offset (constexpr-evaluated)
+  int want[3] = {plane_off<DIMS>(plane, 0), plane_off<DIMS>(plane, 1), plane_off<DIMS>(plane, 2)};
+  want[axis] ^= 1;
+  int found = -1;
+  for (int q = 0; q < nplanes<DIMS>(); ++q)
+    if (plane_off<DIMS>(q, 0) == want[0] && plane_off<DIMS>(q, 1) == want[1] &&
+        plane_off<DIMS>(q, 2) == want[2])
+      found = q;
+  return found;
+}
+// Cell shift of the neighbour at dir = +1 (x + dx_a/2) or -1 (x - dx_a/2):
+// a value at half-lattice 2j+o has its neighbours at 2j+o+-1, i.e. in cell
+// j (o=0,+ / o=1,-), j-1 (o=0,-) or j+1 (o=1,+).
+template <int DIMS>
+__host__ __device__ constexpr int nb_shift(int plane, int axis, int dir) {
+  return plane_off<DIMS>(plane, axis) == 0 ? (dir > 0 ? 0 : -1) : (dir > 0 ? 1 : 0);
+}
+// p = (o_x + o_y) mod 2 selects the sign pattern of the y and z differences:
+// p = 0 (A, C, u):  S = r_x dx - i r_y dy + r_z dz
+// p = 1 (B, D, v):  S = r_x dx + i r_y dy - r_z dz        (Eqs. ss1-ss4)
+template <int DIMS>
+__host__ __device__ constexpr int sign_class(int plane) {
+  return (plane_off<DIMS>(plane, 0) + plane_off<DIMS>(plane, 1)) & 1;
+}
+
+// ------------------------------------------------------------------ precision
+struct F64 {
+  using real = double;
+  using cplx = double2;
+  // F+ = alpha F - gamma S'   (alpha = (1-i th)/(1+i th), gamma = r_x/(1+i th))
+  struct Coef { double2 a, g; };
+  struct Ratio { double v; };      // r_y / r_x, r_z / r_x
+  struct Link { double2 u; };      // exp(-i q A_a dx_a/2)
+};
+struct F32 {
+  using real = float;
+  using cplx = float2;
+  // every coefficient carried as an unevaluated sum hi + lo of two floats so
+  // that its rounding does not accumulate coherently over many steps
+  struct Coef { float2 a_hi, a_lo, g_hi, g_lo; };
+  struct Ratio { float hi, lo; };
+  struct Link { float2 hi, lo; };
+};
+
+__device__ __forceinline__ double2 cmk(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 cmk(float a, float b) { return make_float2(a, b); }
+
+// explicit-rounding primitives (no contraction: every kernel variant that
+// uses these helpers produces bit-identical values)
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+template <class C>
+__device__ __forceinline__ C csub(C a, C b) { return cmk(rsub(a.x, b.x), rsub(a.y, b.y)); }
+template <class C>
+__device__ __forceinline__ C cadd(C a, C b) { return cmk(radd(a.x, b.x), radd(a.y, b.y)); }
+
+// ------------------------------------------------------------------ links
+__device__ __forceinline__ double2 link_mul(const F64::Link& L, double2 v) {
+  return cmk(rfma(L.u.x, v.x, -rmul(L.u.y, v.y)), rfma(L.u.x, v.y, rmul(L.u.y, v.x)));
+}
+// conj(L) * v
+__device__ __forceinline__ double2 link_mulc(const F64::Link& L, double2 v) {
+  return cmk(rfma(L.u.x, v.x, rmul(L.u.y, v.y)), rfma(L.u.x, v.y, -rmul(L.u.y, v.x)));
+}
+__device__ __forceinline__ float2 link_mul(const F32::Link& L, float2 v) {
+  float re = rfma(L.lo.x, v.x, -rmul(L.lo.y, v.y));
+  float im = rfma(L.lo.x, v.y, rmul(L.lo.y, v.x));
+  re = rfma(L.hi.x, v.x, rfma(-L.hi.y, v.y, re));
+  im = rfma(L.hi.x, v.y, rfma(L.hi.y, v.x, im));
+  return cmk(re, im);
+}
+__device__ __forceinline__ float2 link_mulc(const F32::Link& L, float2 v) {
+  float re = rfma(L.lo.x, v.x, rmul(L.lo.y, v.y));
+  float im = rfma(L.lo.x, v.y, -rmul(L.lo.y, v.x));
+  re = rfma(L.hi.x, v.x, rfma(L.hi.y, v.y, re));
+  im = rfma(L.hi.x, v.y, rfma(-L.hi.y, v.x, im));
+  return cmk(re, im);
+}
+
+// ------------------------------------------------------------------ update
+// Difference part of one update without the factor r_x:
+//   S' = d_x + s_y (r_y/r_x) d_y + s_z (r_z/r_x) d_z,
+// d_a = (neighbour at +dx_a/2) - (neighbour at -dx_a/2), s_y = -i (p=0) or +i
+// (p=1), s_z = +1 (p=0) or -1 (p=1)  (Eqs. ss1-ss4; Eqs. scheme2Deq ff.).
+// iso: r_x = r_y = r_z, so the ratios are exactly one.
+template <class P, int DIMS>
+__device__ __forceinline__ typename P::cplx combine(typename P::cplx dx, typename P::cplx dy,
+                                                    typename P::cplx dz, int p, bool iso,
+                                                    const typename P::Ratio& ry,
+                                                    const typename P::Ratio& rz);
+
+template <>
+__device__ __forceinline__ double2 combine<F64, 3>(double2 dx, double2 dy, double2 dz, int p,
+                                                   bool iso, const F64::Ratio& ry,
+                                                   const F64::Ratio& rz) {
+  double2 ty = p ? cmk(-dy.y, dy.x) : cmk(dy.y, -dy.x);
+  double2 tz = p ? cmk(-dz.x, -dz.y) : dz;
+  if (!iso) {
+    ty = cmk(rmul(ry.v, ty.x), rmul(ry.v, ty.y));
+    tz = cmk(rmul(rz.v, tz.x), rmul(rz.v, tz.y));
+  }
+  return cadd(cadd(dx, ty), tz);
+}
+template <>
+__device__ __forceinline__ double2 combine<F64, 2>(double2 dx, double2 dy, double2, int p, bool iso,
+                                                   const F64::Ratio& ry, const F64::Ratio&) {
+  double2 ty = p ? cmk(-dy.y, dy.x) : cmk(dy.y, -dy.x);
+  if (!iso) ty = cmk(rmul(ry.v, ty.x), rmul(ry.v, ty.y));
+  return cadd(dx, ty);
+}
+__device__ __forceinline__ float2 ratio_mul(const F32::Ratio& r, float2 t) {
+  return cmk(rfma(r.hi, t.x, rmul(r.lo, t.x)), rfma(r.hi, t.y, rmul(r.lo, t.y)));
+}
+template <>
+__device__ __forceinline__ float2 combine<F32, 3>(float2 dx, float2 dy, float2 dz, int p, bool iso,
+                                                  const F32::Ratio& ry, const F32::Ratio& rz) {
+  float2 ty = p ? cmk(-dy.y, dy.x) : cmk(dy.y, -dy.x);
+  float2 tz = p ? cmk(-dz.x, -dz.y) : dz;
+  if (!iso) {
+    ty = ratio_mul(ry, ty);
+    tz = ratio_mul(rz, tz);
+  }
+  return cadd(cadd(dx, ty), tz);
+}
+template <>
+__device__ __forceinline__ float2 combine<F32, 2>(float2 dx, float2 dy, float2, int p, bool iso,
+                                                  const F32::Ratio& ry, const F32::Ratio&) {
+  float2 ty = p ? cmk(-dy.y, dy.x) : cmk(dy.y, -dy.x);
+  if (!iso) ty = ratio_mul(ry, ty);
+  return cadd(dx, ty);
+}
+
+// F+ = alpha F - gamma S'  (the Cayley form of Eqs. ss1-ss4:
+//   F+ = ((1 - i th) F - S) / (1 + i th),  th = dt (beta m + V)/2)
+__device__ __forceinline__ double2 apply(const F64::Coef& c, double2 F, double2 S) {
+  double re = rfma(c.a.x, F.x, rfma(-c.a.y, F.y, rfma(-c.g.x, S.x, rmul(c.g.y, S.y))));
+  double im = rfma(c.a.x, F.y, rfma(c.a.y, F.x, rfma(-c.g.x, S.y, -rmul(c.g.y, S.x))));
+  return cmk(re, im);
+}
+__device__ __forceinline__ float2 apply(const F32::Coef& c, float2 F, float2 S) {
+  // small (lo) products first, then the hi products on top
+  float re = rfma(c.a_lo.x, F.x, rfma(-c.a_lo.y, F.y, rfma(-c.g_lo.x, S.x, rmul(c.g_lo.y, S.y))));
+  float im = rfma(c.a_lo.x, F.y, rfma(c.a_lo.y, F.x, rfma(-c.g_lo.x, S.y, -rmul(c.g_lo.y, S.x))));
+  re = rfma(c.a_hi.x, F.x, rfma(-c.a_hi.y, F.y, rfma(-c.g_hi.x, S.x, rfma(c.g_hi.y, S.y, re))));
+  im = rfma(c.a_hi.x, F.y, rfma(c.a_hi.y, F.x, rfma(-c.g_hi.x, S.y, rfma(-c.g_hi.y, S.x, im))));
+  return cmk(re, im);
+}
+
+// ------------------------------------------------------------------ fields
+enum CoefMode { COEF_UNIFORM = 0, COEF_STEP = 1, COEF_GENERAL = 2 };
+enum LinkMode { LINK_NONE = 0, LINK_CONST = 1, LINK_GENERAL = 2 };
+
+// Analytic field description, FP64, for the per-site (general) paths.
+struct FieldDesc {
+  double dt, m, rx;
+  double dx[3];
+  double V0;
+  int step_axis;       // < 0: no step
+  int step_X;          // sites with half-lattice index >= step_X along the axis are beyond it
+  double step_V;
+  double sc_Z, sc_a2, sc_c[3];
+  const double* Vstatic;  // device, one real per site, plane-major like the state (pstride)
+  double Vmod_amp, Vmod_omega;
+  double q, A_const[3], Apw_amp, Apw_k[3], Apw_omega, Apw_phase;
+  int Apw_pol;
+};
+
+// Compute alpha and gamma in FP64 from theta.
+__device__ __forceinline__ void coef_from_theta(double th, double rx, double2& a, double2& g) {
+  double inv = 1.0 / (1.0 + th * th);
+  a = make_double2((1.0 - th * th) * inv, -2.0 * th * inv);
+  g = make_double2(rx * inv, -rx * th * inv);
+}
+
+// scalar potential at half-lattice point (X,Y,Z) at time t, FP64
+__device__ __forceinline__ double potential_at(const FieldDesc& f, int dims, long long X, long long Y,
+                                               long long Z, long long site, long long pstride,
+                                               int plane, double t) {
+  double V = f.V0;
+  long long H[3] = {X, Y, Z};
+  if (f.step_axis >= 0 && H[f.step_axis] >= f.step_X) V += f.step_V;
+  if (f.sc_Z != 0.0) {
+    double r2 = 0.0;
+    for (int a = 0; a < dims; ++a) {
+      double d = (double)H[a] * f.dx[a] * 0.5 - f.sc_c[a];
+      r2 += d * d;
+    }
+    V -= f.sc_Z / sqrt(r2 + f.sc_a2);
+  }
+  if (f.Vstatic) V += f.Vstatic[(long long)plane * pstride + site] * (1.0 + f.Vmod_amp * cos(f.Vmod_omega * t));
+  return V;
+}
+
+// link phase phi = q A_a(midpoint, t) dx_a/2 for the link from half-lattice
+// point H towards dir (+1/-1) along axis a; the midpoint is at H + dir/2.
+__device__ __forceinline__ double link_phase(const FieldDesc& f, int dims, const long long H[3],
+                                             int axis, int dir, double t) {
+  double A = f.A_const[axis];
+  if (f.Apw_amp != 0.0 && f.Apw_pol == axis) {
+    double ph = -f.Apw_omega * t + f.Apw_phase;
+    for (int b = 0; b < dims; ++b) {
+      double y = (double)H[b] * f.dx[b] * 0.5;
+      if (b == axis) y += dir * f.dx[b] * 0.25;
+      ph += f.Apw_k[b] * y;
+    }
+    A += f.Apw_amp * cos(ph);
+  }
+  return f.q * A * f.dx[axis] * 0.5;
+}
+
+}  // namespace dirac

@@ -1,0 +1,431 @@
+// Host side of libdirac: the C ABI declared in include/dirac.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/dirac.h"
+#include "kernels.cuh"
+
+using namespace dirac;
+
+struct dirac_sim {
+  int dims = 0;
+  int N[3] = {1, 1, 1};
+  double dx[3] = {1, 1, 1};
+  double dt = 0, m = 0;
+  dirac_precision prec = DIRAC_FP64;
+  unsigned flags = 0;
+  dirac_fields f{};
+  cudaStream_t stream = nullptr;
+  long long ncell = 0, pstride = 0;
+  int np = 0;
+  size_t elem = 0;            // bytes per complex value
+  void* state = nullptr;      // np * pstride values
+  double2* staging = nullptr; // one canonical plane (FP32 conversions)
+  double* Vstatic = nullptr;  // one real per site (plane-major, pstride)
+  double* partials = nullptr;
+  double* sums_dev = nullptr;
+  double* sums_host = nullptr; // pinned
+  int red_blocks = 0;
+  double t0 = 0;              // time set by dirac_set_time (or 0)
+  long long k = 0;            // steps taken since then: t = t0 + k dt
+  int iso = 1;
+  int coef_mode = COEF_UNIFORM, link_mode = LINK_NONE;
+  int step_X = 0;
+  long long launches = 0;     // kernels launched so far
+  std::string err;
+};
+
+static std::string g_create_error;
+
+static dirac_status fail(dirac_sim* s, dirac_status st, const std::string& msg) {
+  if (s) s->err = msg; else g_create_error = msg;
+  return st;
+}
+static dirac_status cuda_fail(dirac_sim* s, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(s, e == cudaErrorMemoryAllocation ? DIRAC_ERR_OOM : DIRAC_ERR_CUDA, m);
+}
+#define CK(sim, call)                                          \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return cuda_fail((sim), e_, #call); \
+  } while (0)
+
+static long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+static long long cells_of(int dims, const int N[3]) {
+  return (long long)N[0] * N[1] * (dims == 3 ? N[2] : 1);
+}
+
+extern "C" size_t dirac_state_bytes(int dims, const int N[3], dirac_precision p) {
+  if ((dims != 2 && dims != 3) || !N) return 0;
+  long long nc = cells_of(dims, N);
+  long long ps = round_up(nc, 64);
+  size_t elem = p == DIRAC_FP32 ? sizeof(float2) : sizeof(double2);
+  size_t bytes = (size_t)(dims == 3 ? 8 : 4) * ps * elem;
+  if (p == DIRAC_FP32) bytes += (size_t)ps * sizeof(double2);  // conversion staging
+  return bytes;
+}
+
+extern "C" void dirac_fields_default(dirac_fields* f) {
+  if (!f) return;
+  std::memset(f, 0, sizeof(*f));
+  f->q = 1.0;
+  f->step_axis = -1;
+  f->sc_a = 1.0;
+}
+
+extern "C" int dirac_version(void) { return 1; }
+
+extern "C" const char* dirac_last_error(const dirac_sim* s) {
+  return s ? s->err.c_str() : g_create_error.c_str();
+}
+
+// smallest half-lattice index H with (double)H * dx / 2 > x0
+static int threshold_index(double x0, double dx) {
+  double g = std::floor(2.0 * x0 / dx) - 4.0;
+  if (g < -4e9) g = -4e9;
+  long long H = (long long)g;
+  while (!((double)H * dx / 2.0 > x0)) ++H;
+  return (int)H;
+}
+
+template <class P> static typename P::Coef make_coef(double th, double rx);
+template <> F64::Coef make_coef<F64>(double th, double rx) {
+  double inv = 1.0 / (1.0 + th * th);
+  F64::Coef c;
+  c.a = make_double2((1.0 - th * th) * inv, -2.0 * th * inv);
+  c.g = make_double2(rx * inv, -rx * th * inv);
+  return c;
+}
+static void split(double v, float& hi, float& lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+template <> F32::Coef make_coef<F32>(double th, double rx) {
+  F64::Coef d = make_coef<F64>(th, rx);
+  F32::Coef c;
+  split(d.a.x, c.a_hi.x, c.a_lo.x);
+  split(d.a.y, c.a_hi.y, c.a_lo.y);
+  split(d.g.x, c.g_hi.x, c.g_lo.x);
+  split(d.g.y, c.g_hi.y, c.g_lo.y);
+  return c;
+}
+template <class P> static typename P::Ratio make_ratio(double v);
+template <> F64::Ratio make_ratio<F64>(double v) { return F64::Ratio{v}; }
+template <> F32::Ratio make_ratio<F32>(double v) {
+  F32::Ratio r;
+  split(v, r.hi, r.lo);
+  return r;
+}
+template <class P> static typename P::Link make_link(double phi);
+template <> F64::Link make_link<F64>(double phi) {
+  return F64::Link{make_double2(std::cos(phi), -std::sin(phi))};
+}
+template <> F32::Link make_link<F32>(double phi) {
+  F32::Link L;
+  split(std::cos(phi), L.hi.x, L.lo.x);
+  split(-std::sin(phi), L.hi.y, L.lo.y);
+  return L;
+}
+
+static FieldDesc field_desc(const dirac_sim* s) {
+  FieldDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.dt = s->dt;
+  d.m = s->m;
+  d.rx = s->dt / s->dx[0];
+  for (int a = 0; a < 3; ++a) d.dx[a] = s->dx[a];
+  d.V0 = s->f.V0;
+  d.step_axis = s->f.step_axis;
+  d.step_X = s->step_X;
+  d.step_V = s->f.step_V;
+  d.sc_Z = s->f.sc_Z;
+  d.sc_a2 = s->f.sc_a * s->f.sc_a;
+  for (int a = 0; a < 3; ++a) d.sc_c[a] = s->f.sc_center[a];
+  d.Vstatic = s->Vstatic;
+  d.Vmod_amp = s->f.Vmod_amp;
+  d.Vmod_omega = s->f.Vmod_omega;
+  d.q = s->f.q;
+  for (int a = 0; a < 3; ++a) {
+    d.A_const[a] = s->f.A_const[a];
+    d.Apw_k[a] = s->f.Apw_k[a];
+  }
+  d.Apw_amp = s->f.Apw_amp;
+  d.Apw_omega = s->f.Apw_omega;
+  d.Apw_phase = s->f.Apw_phase;
+  d.Apw_pol = s->f.Apw_pol;
+  return d;
+}
+
+template <class P>
+static void plane_ptrs(dirac_sim* s, typename P::cplx* (&pl)[8]) {
+  auto* base = static_cast<typename P::cplx*>(s->state);
+  for (int k = 0; k < 8; ++k) pl[k] = k < s->np ? base + (long long)k * s->pstride : nullptr;
+}
+
+template <class P>
+static HalfStepArgs<P> half_args(dirac_sim* s, bool upper, double t) {
+  HalfStepArgs<P> a;
+  std::memset(&a, 0, sizeof(a));
+  plane_ptrs<P>(s, a.pl);
+  for (int k = 0; k < 3; ++k) a.N[k] = s->N[k];
+  a.pstride = s->pstride;
+  a.iso = s->iso;
+  double rx = s->dt / s->dx[0];
+  a.ry = make_ratio<P>((s->dt / s->dx[1]) / rx);
+  a.rz = make_ratio<P>((s->dt / s->dx[2]) / rx);
+  a.coef_mode = s->coef_mode;
+  double beta = upper ? 1.0 : -1.0;
+  a.c_in = make_coef<P>(s->dt * (beta * s->m + s->f.V0) / 2.0, rx);
+  a.c_out = make_coef<P>(s->dt * (beta * s->m + (s->f.V0 + s->f.step_V)) / 2.0, rx);
+  a.step_axis = s->f.step_axis;
+  a.step_X = s->step_X;
+  a.link_mode = s->link_mode;
+  for (int k = 0; k < 3; ++k) a.L[k] = make_link<P>(s->f.q * s->f.A_const[k] * s->dx[k] / 2.0);
+  a.f = field_desc(s);
+  a.t = t;
+  a.beta = beta;
+  return a;
+}
+
+extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], const double dx[3],
+                                     double dt, double m, const dirac_fields* fields,
+                                     dirac_precision precision, unsigned flags, void* stream) {
+  if (!out) return fail(nullptr, DIRAC_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (dims != 2 && dims != 3) return fail(nullptr, DIRAC_ERR_INVALID, "dims must be 2 or 3");
+  if (!N || !dx) return fail(nullptr, DIRAC_ERR_INVALID, "N or dx is NULL");
+  if (precision != DIRAC_FP32 && precision != DIRAC_FP64)
+    return fail(nullptr, DIRAC_ERR_INVALID, "unknown precision");
+  for (int a = 0; a < dims; ++a) {
+    if (N[a] < 2) return fail(nullptr, DIRAC_ERR_INVALID, "N[a] must be >= 2");
+    if (!(dx[a] > 0.0) || !std::isfinite(dx[a]))
+      return fail(nullptr, DIRAC_ERR_INVALID, "dx[a] must be positive and finite");
+  }
+  if (!(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(m))
+    return fail(nullptr, DIRAC_ERR_INVALID, "dt must be positive; m finite");
+  double r2 = 0.0;
+  for (int a = 0; a < dims; ++a) r2 += (dt / dx[a]) * (dt / dx[a]);
+  if (r2 > 1.0 && !(flags & DIRAC_FLAG_ALLOW_UNSTABLE))
+    return fail(nullptr, DIRAC_ERR_UNSTABLE,
+                "sum_a (dt/dx_a)^2 > 1: beyond the stability bound of the scheme");
+  dirac_fields f;
+  if (fields) f = *fields; else dirac_fields_default(&f);
+  if (f.step_axis >= dims) return fail(nullptr, DIRAC_ERR_INVALID, "step_axis >= dims");
+  if (f.Apw_amp != 0.0 && (f.Apw_pol < 0 || f.Apw_pol >= dims))
+    return fail(nullptr, DIRAC_ERR_INVALID, "Apw_pol must be a spatial axis");
+
+  dirac_sim* s = new (std::nothrow) dirac_sim();
+  if (!s) return fail(nullptr, DIRAC_ERR_OOM, "host allocation failed");
+  s->dims = dims;
+  for (int a = 0; a < 3; ++a) {
+    s->N[a] = (a < dims) ? N[a] : 1;
+    s->dx[a] = (a < dims) ? dx[a] : 1.0;
+  }
+  s->dt = dt;
+  s->m = m;
+  s->prec = precision;
+  s->flags = flags;
+  s->f = f;
+  s->f.V_static = nullptr;
+  s->stream = static_cast<cudaStream_t>(stream);
+  s->ncell = cells_of(dims, s->N);
+  s->pstride = round_up(s->ncell, 64);
+  s->np = dims == 3 ? 8 : 4;
+  s->elem = precision == DIRAC_FP32 ? sizeof(float2) : sizeof(double2);
+  s->iso = (dx[0] == dx[1]) && (dims == 2 || dx[0] == dx[2]);
+  bool general_V = f.sc_Z != 0.0 || fields && fields->V_static;
+  s->coef_mode = general_V ? COEF_GENERAL : (f.step_axis >= 0 ? COEF_STEP : COEF_UNIFORM);
+  if (f.step_axis >= 0) s->step_X = threshold_index(f.step_x0, s->dx[f.step_axis]);
+  bool any_A = f.A_const[0] != 0.0 || f.A_const[1] != 0.0 || f.A_const[2] != 0.0;
+  s->link_mode = f.Apw_amp != 0.0 ? LINK_GENERAL : (any_A ? LINK_CONST : LINK_NONE);
+
+  auto cleanup_fail = [&](dirac_status st) {
+    std::string msg = s->err;
+    dirac_destroy(s);
+    return fail(nullptr, st, msg);
+  };
+  cudaError_t e;
+  size_t sbytes = (size_t)s->np * s->pstride * s->elem;
+  if ((e = cudaMalloc(&s->state, sbytes)) != cudaSuccess) return cleanup_fail(cuda_fail(s, e, "cudaMalloc(state)"));
+  if ((e = cudaMemsetAsync(s->state, 0, sbytes, s->stream)) != cudaSuccess)
+    return cleanup_fail(cuda_fail(s, e, "cudaMemsetAsync(state)"));
+  if (precision == DIRAC_FP32) {
+    if ((e = cudaMalloc(&s->staging, (size_t)s->pstride * sizeof(double2))) != cudaSuccess)
+      return cleanup_fail(cuda_fail(s, e, "cudaMalloc(staging)"));
+  }
+  if (fields && fields->V_static) {
+    size_t vb = (size_t)s->np * s->pstride * sizeof(double);
+    if ((e = cudaMalloc(&s->Vstatic, vb)) != cudaSuccess) return cleanup_fail(cuda_fail(s, e, "cudaMalloc(V)"));
+    for (int k = 0; k < s->np; ++k) {
+      e = cudaMemcpyAsync(s->Vstatic + (long long)k * s->pstride, fields->V_static + (long long)k * s->ncell,
+                          (size_t)s->ncell * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+      if (e != cudaSuccess) return cleanup_fail(cuda_fail(s, e, "cudaMemcpyAsync(V)"));
+    }
+  }
+  long long want = (s->ncell + 255) / 256;
+  s->red_blocks = (int)(want > 152 * 8 ? 152 * 8 : (want < 1 ? 1 : want));
+  if ((e = cudaMalloc(&s->partials, (size_t)s->red_blocks * kObsSums * sizeof(double))) != cudaSuccess)
+    return cleanup_fail(cuda_fail(s, e, "cudaMalloc(partials)"));
+  if ((e = cudaMalloc(&s->sums_dev, kObsSums * sizeof(double))) != cudaSuccess)
+    return cleanup_fail(cuda_fail(s, e, "cudaMalloc(sums)"));
+  if ((e = cudaMallocHost(&s->sums_host, kObsSums * sizeof(double))) != cudaSuccess)
+    return cleanup_fail(cuda_fail(s, e, "cudaMallocHost(sums)"));
+  if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
+    return cleanup_fail(cuda_fail(s, e, "cudaStreamSynchronize"));
+  *out = s;
+  return DIRAC_OK;
+}
+
+extern "C" void dirac_destroy(dirac_sim* s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->stream);
+  cudaFree(s->state);
+  cudaFree(s->staging);
+  cudaFree(s->Vstatic);
+  cudaFree(s->partials);
+  cudaFree(s->sums_dev);
+  if (s->sums_host) cudaFreeHost(s->sums_host);
+  delete s;
+}
+
+extern "C" dirac_status dirac_set_spinor(dirac_sim* s, const double* host) {
+  if (!s || !host) return fail(s, DIRAC_ERR_INVALID, "NULL argument");
+  for (int k = 0; k < s->np; ++k) {
+    const double* src = host + 2LL * k * s->ncell;
+    size_t bytes = (size_t)s->ncell * sizeof(double2);
+    if (s->prec == DIRAC_FP64) {
+      double2* dst = static_cast<double2*>(s->state) + (long long)k * s->pstride;
+      CK(s, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream));
+    } else {
+      float2* dst = static_cast<float2*>(s->state) + (long long)k * s->pstride;
+      CK(s, cudaMemcpyAsync(s->staging, src, bytes, cudaMemcpyHostToDevice, s->stream));
+      launch_convert_in(s->staging, dst, s->ncell, s->stream);
+      s->launches += 1;
+      CK(s, cudaGetLastError());
+    }
+  }
+  return DIRAC_OK;
+}
+
+extern "C" dirac_status dirac_get_spinor(dirac_sim* s, double* host) {
+  if (!s || !host) return fail(s, DIRAC_ERR_INVALID, "NULL argument");
+  for (int k = 0; k < s->np; ++k) {
+    double* dst = host + 2LL * k * s->ncell;
+    size_t bytes = (size_t)s->ncell * sizeof(double2);
+    if (s->prec == DIRAC_FP64) {
+      const double2* src = static_cast<double2*>(s->state) + (long long)k * s->pstride;
+      CK(s, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s->stream));
+    } else {
+      const float2* src = static_cast<float2*>(s->state) + (long long)k * s->pstride;
+      launch_convert_out(src, s->staging, s->ncell, s->stream);
+      s->launches += 1;
+      CK(s, cudaGetLastError());
+      CK(s, cudaMemcpyAsync(dst, s->staging, bytes, cudaMemcpyDeviceToHost, s->stream));
+    }
+  }
+  CK(s, cudaStreamSynchronize(s->stream));
+  return DIRAC_OK;
+}
+
+static double sim_time(const dirac_sim* s) { return s->t0 + (double)s->k * s->dt; }
+
+template <class P>
+static dirac_status step_split(dirac_sim* s, long n) {
+  for (long i = 0; i < n; ++i) {
+    double t = sim_time(s);
+    HalfStepArgs<P> up = half_args<P>(s, true, t);
+    HalfStepArgs<P> lo = half_args<P>(s, false, t + s->dt / 2.0);
+    if (s->dims == 3) {
+      launch_half_step<P, 3>(up, true, s->stream);
+      launch_half_step<P, 3>(lo, false, s->stream);
+    } else {
+      launch_half_step<P, 2>(up, true, s->stream);
+      launch_half_step<P, 2>(lo, false, s->stream);
+    }
+    s->launches += 2;
+    CK(s, cudaGetLastError());
+    s->k += 1;
+  }
+  return DIRAC_OK;
+}
+
+extern "C" dirac_status dirac_step(dirac_sim* s, long nsteps) {
+  if (!s) return fail(s, DIRAC_ERR_INVALID, "NULL sim");
+  if (nsteps < 0) return fail(s, DIRAC_ERR_INVALID, "nsteps < 0");
+  if (s->prec == DIRAC_FP64) return step_split<F64>(s, nsteps);
+  return step_split<F32>(s, nsteps);
+}
+
+template <class P>
+static dirac_status observe(dirac_sim* s, int dens_axis, int dens_X) {
+  ObsArgs<P> a;
+  std::memset(&a, 0, sizeof(a));
+  typename P::cplx* pl[8];
+  plane_ptrs<P>(s, pl);
+  for (int k = 0; k < 8; ++k) a.pl[k] = pl[k];
+  for (int k = 0; k < 3; ++k) a.N[k] = s->N[k];
+  a.pstride = s->pstride;
+  a.link_mode = s->link_mode;
+  for (int k = 0; k < 3; ++k) a.L[k] = make_link<P>(s->f.q * s->f.A_const[k] * s->dx[k] / 2.0);
+  a.f = field_desc(s);
+  a.t_links = sim_time(s) - s->dt / 2.0;
+  a.dens_axis = dens_axis;
+  a.dens_X = dens_X;
+  a.partials = s->partials;
+  if (s->dims == 3) launch_observables<P, 3>(a, s->red_blocks, s->stream);
+  else launch_observables<P, 2>(a, s->red_blocks, s->stream);
+  CK(s, cudaGetLastError());
+  launch_finish_sums(s->partials, s->red_blocks, s->sums_dev, s->stream);
+  s->launches += 2;
+  CK(s, cudaGetLastError());
+  CK(s, cudaMemcpyAsync(s->sums_host, s->sums_dev, kObsSums * sizeof(double), cudaMemcpyDeviceToHost,
+                        s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  return DIRAC_OK;
+}
+
+static dirac_status observe_any(dirac_sim* s, int dens_axis, int dens_X) {
+  return s->prec == DIRAC_FP64 ? observe<F64>(s, dens_axis, dens_X) : observe<F32>(s, dens_axis, dens_X);
+}
+
+extern "C" dirac_status dirac_norm(dirac_sim* s, double* E, double* naive) {
+  if (!s || !E) return fail(s, DIRAC_ERR_INVALID, "NULL argument");
+  dirac_status st = observe_any(s, -1, 0);
+  if (st != DIRAC_OK) return st;
+  const double* v = s->sums_host;
+  double e = v[0];
+  for (int a = 0; a < s->dims; ++a) e += (s->dt / s->dx[a]) * v[1 + a];
+  *E = e;
+  if (naive) *naive = v[0];
+  if (!std::isfinite(e)) return fail(s, DIRAC_ERR_DIVERGED, "conserved functional is not finite");
+  return DIRAC_OK;
+}
+
+extern "C" dirac_status dirac_partial_density(dirac_sim* s, int axis, double x0, double* out) {
+  if (!s || !out) return fail(s, DIRAC_ERR_INVALID, "NULL argument");
+  if (axis < 0 || axis >= s->dims) return fail(s, DIRAC_ERR_INVALID, "axis out of range");
+  dirac_status st = observe_any(s, axis, threshold_index(x0, s->dx[axis]));
+  if (st != DIRAC_OK) return st;
+  *out = s->sums_host[4];
+  return DIRAC_OK;
+}
+
+extern "C" long long dirac_kernel_launches(const dirac_sim* s) { return s ? s->launches : 0; }
+
+extern "C" dirac_status dirac_get_time(const dirac_sim* s, double* t) {
+  if (!s || !t) return DIRAC_ERR_INVALID;
+  *t = sim_time(s);
+  return DIRAC_OK;
+}
+
+extern "C" dirac_status dirac_set_time(dirac_sim* s, double t) {
+  if (!s || !std::isfinite(t)) return fail(s, DIRAC_ERR_INVALID, "bad time");
+  s->t0 = t;
+  s->k = 0;
+  return DIRAC_OK;
+}

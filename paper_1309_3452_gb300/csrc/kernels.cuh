@@ -1,0 +1,56 @@
+// Kernel argument blocks and launcher declarations of libdirac.
+#pragma once
+
+#include "common.cuh"
+
+namespace dirac {
+
+// One half-step (all upper or all lower values) of the scheme.
+template <class P>
+struct HalfStepArgs {
+  typename P::cplx* pl[8];  // plane base pointers (updated in place)
+  int N[3];
+  long long pstride;
+  int iso;                  // r_x = r_y (= r_z)
+  typename P::Ratio ry, rz; // r_y/r_x, r_z/r_x
+  int coef_mode;            // CoefMode
+  typename P::Coef c_in;    // uniform coefficient (or: before the Klein step)
+  typename P::Coef c_out;   // beyond the Klein step
+  int step_axis, step_X;    // Klein step: half-lattice index threshold
+  int link_mode;            // LinkMode
+  typename P::Link L[3];    // constant link factors exp(-i q A_a dx_a/2)
+  FieldDesc f;              // general paths
+  double t;                 // field time of this half-step
+  double beta;              // +1 upper (A,B,u), -1 lower (C,D,v)
+};
+
+template <class P, int DIMS>
+void launch_half_step(const HalfStepArgs<P>& a, bool upper, cudaStream_t s);
+
+// Observables of the stored state: per-block FP64 partial sums of
+// [sum|psi|^2, Bx, By, Bz, sum_{beyond} |psi|^2] with
+// B_a = Re sum_lower conj(G) s_a d_a(G)  (E = naive + r_x Bx + r_y By + r_z Bz).
+template <class P>
+struct ObsArgs {
+  const typename P::cplx* pl[8];
+  int N[3];
+  long long pstride;
+  int link_mode;
+  typename P::Link L[3];
+  FieldDesc f;
+  double t_links;           // time of the upper sheet (t - dt/2)
+  int dens_axis, dens_X;    // partial density: half-lattice index >= dens_X along axis
+  double* partials;         // [gridDim.x][5]
+};
+constexpr int kObsSums = 5;
+
+template <class P, int DIMS>
+void launch_observables(const ObsArgs<P>& a, int blocks, cudaStream_t s);
+// fixed-order sum of partials[nblocks][5] into out[5]
+void launch_finish_sums(const double* partials, int nblocks, double* out, cudaStream_t s);
+
+// canonical complex128 plane <-> device plane of the simulation precision
+void launch_convert_in(const double2* src, float2* dst, long long n, cudaStream_t s);
+void launch_convert_out(const float2* src, double2* dst, long long n, cudaStream_t s);
+
+}  // namespace dirac

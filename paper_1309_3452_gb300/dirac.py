@@ -1,0 +1,200 @@
+"""Python binding of libdirac (include/dirac.h): argument marshalling only.
+
+Every step of the scheme runs in the CUDA library; this module converts
+numpy arrays and workloads.Problem descriptions into the C ABI and raises on
+any non-OK status.  Importing it loads libdirac.so and fails loudly when the
+library has not been built (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libdirac.so not found at {LIB_PATH}; build it with "
+                      "`python -m paper_1309_3452_gb300.build` (no CPU fallback exists)")
+
+_lib = C.CDLL(LIB_PATH)
+
+OK, ERR_INVALID, ERR_UNSTABLE, ERR_OOM, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT, ERR_UNSUPPORTED = range(8)
+FP64, FP32 = 0, 1
+FLAG_ALLOW_UNSTABLE = 0x1
+STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "UNSTABLE", 3: "OOM", 4: "CUDA", 5: "DIVERGED",
+                6: "TIMEOUT", 7: "UNSUPPORTED"}
+
+
+class DiracError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Fields(C.Structure):
+    _fields_ = [
+        ("V0", C.c_double), ("step_axis", C.c_int), ("step_x0", C.c_double), ("step_V", C.c_double),
+        ("sc_Z", C.c_double), ("sc_a", C.c_double), ("sc_center", C.c_double * 3),
+        ("V_static", C.POINTER(C.c_double)), ("Vmod_amp", C.c_double), ("Vmod_omega", C.c_double),
+        ("q", C.c_double), ("A_const", C.c_double * 3), ("Apw_amp", C.c_double),
+        ("Apw_k", C.c_double * 3), ("Apw_omega", C.c_double), ("Apw_phase", C.c_double),
+        ("Apw_pol", C.c_int),
+    ]
+
+
+_vp = C.c_void_p
+_dp = C.POINTER(C.c_double)
+_lib.dirac_create.argtypes = [C.POINTER(_vp), C.c_int, C.POINTER(C.c_int), _dp, C.c_double,
+                              C.c_double, C.POINTER(Fields), C.c_int, C.c_uint, _vp]
+_lib.dirac_set_spinor.argtypes = [_vp, _dp]
+_lib.dirac_get_spinor.argtypes = [_vp, _dp]
+_lib.dirac_step.argtypes = [_vp, C.c_long]
+_lib.dirac_norm.argtypes = [_vp, _dp, _dp]
+_lib.dirac_partial_density.argtypes = [_vp, C.c_int, C.c_double, _dp]
+_lib.dirac_get_time.argtypes = [_vp, _dp]
+_lib.dirac_set_time.argtypes = [_vp, C.c_double]
+_lib.dirac_state_bytes.argtypes = [C.c_int, C.POINTER(C.c_int), C.c_int]
+_lib.dirac_state_bytes.restype = C.c_size_t
+_lib.dirac_last_error.argtypes = [_vp]
+_lib.dirac_last_error.restype = C.c_char_p
+_lib.dirac_destroy.argtypes = [_vp]
+_lib.dirac_fields_default.argtypes = [C.POINTER(Fields)]
+_lib.dirac_version.restype = C.c_int
+_lib.dirac_kernel_launches.argtypes = [_vp]
+_lib.dirac_kernel_launches.restype = C.c_longlong
+
+for _name in ("dirac_create", "dirac_set_spinor", "dirac_get_spinor", "dirac_step", "dirac_norm",
+              "dirac_partial_density", "dirac_get_time", "dirac_set_time"):
+    getattr(_lib, _name).restype = C.c_int
+
+
+def lib():
+    return _lib
+
+
+def _fields_struct(f):
+    s = Fields()
+    _lib.dirac_fields_default(C.byref(s))
+    if f is None:
+        return s, None
+    s.V0 = f.V0
+    s.step_axis, s.step_x0, s.step_V = int(f.step_axis), float(f.step_x0), float(f.step_V)
+    s.sc_Z, s.sc_a = float(f.sc_Z), float(f.sc_a)
+    for a in range(3):
+        s.sc_center[a] = float(f.sc_center[a]) if a < len(f.sc_center) else 0.0
+        s.A_const[a] = float(f.A_const[a]) if a < len(f.A_const) else 0.0
+        s.Apw_k[a] = float(f.Apw_k[a]) if a < len(f.Apw_k) else 0.0
+    keep = None
+    if f.V_static is not None:
+        keep = np.ascontiguousarray(f.V_static, dtype=np.float64)
+        s.V_static = keep.ctypes.data_as(_dp)
+    s.Vmod_amp, s.Vmod_omega = float(f.Vmod_amp), float(f.Vmod_omega)
+    s.q = float(f.q)
+    s.Apw_amp, s.Apw_omega, s.Apw_phase = float(f.Apw_amp), float(f.Apw_omega), float(f.Apw_phase)
+    s.Apw_pol = int(f.Apw_pol)
+    return s, keep
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+def state_bytes(dims, N, precision):
+    n = (C.c_int * 3)(*[int(v) for v in (list(N) + [1, 1, 1])[:3]])
+    return int(_lib.dirac_state_bytes(int(dims), n, int(precision)))
+
+
+class Sim:
+    """One simulation owned by libdirac.  `prob` is a workloads.Problem."""
+
+    def __init__(self, prob, precision=FP64, flags=0, stream=None):
+        self.prob = prob
+        self.precision = precision
+        n = (C.c_int * 3)(*[int(v) for v in (list(prob.N) + [1, 1, 1])[:3]])
+        dx = (C.c_double * 3)(*[float(v) for v in (list(prob.dx) + [1.0, 1.0, 1.0])[:3]])
+        fs, keep = _fields_struct(prob.fields)
+        if keep is not None and keep.size != int(np.prod(prob.shape)):
+            raise ValueError("V_static must have one value per site (canonical layout)")
+        self._h = _vp()
+        st = stream if stream is not None else _current_stream()
+        rc = _lib.dirac_create(C.byref(self._h), int(prob.dims), n, dx, float(prob.dt), float(prob.m),
+                               C.byref(fs), int(precision), int(flags), st)
+        if rc != OK:
+            raise DiracError(rc, _lib.dirac_last_error(None).decode())
+        del keep
+
+    def _check(self, rc):
+        if rc != OK:
+            raise DiracError(rc, _lib.dirac_last_error(self._h).decode())
+
+    def set_spinor(self, psi):
+        a = np.ascontiguousarray(psi, dtype=np.complex128)
+        if a.size != int(np.prod(self.prob.shape)):
+            raise ValueError("state has the wrong number of values")
+        self._check(_lib.dirac_set_spinor(self._h, a.ctypes.data_as(_dp)))
+
+    def set_spinor_ptr(self, host_ptr: int):
+        """Canonical complex128 state at a raw host address (e.g. pinned memory)."""
+        self._check(_lib.dirac_set_spinor(self._h, C.cast(C.c_void_p(host_ptr), _dp)))
+
+    def get_spinor(self):
+        out = np.empty(self.prob.shape, np.complex128)
+        self._check(_lib.dirac_get_spinor(self._h, out.ctypes.data_as(_dp)))
+        return out
+
+    def get_spinor_ptr(self, host_ptr: int):
+        self._check(_lib.dirac_get_spinor(self._h, C.cast(C.c_void_p(host_ptr), _dp)))
+
+    def step(self, n):
+        self._check(_lib.dirac_step(self._h, int(n)))
+
+    def norm(self):
+        E, naive = C.c_double(), C.c_double()
+        self._check(_lib.dirac_norm(self._h, C.byref(E), C.byref(naive)))
+        return E.value, naive.value
+
+    def partial_density(self, axis, x0):
+        out = C.c_double()
+        self._check(_lib.dirac_partial_density(self._h, int(axis), float(x0), C.byref(out)))
+        return out.value
+
+    @property
+    def launches(self):
+        return int(_lib.dirac_kernel_launches(self._h))
+
+    @property
+    def time(self):
+        t = C.c_double()
+        self._check(_lib.dirac_get_time(self._h, C.byref(t)))
+        return t.value
+
+    @time.setter
+    def time(self, t):
+        self._check(_lib.dirac_set_time(self._h, float(t)))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.dirac_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,63 @@
+"""The C-ABI library builds, loads without a GPU and exports every function
+include/dirac.h declares; host-only argument validation works on the CPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_1309_3452_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(dirac_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return C.CDLL(B.build())
+
+
+def test_header_declares_the_api():
+    names = declared_functions()
+    for want in ("dirac_create", "dirac_set_spinor", "dirac_get_spinor", "dirac_step", "dirac_norm",
+                 "dirac_partial_density", "dirac_destroy", "dirac_last_error"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_validation(lib):
+    from paper_1309_3452_gb300 import dirac as D
+
+    assert D.lib().dirac_version() == 1
+    f = D.Fields()
+    D.lib().dirac_fields_default(C.byref(f))
+    assert f.q == 1.0 and f.step_axis == -1 and f.sc_a == 1.0 and f.V0 == 0.0
+    h = C.c_void_p()
+    N = (C.c_int * 3)(8, 8, 8)
+    dx = (C.c_double * 3)(1.0, 1.0, 1.0)
+    L = D.lib()
+    # rejected before any CUDA call
+    assert L.dirac_create(C.byref(h), 4, N, dx, 0.5, 0.0, None, 0, 0, None) == D.ERR_INVALID
+    assert L.dirac_create(C.byref(h), 3, N, dx, 0.6, 0.0, None, 0, 0, None) == D.ERR_UNSTABLE
+    assert b"stability" in L.dirac_last_error(None)
+    bad = (C.c_int * 3)(1, 8, 8)
+    assert L.dirac_create(C.byref(h), 3, bad, dx, 0.5, 0.0, None, 0, 0, None) == D.ERR_INVALID
+    assert L.dirac_create(C.byref(h), 2, N, dx, -0.1, 0.0, None, 0, 0, None) == D.ERR_INVALID
+    assert not h.value
+    # device bytes: 8 planes x 8^3 cells x complex128
+    assert D.state_bytes(3, (8, 8, 8), D.FP64) == 8 * 512 * 16
+    assert D.state_bytes(2, (10, 10), D.FP32) == 4 * 128 * 8 + 128 * 16

@@ -1,0 +1,198 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs, element by element.
+
+Tolerances (relative L2 over the whole state, and E):
+  FP64: 1e-12 (rounding-order differences only);
+  FP32: 1e-5 rel L2 and 1e-6 relative drift of E (compensated coefficients).
+Sizes span several thread blocks and ragged tails (N not a multiple of any
+tile), both dimensions, all field paths.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1309_3452_gb300 import workloads as W
+from tests import closed_forms as CF
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 1e-5
+FP32_EDRIFT = 1e-6
+
+
+@pytest.fixture(scope="module")
+def D():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1309_3452_gb300 import dirac
+    return dirac
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run_gpu(D, prob, psi, n, precision, t0=0.0, chunks=1):
+    with D.Sim(prob, precision) as s:
+        s.time = t0
+        s.set_spinor(psi)
+        E0, _ = s.norm()
+        for c in range(chunks):
+            s.step(n // chunks + (1 if c < n % chunks else 0))
+        E1, naive = s.norm()
+        out = s.get_spinor()
+        t = s.time
+    return out, E0, E1, naive, t
+
+
+def field_cases(dims, N):
+    c = [n / 2.0 for n in N]
+    L = [float(n) for n in N]
+    cases = {
+        "free": W.Fields(),
+        "V0": W.Fields(V0=0.37),
+        "klein": W.Fields(V0=0.05, step_axis=0, step_x0=N[0] / 2 + 0.25, step_V=0.8),
+        "klein_y": W.Fields(step_axis=1, step_x0=N[1] / 3 + 0.25, step_V=-0.6),
+        "softcore": W.Fields(sc_Z=1.0, sc_a=1.0, sc_center=tuple(c)),
+        "A_const": W.Fields(q=0.8, A_const=(0.3, -0.45, 0.2)),
+        "A_wave": W.Fields(q=1.0, Apw_amp=0.5, Apw_k=(0, 0, 2 * math.pi / L[dims - 1]) if dims == 3
+                           else (0, 2 * math.pi / L[1], 0), Apw_omega=0.3, Apw_pol=0),
+        "A_wave_long": W.Fields(q=1.0, Apw_amp=0.4, Apw_k=(2 * math.pi / L[0], 0, 0),
+                                Apw_omega=0.0, Apw_pol=0, Apw_phase=0.3),
+    }
+    return cases
+
+
+@pytest.mark.parametrize("dims,N", [(2, (37, 29)), (3, (13, 11, 9))])
+@pytest.mark.parametrize("case", ["free", "V0", "klein", "klein_y", "softcore", "A_const", "A_wave",
+                                  "A_wave_long", "Vstatic_mod"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_parity_fields(D, dims, N, case, precision):
+    full = tuple(N) + ((1,) if dims == 2 else ())
+    prob = W.Problem(dims, full, (1.0, 1.0, 1.0), 0.9 * W.stability_limit(dims), 0.45)
+    if case == "Vstatic_mod":
+        f = W.Fields(V_static=W.random_potential(prob, 4, 0.6), Vmod_amp=0.5, Vmod_omega=0.7)
+    else:
+        f = field_cases(dims, N)[case]
+    prob = W.Problem(prob.dims, prob.N, prob.dx, prob.dt, prob.m, f)
+    psi = W.random_state(prob, 17)
+    n = 60
+    t0 = 0.25
+    ref = O.step(prob, psi, n, t0)
+    ob0 = O.observables(prob, psi, t0)
+    ob1 = O.observables(prob, ref, t0 + n * prob.dt)
+    prec = D.FP64 if precision == "fp64" else D.FP32
+    out, E0, E1, naive, t = run_gpu(D, prob, psi, n, prec, t0, chunks=3)
+    assert abs(t - (t0 + n * prob.dt)) < 1e-12
+    tol = FP64_TOL if precision == "fp64" else FP32_TOL
+    assert rel(out, ref) < tol
+    if precision == "fp64":
+        assert abs(E0 - ob0["E"]) < 1e-13 * abs(ob0["E"])
+        assert abs(E1 - ob1["E"]) < 1e-12 * abs(ob1["E"])
+        assert abs(naive - ob1["naive"]) < 1e-12 * ob1["naive"]
+    else:
+        assert abs(E1 - ob1["E"]) < 1e-5 * abs(ob1["E"])
+        if case != "A_wave":  # time-dependent A: E is not conserved
+            assert abs(E1 - E0) < FP32_EDRIFT * abs(E0)
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_anisotropic_grid(D, dims, precision):
+    if dims == 2:
+        prob = W.Problem(2, (21, 18, 1), (1.0, 1.3, 1.0), 0.5, 0.3, W.Fields(V0=0.1))
+    else:
+        prob = W.Problem(3, (10, 12, 7), (1.0, 1.2, 0.9), 0.45, 0.3, W.Fields(V0=0.1))
+    psi = W.random_state(prob, 3)
+    ref = O.step(prob, psi, 40)
+    out, E0, E1, _, _ = run_gpu(D, prob, psi, 40, D.FP64 if precision == "fp64" else D.FP32)
+    assert rel(out, ref) < (FP64_TOL if precision == "fp64" else FP32_TOL)
+    assert abs(E1 - E0) < (1e-13 if precision == "fp64" else FP32_EDRIFT) * abs(E0)
+
+
+@pytest.mark.parametrize("m", [0.0, 0.5])
+def test_workload_2d64_fp64(D, m):
+    """(2+1)D 64^2 packet, 200 steps, FP64: parity with the oracle and
+    conservation of E."""
+    prob, psi, n = W.workload_2d64(m)
+    ref = O.step(prob, psi, n)
+    out, E0, E1, _, _ = run_gpu(D, prob, psi, n, D.FP64)
+    assert rel(out, ref) < FP64_TOL
+    assert abs(E1 - E0) < 1e-13 * E0
+
+
+@pytest.mark.parametrize("dims,modes,m", [(2, (5, 3), 0.5), (3, (2, -1, 3), 1.0)])
+def test_plane_wave_closed_form(D, dims, modes, m):
+    """Eq. pwdsip on the GPU: a lattice plane wave advances by exp(-i w n dt)."""
+    if dims == 2:
+        prob = W.Problem(2, (64, 64, 1), (1.0, 1.0, 1.0), 0.9 * W.stability_limit(2), m)
+        n = 200
+    else:
+        prob = W.Problem(3, (16, 12, 20), (1.0, 1.0, 1.0), 0.9 * W.stability_limit(3), m)
+        n = 100
+    psi, w = CF.plane_wave_state(prob, modes)
+    out, _, _, _, _ = run_gpu(D, prob, psi, n, D.FP64)
+    assert rel(out, psi * np.exp(-1j * w * n * prob.dt)) < 1e-12
+    out32, _, _, _, _ = run_gpu(D, prob, psi, n, D.FP32)
+    assert rel(out32, psi * np.exp(-1j * w * n * prob.dt)) < FP32_TOL
+
+
+def test_observables_match_oracle(D):
+    prob = W.Problem(3, (9, 10, 11), (1.0, 1.0, 1.0), 0.5, 0.2,
+                     W.Fields(q=0.9, A_const=(0.2, 0.1, -0.3)))
+    psi = W.random_state(prob, 8)
+    with D.Sim(prob, D.FP64) as s:
+        s.set_spinor(psi)
+        E, naive = s.norm()
+        pd = s.partial_density(1, 4.6)
+        back = s.get_spinor()
+    ob = O.observables(prob, psi, 0.0)
+    assert np.array_equal(back, psi)
+    assert abs(E - ob["E"]) < 1e-14 * abs(ob["E"])
+    assert abs(naive - ob["naive"]) < 1e-14
+    assert abs(pd - O.partial_density(prob, psi, 1, 4.6)) < 1e-14
+
+
+def test_fp32_roundtrip_is_float_rounding(D):
+    prob = W.Problem(2, (33, 17, 1), (1.0, 1.0, 1.0), 0.5, 0.0)
+    psi = W.random_state(prob, 2)
+    with D.Sim(prob, D.FP32) as s:
+        s.set_spinor(psi)
+        back = s.get_spinor()
+    want = psi.real.astype(np.float32).astype(np.float64) + 1j * psi.imag.astype(np.float32)
+    assert np.array_equal(back, want)
+
+
+def test_light_cone_on_gpu(D):
+    """Nearest-neighbour stencil: exact zeros outside the light cone (catches
+    wrong neighbour offsets and wrap-around mistakes at block edges)."""
+    prob = W.Problem(3, (40, 36, 20), (1.0, 1.0, 1.0), 0.5, 0.5)
+    for plane, cell in ((0, (0, 0, 0)), (5, (39, 35, 19)), (7, (17, 20, 10))):
+        psi = W.delta_state(prob, plane, cell)
+        n = 3
+        out, _, _, _, _ = run_gpu(D, prob, psi, n, D.FP64)
+        ref = O.step(prob, psi, n)
+        assert rel(out, ref) < FP64_TOL
+        assert np.array_equal(out == 0, ref == 0)
+
+
+def test_unstable_is_rejected_and_diverges_when_forced(D):
+    prob = W.Problem(2, (8, 8, 1), (1.0, 1.0, 1.0), 1.2 * W.stability_limit(2), 0.3)
+    with pytest.raises(D.DiracError) as e:
+        D.Sim(prob, D.FP64)
+    assert e.value.status == D.ERR_UNSTABLE
+    psi = W.random_state(prob, 1)
+    with D.Sim(prob, D.FP64, flags=D.FLAG_ALLOW_UNSTABLE) as s:
+        s.set_spinor(psi)
+        E0, _ = s.norm()
+        s.step(4000)
+        try:
+            E1, naive = s.norm()
+            grew = not math.isfinite(naive) or naive > 1e6
+        except D.DiracError as err:
+            grew = err.status == D.ERR_DIVERGED
+    assert grew
