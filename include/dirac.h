@@ -76,7 +76,10 @@ typedef enum {
 } dirac_precision;
 
 /* flags for dirac_create */
-#define DIRAC_FLAG_ALLOW_UNSTABLE 0x1u /* accept r beyond the stability bound */
+#define DIRAC_FLAG_ALLOW_UNSTABLE 0x1u   /* accept r beyond the stability bound */
+#define DIRAC_FLAG_REFERENCE_KERNELS 0x2u /* FP32: use the plain one-kernel-per-half-step
+                                             path instead of the fused time-step kernel
+                                             (same per-value arithmetic, same results) */
 
 /*
  * External fields (Sect. 2: V in Eq. 3+3D; Sect. 4: vector potential).
@@ -164,7 +167,9 @@ dirac_status dirac_set_time(dirac_sim* sim, double t);
    (every launch of every call counts once) */
 long long dirac_kernel_launches(const dirac_sim* sim);
 
-/* device bytes a simulation of this shape and precision allocates */
+/* device bytes a simulation of this shape and precision allocates (without
+   the optional static potential): the state, plus for DIRAC_FP32 a second
+   state buffer and one complex128 conversion plane */
 size_t dirac_state_bytes(int dims, const int N[3], dirac_precision precision);
 
 /* human-readable description of the last failure on sim (or of the last

@@ -226,7 +226,8 @@ __device__ __forceinline__ double potential_at(const FieldDesc& f, int dims, lon
                                                int plane, double t) {
   double V = f.V0;
   long long H[3] = {X, Y, Z};
-  if (f.step_axis >= 0 && H[f.step_axis] >= f.step_X) V += f.step_V;
+  const long long hs = f.step_axis == 0 ? X : (f.step_axis == 1 ? Y : Z);
+  if (f.step_axis >= 0 && hs >= f.step_X) V += f.step_V;
   if (f.sc_Z != 0.0) {
     double r2 = 0.0;
     for (int a = 0; a < dims; ++a) {
@@ -254,6 +255,97 @@ __device__ __forceinline__ double link_phase(const FieldDesc& f, int dims, const
     A += f.Apw_amp * cos(ph);
   }
   return f.q * A * f.dx[axis] * 0.5;
+}
+
+// ------------------------------------------------------------------ site update
+// FP64 -> coefficient / link of the working precision
+__device__ __forceinline__ F64::Coef coef_from(const double2& a, const double2& g, F64*) {
+  return F64::Coef{a, g};
+}
+__device__ __forceinline__ float2 hi2(double2 v) {
+  return make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+}
+__device__ __forceinline__ float2 lo2(double2 v, float2 h) {
+  return make_float2(__double2float_rn(v.x - (double)h.x), __double2float_rn(v.y - (double)h.y));
+}
+__device__ __forceinline__ F32::Coef coef_from(const double2& a, const double2& g, F32*) {
+  F32::Coef c;
+  c.a_hi = hi2(a);
+  c.a_lo = lo2(a, c.a_hi);
+  c.g_hi = hi2(g);
+  c.g_lo = lo2(g, c.g_hi);
+  return c;
+}
+__device__ __forceinline__ F64::Link link_from(double phi, F64*) {
+  double s, c;
+  sincos(phi, &s, &c);
+  return F64::Link{make_double2(c, -s)};  // exp(-i phi)
+}
+__device__ __forceinline__ F32::Link link_from(double phi, F32*) {
+  double s, c;
+  sincos(phi, &s, &c);
+  double2 u = make_double2(c, -s);
+  F32::Link L;
+  L.hi = hi2(u);
+  L.lo = lo2(u, L.hi);
+  return L;
+}
+
+// Field parameters of one half-step, shared by every kernel variant.
+template <class P>
+struct HalfFields {
+  int coef_mode;            // CoefMode
+  typename P::Coef c_in;    // uniform coefficient (or: before the Klein step)
+  typename P::Coef c_out;   // beyond the Klein step
+  int step_axis, step_X;    // Klein step: half-lattice index threshold
+  int link_mode;            // LinkMode
+  typename P::Link L[3];    // constant link factors exp(-i q A_a dx_a/2)
+  double t;                 // field time of this half-step
+  double beta;              // +1 upper (A,B,u), -1 lower (C,D,v)
+};
+
+// One value of the scheme (Eqs. ss1-ss4 / scheme2Deq ff.):
+//   F+ = ((1 - i th) F - S) / (1 + i th)  as  alpha F - gamma S'.
+// nb = neighbours {x+, x-, y+, y-, z+, z-} (z ignored in (2+1)D) at
+// +-dx_a/2; H = half-lattice coordinates of the value; site = cell index
+// inside its plane (for a static potential).  GENERAL selects the per-site
+// FP64 field paths (any potential, plane-wave links); otherwise only the
+// uniform / Klein-step coefficients and constant links are compiled in.
+template <class P, int DIMS, bool GENERAL>
+__device__ __forceinline__ typename P::cplx site_update(
+    const HalfFields<P>& h, const FieldDesc& f, bool iso, const typename P::Ratio& ry,
+    const typename P::Ratio& rz, int plane, typename P::cplx F, typename P::cplx (&nb)[6],
+    const int (&H)[3], long long site, long long pstride) {
+  using C = typename P::cplx;
+  C d[3];
+#pragma unroll
+  for (int ax = 0; ax < DIMS; ++ax) {
+    C up = nb[2 * ax], dn = nb[2 * ax + 1];
+    if (h.link_mode == LINK_CONST) {
+      up = link_mul(h.L[ax], up);
+      dn = link_mulc(h.L[ax], dn);
+    } else if (GENERAL && h.link_mode == LINK_GENERAL) {
+      long long HH[3] = {H[0], H[1], H[2]};
+      up = link_mul(link_from(link_phase(f, DIMS, HH, ax, +1, h.t), (P*)nullptr), up);
+      // exp(+i phi-) = conj(exp(-i phi-))
+      dn = link_mulc(link_from(link_phase(f, DIMS, HH, ax, -1, h.t), (P*)nullptr), dn);
+    }
+    d[ax] = csub(up, dn);
+  }
+  if (DIMS == 2) d[2] = d[0];
+  const C S = combine<P, DIMS>(d[0], d[1], d[2], sign_class<DIMS>(plane), iso, ry, rz);
+  typename P::Coef c = h.c_in;
+  if (h.coef_mode == COEF_STEP) {
+    const int hs = h.step_axis == 0 ? H[0] : (h.step_axis == 1 ? H[1] : H[2]);
+    if (hs >= h.step_X) c = h.c_out;
+  } else if (GENERAL && h.coef_mode == COEF_GENERAL) {
+    double V = potential_at(f, DIMS, H[0], H[1], H[2], site, pstride, plane, h.t);
+    double th = f.dt * (h.beta * f.m + V) * 0.5;
+    double2 al, ga;
+    coef_from_theta(th, f.rx, al, ga);
+    c = coef_from(al, ga, (P*)nullptr);
+  }
+  return apply(c, F, S);
 }
 
 }  // namespace dirac

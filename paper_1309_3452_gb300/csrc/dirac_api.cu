@@ -1,8 +1,10 @@
 // Host side of libdirac: the C ABI declared in include/dirac.h.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <string>
 
 #include "../../include/dirac.h"
@@ -22,7 +24,10 @@ struct dirac_sim {
   long long ncell = 0, pstride = 0;
   int np = 0;
   size_t elem = 0;            // bytes per complex value
-  void* state = nullptr;      // np * pstride values
+  void* state = nullptr;      // np * pstride values: the current state
+  void* state_alt = nullptr;  // second buffer for the out-of-place fused kernels
+  int fused = 0;              // one kernel per time step (FP32 without the reference flag)
+  int chunk = 16;             // fused kernels: march levels per block
   double2* staging = nullptr; // one canonical plane (FP32 conversions)
   double* Vstatic = nullptr;  // one real per site (plane-major, pstride)
   double* partials = nullptr;
@@ -66,7 +71,8 @@ extern "C" size_t dirac_state_bytes(int dims, const int N[3], dirac_precision p)
   long long ps = round_up(nc, 64);
   size_t elem = p == DIRAC_FP32 ? sizeof(float2) : sizeof(double2);
   size_t bytes = (size_t)(dims == 3 ? 8 : 4) * ps * elem;
-  if (p == DIRAC_FP32) bytes += (size_t)ps * sizeof(double2);  // conversion staging
+  // FP32: a second state buffer (out-of-place fused step) and a conversion staging plane
+  if (p == DIRAC_FP32) bytes = 2 * bytes + (size_t)ps * sizeof(double2);
   return bytes;
 }
 
@@ -168,6 +174,28 @@ static void plane_ptrs(dirac_sim* s, typename P::cplx* (&pl)[8]) {
 }
 
 template <class P>
+static HalfFields<P> half_fields(const dirac_sim* s, bool upper, double t) {
+  HalfFields<P> h;
+  std::memset(&h, 0, sizeof(h));
+  double rx = s->dt / s->dx[0];
+  double beta = upper ? 1.0 : -1.0;
+  h.coef_mode = s->coef_mode;
+  h.c_in = make_coef<P>(s->dt * (beta * s->m + s->f.V0) / 2.0, rx);
+  h.c_out = make_coef<P>(s->dt * (beta * s->m + (s->f.V0 + s->f.step_V)) / 2.0, rx);
+  h.step_axis = s->f.step_axis < 0 ? 0 : s->f.step_axis;
+  h.step_X = s->step_X;
+  h.link_mode = s->link_mode;
+  for (int k = 0; k < 3; ++k) h.L[k] = make_link<P>(s->f.q * s->f.A_const[k] * s->dx[k] / 2.0);
+  h.t = t;
+  h.beta = beta;
+  return h;
+}
+
+static bool general_fields(const dirac_sim* s) {
+  return s->coef_mode == COEF_GENERAL || s->link_mode == LINK_GENERAL;
+}
+
+template <class P>
 static HalfStepArgs<P> half_args(dirac_sim* s, bool upper, double t) {
   HalfStepArgs<P> a;
   std::memset(&a, 0, sizeof(a));
@@ -178,18 +206,55 @@ static HalfStepArgs<P> half_args(dirac_sim* s, bool upper, double t) {
   double rx = s->dt / s->dx[0];
   a.ry = make_ratio<P>((s->dt / s->dx[1]) / rx);
   a.rz = make_ratio<P>((s->dt / s->dx[2]) / rx);
-  a.coef_mode = s->coef_mode;
-  double beta = upper ? 1.0 : -1.0;
-  a.c_in = make_coef<P>(s->dt * (beta * s->m + s->f.V0) / 2.0, rx);
-  a.c_out = make_coef<P>(s->dt * (beta * s->m + (s->f.V0 + s->f.step_V)) / 2.0, rx);
-  a.step_axis = s->f.step_axis;
-  a.step_X = s->step_X;
-  a.link_mode = s->link_mode;
-  for (int k = 0; k < 3; ++k) a.L[k] = make_link<P>(s->f.q * s->f.A_const[k] * s->dx[k] / 2.0);
+  a.h = half_fields<P>(s, upper, t);
   a.f = field_desc(s);
-  a.t = t;
-  a.beta = beta;
+  a.general = general_fields(s);
   return a;
+}
+
+template <class P>
+static FusedArgs<P> fused_args(dirac_sim* s, double t) {
+  FusedArgs<P> a;
+  std::memset(&a, 0, sizeof(a));
+  typename P::cplx* in[8];
+  plane_ptrs<P>(s, in);
+  auto* alt = static_cast<typename P::cplx*>(s->state_alt);
+  for (int k = 0; k < 8; ++k) {
+    a.in[k] = in[k];
+    a.out[k] = k < s->np ? alt + (long long)k * s->pstride : nullptr;
+  }
+  for (int k = 0; k < 3; ++k) a.N[k] = s->N[k];
+  a.chunk = s->chunk;
+  a.pstride = s->pstride;
+  a.iso = s->iso;
+  double rx = s->dt / s->dx[0];
+  a.ry = make_ratio<P>((s->dt / s->dx[1]) / rx);
+  a.rz = make_ratio<P>((s->dt / s->dx[2]) / rx);
+  a.hu = half_fields<P>(s, true, t);
+  a.hl = half_fields<P>(s, false, t + s->dt / 2.0);
+  a.f = field_desc(s);
+  a.general = general_fields(s);
+  return a;
+}
+
+// Levels per block of the fused kernels: enough blocks to give every SM
+// several, without making the one-level restart of each chunk costly.
+static int pick_chunk(const dirac_sim* s) {
+  const char* env = std::getenv("DIRAC_FUSED_CHUNK");
+  if (env && std::atoi(env) > 0) return std::atoi(env);
+  int n_march = s->dims == 3 ? s->N[2] : s->N[1];
+  long long tiles;
+  if (s->dims == 3)
+    tiles = (long long)((s->N[0] + kCore - 1) / kCore) * ((s->N[1] + kFused3dRows - 3) / (kFused3dRows - 2));
+  else
+    tiles = ((s->N[0] + kCore - 1) / kCore + kFused2dWarps - 1) / kFused2dWarps;
+  const long long want_blocks = s->dims == 3 ? 152LL * 4 : 152LL * 8;
+  long long chunks = (want_blocks + tiles - 1) / tiles;
+  int c = (int)((n_march + chunks - 1) / (chunks > 0 ? chunks : 1));
+  int lo = s->dims == 3 ? 8 : 32;
+  if (c < lo) c = lo;
+  if (c > n_march) c = n_march;
+  return c < 1 ? 1 : c;
 }
 
 extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], const double dx[3],
@@ -258,6 +323,12 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
     if ((e = cudaMalloc(&s->staging, (size_t)s->pstride * sizeof(double2))) != cudaSuccess)
       return cleanup_fail(cuda_fail(s, e, "cudaMalloc(staging)"));
   }
+  s->fused = precision == DIRAC_FP32 && !(flags & DIRAC_FLAG_REFERENCE_KERNELS);
+  if (s->fused) {
+    if ((e = cudaMalloc(&s->state_alt, sbytes)) != cudaSuccess)
+      return cleanup_fail(cuda_fail(s, e, "cudaMalloc(state_alt)"));
+    s->chunk = pick_chunk(s);
+  }
   if (fields && fields->V_static) {
     size_t vb = (size_t)s->np * s->pstride * sizeof(double);
     if ((e = cudaMalloc(&s->Vstatic, vb)) != cudaSuccess) return cleanup_fail(cuda_fail(s, e, "cudaMalloc(V)"));
@@ -285,6 +356,7 @@ extern "C" void dirac_destroy(dirac_sim* s) {
   if (!s) return;
   cudaStreamSynchronize(s->stream);
   cudaFree(s->state);
+  cudaFree(s->state_alt);
   cudaFree(s->staging);
   cudaFree(s->Vstatic);
   cudaFree(s->partials);
@@ -354,10 +426,25 @@ static dirac_status step_split(dirac_sim* s, long n) {
   return DIRAC_OK;
 }
 
+template <class P>
+static dirac_status step_fused(dirac_sim* s, long n) {
+  for (long i = 0; i < n; ++i) {
+    FusedArgs<P> a = fused_args<P>(s, sim_time(s));
+    if (s->dims == 3) launch_fused<P, 3>(a, s->stream);
+    else launch_fused<P, 2>(a, s->stream);
+    s->launches += 1;
+    CK(s, cudaGetLastError());
+    std::swap(s->state, s->state_alt);
+    s->k += 1;
+  }
+  return DIRAC_OK;
+}
+
 extern "C" dirac_status dirac_step(dirac_sim* s, long nsteps) {
   if (!s) return fail(s, DIRAC_ERR_INVALID, "NULL sim");
   if (nsteps < 0) return fail(s, DIRAC_ERR_INVALID, "nsteps < 0");
   if (s->prec == DIRAC_FP64) return step_split<F64>(s, nsteps);
+  if (s->fused) return step_fused<F32>(s, nsteps);
   return step_split<F32>(s, nsteps);
 }
 

@@ -5,7 +5,7 @@
 
 namespace dirac {
 
-// One half-step (all upper or all lower values) of the scheme.
+// One half-step (all upper or all lower values) of the scheme, one kernel.
 template <class P>
 struct HalfStepArgs {
   typename P::cplx* pl[8];  // plane base pointers (updated in place)
@@ -13,19 +13,35 @@ struct HalfStepArgs {
   long long pstride;
   int iso;                  // r_x = r_y (= r_z)
   typename P::Ratio ry, rz; // r_y/r_x, r_z/r_x
-  int coef_mode;            // CoefMode
-  typename P::Coef c_in;    // uniform coefficient (or: before the Klein step)
-  typename P::Coef c_out;   // beyond the Klein step
-  int step_axis, step_X;    // Klein step: half-lattice index threshold
-  int link_mode;            // LinkMode
-  typename P::Link L[3];    // constant link factors exp(-i q A_a dx_a/2)
-  FieldDesc f;              // general paths
-  double t;                 // field time of this half-step
-  double beta;              // +1 upper (A,B,u), -1 lower (C,D,v)
+  HalfFields<P> h;
+  FieldDesc f;
+  int general;              // per-site FP64 field paths needed
 };
 
 template <class P, int DIMS>
 void launch_half_step(const HalfStepArgs<P>& a, bool upper, cudaStream_t s);
+
+// One full time step (both half-steps) in one kernel, out of place.
+template <class P>
+struct FusedArgs {
+  const typename P::cplx* in[8];
+  typename P::cplx* out[8];
+  int N[3];
+  int chunk;                // march levels (z in (3+1)D, y in (2+1)D) per thread block
+  long long pstride;
+  int iso;
+  typename P::Ratio ry, rz;
+  HalfFields<P> hu, hl;     // upper / lower half-step fields
+  FieldDesc f;
+  int general;
+};
+// tile geometry of the fused kernels
+constexpr int kFused3dRows = 16;   // warps per block (y rows incl. 2 halo rows)
+constexpr int kFused2dWarps = 8;   // independent x strips per block
+constexpr int kCore = 30;          // interior lanes of a 32-lane strip
+
+template <class P, int DIMS>
+void launch_fused(const FusedArgs<P>& a, cudaStream_t s);
 
 // Observables of the stored state: per-block FP64 partial sums of
 // [sum|psi|^2, Bx, By, Bz, sum_{beyond} |psi|^2] with

@@ -25,6 +25,7 @@ _lib = C.CDLL(LIB_PATH)
 OK, ERR_INVALID, ERR_UNSTABLE, ERR_OOM, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT, ERR_UNSUPPORTED = range(8)
 FP64, FP32 = 0, 1
 FLAG_ALLOW_UNSTABLE = 0x1
+FLAG_REFERENCE_KERNELS = 0x2
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "UNSTABLE", 3: "OOM", 4: "CUDA", 5: "DIVERGED",
                 6: "TIMEOUT", 7: "UNSUPPORTED"}
 

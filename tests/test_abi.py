@@ -60,4 +60,4 @@ def test_host_only_validation(lib):
     assert not h.value
     # device bytes: 8 planes x 8^3 cells x complex128
     assert D.state_bytes(3, (8, 8, 8), D.FP64) == 8 * 512 * 16
-    assert D.state_bytes(2, (10, 10), D.FP32) == 4 * 128 * 8 + 128 * 16
+    assert D.state_bytes(2, (10, 10), D.FP32) == 2 * 4 * 128 * 8 + 128 * 16
