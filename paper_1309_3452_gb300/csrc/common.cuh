@@ -304,27 +304,33 @@ struct HalfFields {
   double beta;              // +1 upper (A,B,u), -1 lower (C,D,v)
 };
 
+// Field-path selectors for site_update: a fixed CoefMode / LinkMode compiles
+// only that path; kAnyMode reads h.coef_mode / h.link_mode at run time and
+// includes the per-site FP64 (general) paths.
+constexpr int kAnyMode = -1;
+
 // One value of the scheme (Eqs. ss1-ss4 / scheme2Deq ff.):
 //   F+ = ((1 - i th) F - S) / (1 + i th)  as  alpha F - gamma S'.
 // nb = neighbours {x+, x-, y+, y-, z+, z-} (z ignored in (2+1)D) at
 // +-dx_a/2; H = half-lattice coordinates of the value; site = cell index
-// inside its plane (for a static potential).  GENERAL selects the per-site
-// FP64 field paths (any potential, plane-wave links); otherwise only the
-// uniform / Klein-step coefficients and constant links are compiled in.
-template <class P, int DIMS, bool GENERAL>
+// inside its plane (for a static potential).  Every kernel computes every
+// value through this function, so all kernel variants agree bit for bit.
+template <class P, int DIMS, int COEF, int LINK>
 __device__ __forceinline__ typename P::cplx site_update(
     const HalfFields<P>& h, const FieldDesc& f, bool iso, const typename P::Ratio& ry,
     const typename P::Ratio& rz, int plane, typename P::cplx F, typename P::cplx (&nb)[6],
     const int (&H)[3], long long site, long long pstride) {
   using C = typename P::cplx;
+  const int link = LINK == kAnyMode ? h.link_mode : LINK;
+  const int coef = COEF == kAnyMode ? h.coef_mode : COEF;
   C d[3];
 #pragma unroll
   for (int ax = 0; ax < DIMS; ++ax) {
     C up = nb[2 * ax], dn = nb[2 * ax + 1];
-    if (h.link_mode == LINK_CONST) {
+    if (link == LINK_CONST) {
       up = link_mul(h.L[ax], up);
       dn = link_mulc(h.L[ax], dn);
-    } else if (GENERAL && h.link_mode == LINK_GENERAL) {
+    } else if (LINK == kAnyMode && link == LINK_GENERAL) {
       long long HH[3] = {H[0], H[1], H[2]};
       up = link_mul(link_from(link_phase(f, DIMS, HH, ax, +1, h.t), (P*)nullptr), up);
       // exp(+i phi-) = conj(exp(-i phi-))
@@ -334,18 +340,16 @@ __device__ __forceinline__ typename P::cplx site_update(
   }
   if (DIMS == 2) d[2] = d[0];
   const C S = combine<P, DIMS>(d[0], d[1], d[2], sign_class<DIMS>(plane), iso, ry, rz);
-  typename P::Coef c = h.c_in;
-  if (h.coef_mode == COEF_STEP) {
+  if (coef == COEF_UNIFORM) return apply(h.c_in, F, S);
+  if (coef == COEF_STEP) {
     const int hs = h.step_axis == 0 ? H[0] : (h.step_axis == 1 ? H[1] : H[2]);
-    if (hs >= h.step_X) c = h.c_out;
-  } else if (GENERAL && h.coef_mode == COEF_GENERAL) {
-    double V = potential_at(f, DIMS, H[0], H[1], H[2], site, pstride, plane, h.t);
-    double th = f.dt * (h.beta * f.m + V) * 0.5;
-    double2 al, ga;
-    coef_from_theta(th, f.rx, al, ga);
-    c = coef_from(al, ga, (P*)nullptr);
+    return hs >= h.step_X ? apply(h.c_out, F, S) : apply(h.c_in, F, S);
   }
-  return apply(c, F, S);
+  double V = potential_at(f, DIMS, H[0], H[1], H[2], site, pstride, plane, h.t);
+  double th = f.dt * (h.beta * f.m + V) * 0.5;
+  double2 al, ga;
+  coef_from_theta(th, f.rx, al, ga);
+  return apply(coef_from(al, ga, (P*)nullptr), F, S);
 }
 
 }  // namespace dirac

@@ -27,7 +27,6 @@ struct dirac_sim {
   void* state = nullptr;      // np * pstride values: the current state
   void* state_alt = nullptr;  // second buffer for the out-of-place fused kernels
   int fused = 0;              // one kernel per time step (FP32 without the reference flag)
-  int chunk = 16;             // fused kernels: march levels per block
   double2* staging = nullptr; // one canonical plane (FP32 conversions)
   double* Vstatic = nullptr;  // one real per site (plane-major, pstride)
   double* partials = nullptr;
@@ -224,7 +223,6 @@ static FusedArgs<P> fused_args(dirac_sim* s, double t) {
     a.out[k] = k < s->np ? alt + (long long)k * s->pstride : nullptr;
   }
   for (int k = 0; k < 3; ++k) a.N[k] = s->N[k];
-  a.chunk = s->chunk;
   a.pstride = s->pstride;
   a.iso = s->iso;
   double rx = s->dt / s->dx[0];
@@ -233,28 +231,7 @@ static FusedArgs<P> fused_args(dirac_sim* s, double t) {
   a.hu = half_fields<P>(s, true, t);
   a.hl = half_fields<P>(s, false, t + s->dt / 2.0);
   a.f = field_desc(s);
-  a.general = general_fields(s);
   return a;
-}
-
-// Levels per block of the fused kernels: enough blocks to give every SM
-// several, without making the one-level restart of each chunk costly.
-static int pick_chunk(const dirac_sim* s) {
-  const char* env = std::getenv("DIRAC_FUSED_CHUNK");
-  if (env && std::atoi(env) > 0) return std::atoi(env);
-  int n_march = s->dims == 3 ? s->N[2] : s->N[1];
-  long long tiles;
-  if (s->dims == 3)
-    tiles = (long long)((s->N[0] + kCore - 1) / kCore) * ((s->N[1] + kFused3dRows - 3) / (kFused3dRows - 2));
-  else
-    tiles = ((s->N[0] + kCore - 1) / kCore + kFused2dWarps - 1) / kFused2dWarps;
-  const long long want_blocks = s->dims == 3 ? 152LL * 4 : 152LL * 8;
-  long long chunks = (want_blocks + tiles - 1) / tiles;
-  int c = (int)((n_march + chunks - 1) / (chunks > 0 ? chunks : 1));
-  int lo = s->dims == 3 ? 8 : 32;
-  if (c < lo) c = lo;
-  if (c > n_march) c = n_march;
-  return c < 1 ? 1 : c;
 }
 
 extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], const double dx[3],
@@ -278,6 +255,8 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
   if (r2 > 1.0 && !(flags & DIRAC_FLAG_ALLOW_UNSTABLE))
     return fail(nullptr, DIRAC_ERR_UNSTABLE,
                 "sum_a (dt/dx_a)^2 > 1: beyond the stability bound of the scheme");
+  if ((long long)N[0] * N[1] >= (1LL << 31))
+    return fail(nullptr, DIRAC_ERR_UNSUPPORTED, "N[0]*N[1] must be below 2^31");
   dirac_fields f;
   if (fields) f = *fields; else dirac_fields_default(&f);
   if (f.step_axis >= dims) return fail(nullptr, DIRAC_ERR_INVALID, "step_axis >= dims");
@@ -327,7 +306,6 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
   if (s->fused) {
     if ((e = cudaMalloc(&s->state_alt, sbytes)) != cudaSuccess)
       return cleanup_fail(cuda_fail(s, e, "cudaMalloc(state_alt)"));
-    s->chunk = pick_chunk(s);
   }
   if (fields && fields->V_static) {
     size_t vb = (size_t)s->np * s->pstride * sizeof(double);

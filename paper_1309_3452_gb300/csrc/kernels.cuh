@@ -27,16 +27,14 @@ struct FusedArgs {
   const typename P::cplx* in[8];
   typename P::cplx* out[8];
   int N[3];
-  int chunk;                // march levels (z in (3+1)D, y in (2+1)D) per thread block
+  long long per_worker;     // (tile, level) items per block ((3+1)D) or warp ((2+1)D)
   long long pstride;
   int iso;
   typename P::Ratio ry, rz;
   HalfFields<P> hu, hl;     // upper / lower half-step fields
   FieldDesc f;
-  int general;
 };
-// tile geometry of the fused kernels
-constexpr int kFused3dRows = 16;   // warps per block (y rows incl. 2 halo rows)
+// (2+1)D fused kernel geometry
 constexpr int kFused2dWarps = 8;   // independent x strips per block
 constexpr int kCore = 30;          // interior lanes of a 32-lane strip
 

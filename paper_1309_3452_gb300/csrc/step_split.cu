@@ -10,7 +10,7 @@ namespace dirac {
 
 namespace {
 
-template <class P, int DIMS, bool UPPER, bool GENERAL>
+template <class P, int DIMS, bool UPPER>
 __global__ void __launch_bounds__(128) half_step_kernel(const HalfStepArgs<P> a) {
   using C = typename P::cplx;
   const int x = blockIdx.x * 32 + threadIdx.x;
@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(128) half_step_kernel(const HalfStepArgs<P> a)
         nb[2 * ax + dir] = src[cell + (long long)(jj - j[ax]) * stride[ax]];
       }
     }
-    self[cell] = site_update<P, DIMS, GENERAL>(a.h, a.f, a.iso != 0, a.ry, a.rz, plane, self[cell],
+    self[cell] = site_update<P, DIMS, kAnyMode, kAnyMode>(a.h, a.f, a.iso != 0, a.ry, a.rz, plane, self[cell],
                                                nb, H, cell, a.pstride);
   }
 }
@@ -52,10 +52,7 @@ template <class P, int DIMS, bool UPPER>
 void launch_one(const HalfStepArgs<P>& a, cudaStream_t s) {
   dim3 block(32, 4);
   dim3 grid((a.N[0] + 31) / 32, (a.N[1] + 3) / 4, DIMS == 3 ? a.N[2] : 1);
-  if (a.general)
-    half_step_kernel<P, DIMS, UPPER, true><<<grid, block, 0, s>>>(a);
-  else
-    half_step_kernel<P, DIMS, UPPER, false><<<grid, block, 0, s>>>(a);
+  half_step_kernel<P, DIMS, UPPER><<<grid, block, 0, s>>>(a);
 }
 
 }  // namespace
