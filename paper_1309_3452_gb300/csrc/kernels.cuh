@@ -27,7 +27,8 @@ struct FusedArgs {
   const typename P::cplx* in[8];
   typename P::cplx* out[8];
   int N[3];
-  long long per_worker;     // (tile, level) items per block ((3+1)D) or warp ((2+1)D)
+  int chunk;                // levels (z in (3+1)D, y in (2+1)D) per work item
+  int workers;              // persistent workers: blocks ((3+1)D) or warps ((2+1)D)
   long long pstride;
   int iso;
   typename P::Ratio ry, rz;

@@ -20,10 +20,13 @@
 // along y with the same pipeline (u0 ~ A, u1 ~ B, v1 ~ C, v0 ~ D with y as the
 // marching axis); x neighbours come from warp shuffles, no block barrier.
 //
-// Scheduling: the grid holds exactly the blocks that fit on the GPU at once
-// (or fewer for small grids) and every block (warp, in (2+1)D) takes an equal
-// contiguous run of the (tile, level) items, so all finish together; a run
-// that crosses a tile boundary restarts the march there.
+// Scheduling: the grid holds the blocks that fit on the GPU at once (fewer
+// for small grids); these persistent workers (blocks in (3+1)D, warps in
+// (2+1)D) take work items round-robin.  An item is one tile over one chunk of
+// levels, ordered chunk-major and tile-minor, so every round processes
+// neighbouring tiles at the same levels at the same time and the overlapping
+// halo loads hit L2.  The chunk length balances full rounds against the one
+// restart level of each item.
 //
 // Cells outside the grid (ragged last tiles) are wrapped periodically, so
 // they compute correct duplicates and only the owning interior thread stores.
@@ -65,9 +68,8 @@ __global__ void __launch_bounds__(kThreads3d, 2) fused3d_kernel(const FusedArgs<
   const int lx = t % TW, ly = t / TW;
   const int Nx = a.N[0], Ny = a.N[1], Nz = a.N[2];
   const int tiles_x = (Nx + CX - 1) / CX;
-  const long long total = (long long)tiles_x * ((Ny + CY - 1) / CY) * Nz;
-  long long i = (long long)blockIdx.x * a.per_worker;
-  const long long iend = min(total, i + a.per_worker);
+  const long long tiles = (long long)tiles_x * ((Ny + CY - 1) / CY);
+  const long long items = tiles * ((Nz + a.chunk - 1) / a.chunk);
   // shared-memory slots of this thread and of its x/y neighbours (clamped at
   // the tile edge: halo threads then read their own slot, values never used)
   const int sxm = lx > 0 ? t - 1 : t, sxp = lx < TW - 1 ? t + 1 : t;
@@ -75,11 +77,10 @@ __global__ void __launch_bounds__(kThreads3d, 2) fused3d_kernel(const FusedArgs<
   const bool iso = a.iso != 0;
   const long long nxy = (long long)Nx * Ny;
 
-  while (i < iend) {
-    const long long tile = i / Nz;
-    const int z0 = (int)(i - tile * Nz);
-    const int z1 = (int)min((long long)Nz, z0 + (iend - i));
-    i += z1 - z0;
+  for (long long item = blockIdx.x; item < items; item += a.workers) {
+    const long long chunk = item / tiles, tile = item - chunk * tiles;
+    const int z0 = (int)chunk * a.chunk;
+    const int z1 = min(Nz, z0 + a.chunk);
     const int gx = (int)(tile % tiles_x) * CX + lx - 1;
     const int gy = (int)(tile / tiles_x) * CY + ly - 1;
     const int x = wrapi(gx, Nx), y = wrapi(gy, Ny);
@@ -189,15 +190,13 @@ __global__ void __launch_bounds__(32 * kFused2dWarps) fused2d_kernel(const Fused
   const long long worker = (long long)blockIdx.x * kFused2dWarps + (threadIdx.x >> 5);
   const int Nx = a.N[0], Ny = a.N[1];
   const int strips = (Nx + kCore - 1) / kCore;
-  const long long total = (long long)strips * Ny;
-  long long i = worker * a.per_worker;
-  const long long iend = min(total, i + a.per_worker);
+  const long long items = (long long)strips * ((Ny + a.chunk - 1) / a.chunk);
   const bool iso = a.iso != 0;
-  while (i < iend) {  // uniform per warp
-    const int strip = (int)(i / Ny);
-    const int y0 = (int)(i - (long long)strip * Ny);
-    const int y1 = (int)min((long long)Ny, y0 + (iend - i));
-    i += y1 - y0;
+  for (long long item = worker; item < items; item += a.workers) {  // uniform per warp
+    const long long chunk = item / strips;
+    const int strip = (int)(item - chunk * strips);
+    const int y0 = (int)chunk * a.chunk;
+    const int y1 = min(Ny, y0 + a.chunk);
     const int gx = strip * kCore + lane - 1;
     const int x = wrapi(gx, Nx);
     const bool core = lane >= 1 && lane <= kCore && gx < Nx;
@@ -259,35 +258,57 @@ int sm_count() {
   return n > 0 ? n : 1;
 }
 
-// Grid of at most (resident blocks) with an equal run of items per worker,
-// and at least `min_run` items per worker.
+// Chunk length (levels per item) for `tiles` items per level chunk, `levels`
+// levels and `workers` persistent workers: maximise the busy fraction of the
+// rounds times the useful fraction chunk/(chunk+1) of each item.
+int plan_chunk(long long tiles, int levels, long long workers, int min_chunk) {
+  int best = levels;
+  double best_eff = -1.0;
+  for (int c = 1; c <= levels; ++c) {
+    int len = (levels + c - 1) / c;
+    if (len < min_chunk && c > 1) break;
+    int chunks = (levels + len - 1) / len;
+    long long items = tiles * chunks;
+    long long rounds = (items + workers - 1) / workers;
+    // work of a round ~ len + 1 levels; total time ~ rounds * (len + 1)
+    double eff = (double)tiles * levels / ((double)rounds * workers * (len + 1));
+    if (eff > best_eff * 1.0001) {
+      best_eff = eff;
+      best = len;
+    }
+  }
+  return best;
+}
+
 template <class K>
-long long schedule(K kernel, int threads, long long total, int workers_per_block, int min_run,
-                   long long& per_worker) {
+int resident_blocks(K kernel, int threads) {
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
-  if (per_sm < 1) per_sm = 1;
-  long long workers = (long long)sm_count() * per_sm * workers_per_block;
-  per_worker = (total + workers - 1) / workers;
-  if (per_worker < min_run) per_worker = min_run;
-  long long used = (total + per_worker - 1) / per_worker;
-  return (used + workers_per_block - 1) / workers_per_block;
+  return (per_sm < 1 ? 1 : per_sm) * sm_count();
 }
 
 template <int COEF, int LINK>
 void launch3d(FusedArgs<F32> a, cudaStream_t s) {
   auto k = fused3d_kernel<F32, COEF, LINK>;
-  long long total = (long long)((a.N[0] + CX - 1) / CX) * ((a.N[1] + CY - 1) / CY) * a.N[2];
-  long long blocks = schedule(k, kThreads3d, total, 1, 4, a.per_worker);
-  k<<<(unsigned)blocks, kThreads3d, 0, s>>>(a);
+  static int resident = resident_blocks(k, kThreads3d);
+  long long tiles = (long long)((a.N[0] + CX - 1) / CX) * ((a.N[1] + CY - 1) / CY);
+  a.chunk = plan_chunk(tiles, a.N[2], resident, 4);
+  long long items = tiles * ((a.N[2] + a.chunk - 1) / a.chunk);
+  a.workers = (int)(items < resident ? items : resident);
+  k<<<(unsigned)a.workers, kThreads3d, 0, s>>>(a);
 }
 
 template <int COEF, int LINK>
 void launch2d(FusedArgs<F32> a, cudaStream_t s) {
   auto k = fused2d_kernel<F32, COEF, LINK>;
-  long long total = (long long)((a.N[0] + kCore - 1) / kCore) * a.N[1];
-  long long blocks = schedule(k, 32 * kFused2dWarps, total, kFused2dWarps, 16, a.per_worker);
-  k<<<(unsigned)blocks, 32 * kFused2dWarps, 0, s>>>(a);
+  static int resident = resident_blocks(k, 32 * kFused2dWarps);
+  long long strips = (a.N[0] + kCore - 1) / kCore;
+  long long warps = (long long)resident * kFused2dWarps;
+  a.chunk = plan_chunk(strips, a.N[1], warps, 16);
+  long long items = strips * ((a.N[1] + a.chunk - 1) / a.chunk);
+  long long w = items < warps ? items : warps;
+  a.workers = (int)w;
+  k<<<(unsigned)((w + kFused2dWarps - 1) / kFused2dWarps), 32 * kFused2dWarps, 0, s>>>(a);
 }
 
 template <int DIMS, int COEF, int LINK>

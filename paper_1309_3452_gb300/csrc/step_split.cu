@@ -10,7 +10,7 @@ namespace dirac {
 
 namespace {
 
-template <class P, int DIMS, bool UPPER>
+template <class P, int DIMS, bool UPPER, int COEF, int LINK>
 __global__ void __launch_bounds__(128) half_step_kernel(const HalfStepArgs<P> a) {
   using C = typename P::cplx;
   const int x = blockIdx.x * 32 + threadIdx.x;
@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(128) half_step_kernel(const HalfStepArgs<P> a)
         nb[2 * ax + dir] = src[cell + (long long)(jj - j[ax]) * stride[ax]];
       }
     }
-    self[cell] = site_update<P, DIMS, kAnyMode, kAnyMode>(a.h, a.f, a.iso != 0, a.ry, a.rz, plane, self[cell],
+    self[cell] = site_update<P, DIMS, COEF, LINK>(a.h, a.f, a.iso != 0, a.ry, a.rz, plane, self[cell],
                                                nb, H, cell, a.pstride);
   }
 }
@@ -52,7 +52,13 @@ template <class P, int DIMS, bool UPPER>
 void launch_one(const HalfStepArgs<P>& a, cudaStream_t s) {
   dim3 block(32, 4);
   dim3 grid((a.N[0] + 31) / 32, (a.N[1] + 3) / 4, DIMS == 3 ? a.N[2] : 1);
-  half_step_kernel<P, DIMS, UPPER><<<grid, block, 0, s>>>(a);
+  const int c = a.h.coef_mode, l = a.h.link_mode;
+  if (c == COEF_UNIFORM && l == LINK_NONE)
+    half_step_kernel<P, DIMS, UPPER, COEF_UNIFORM, LINK_NONE><<<grid, block, 0, s>>>(a);
+  else if (c == COEF_STEP && l == LINK_NONE)
+    half_step_kernel<P, DIMS, UPPER, COEF_STEP, LINK_NONE><<<grid, block, 0, s>>>(a);
+  else
+    half_step_kernel<P, DIMS, UPPER, kAnyMode, kAnyMode><<<grid, block, 0, s>>>(a);
 }
 
 }  // namespace
