@@ -316,8 +316,7 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
       if (e != cudaSuccess) return cleanup_fail(cuda_fail(s, e, "cudaMemcpyAsync(V)"));
     }
   }
-  long long want = (s->ncell + 255) / 256;
-  s->red_blocks = (int)(want > 152 * 8 ? 152 * 8 : (want < 1 ? 1 : want));
+  s->red_blocks = observables_blocks(s->N, dims);
   if ((e = cudaMalloc(&s->partials, (size_t)s->red_blocks * kObsSums * sizeof(double))) != cudaSuccess)
     return cleanup_fail(cuda_fail(s, e, "cudaMalloc(partials)"));
   if ((e = cudaMalloc(&s->sums_dev, kObsSums * sizeof(double))) != cudaSuccess)

@@ -59,6 +59,8 @@ struct ObsArgs {
 };
 constexpr int kObsSums = 5;
 
+// number of blocks (= partial sums) the observables kernel uses for a grid
+int observables_blocks(const int N[3], int dims);
 template <class P, int DIMS>
 void launch_observables(const ObsArgs<P>& a, int blocks, cudaStream_t s);
 // fixed-order sum of partials[nblocks][5] into out[5]

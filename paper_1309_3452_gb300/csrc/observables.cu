@@ -1,10 +1,10 @@
 // Reductions of the stored state: the naive norm, the cross terms of the
 // conserved functional (Lemma of Sect. 2, Eq. EPM, in its "lower" form; see
 // dirac.h) and the partial density used for the Klein-step transmission.
-// Every per-site term is formed in FP64 from the stored values (exact
-// widening for FP32 states), summed per thread, per warp (shuffles), per
-// block (shared memory) and finally over blocks in a fixed order, so the
-// result is deterministic for a given grid.
+// One thread per cell (z strided over the grid's z blocks): the cell's terms
+// are summed in the state's precision, then accumulated in FP64 per thread,
+// per warp (shuffles), per block (shared memory) and finally over blocks in a
+// fixed order, so the result is deterministic for a given grid.
 #include "kernels.cuh"
 
 namespace dirac {
@@ -19,15 +19,12 @@ __device__ __forceinline__ double2 mul_expm(double2 v, double phi) {  // v * exp
   sincos(phi, &s, &c);
   return make_double2(c * v.x + s * v.y, c * v.y - s * v.x);
 }
-__device__ __forceinline__ double2 widen_link(const F64::Link& L) { return L.u; }
-__device__ __forceinline__ double2 widen_link(const F32::Link& L) {
-  return make_double2((double)L.hi.x + (double)L.lo.x, (double)L.hi.y + (double)L.lo.y);
-}
 
 template <int NS>
 __device__ __forceinline__ void block_reduce_store(double (&v)[NS], double* out) {
   __shared__ double sh[32][NS];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int k = 0; k < NS; ++k)
 #pragma unroll
@@ -37,7 +34,7 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NS], double* out)
     for (int k = 0; k < NS; ++k) sh[warp][k] = v[k];
   __syncthreads();
   if (warp == 0) {
-    const int nw = blockDim.x >> 5;
+    const int nw = (blockDim.x * blockDim.y) >> 5;
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       double x = lane < nw ? sh[lane][k] : 0.0;
@@ -48,58 +45,87 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NS], double* out)
   }
 }
 
+// Per-cell terms are formed in the working precision of the state (FP32
+// states: every term is a product of two stored floats, rounded once; the
+// FP64 accumulation over cells keeps the sum accurate), except with
+// plane-wave link factors, which are evaluated in FP64.
 template <class P, int DIMS>
 __global__ void __launch_bounds__(256) observables_kernel(const ObsArgs<P> a) {
-  const long long N0 = a.N[0], N1 = a.N[1], N2 = (DIMS == 3) ? a.N[2] : 1;
-  const long long ncell = N0 * N1 * N2;
-  const long long Nn[3] = {N0, N1, N2};
+  using C = typename P::cplx;
+  using R = typename P::real;
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * 8 + threadIdx.y;
+  const int Nx = a.N[0], Ny = a.N[1], Nz = DIMS == 3 ? a.N[2] : 1;
+  const long long nxy = (long long)Nx * Ny;
   double acc[kObsSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < ncell;
-       cell += (long long)gridDim.x * blockDim.x) {
-    const long long j[3] = {cell % N0, (cell / N0) % N1, cell / (N0 * N1)};
+  if (x < Nx && y < Ny) {
+    for (int z = blockIdx.z; z < Nz; z += gridDim.z) {
+      const long long cell = z * nxy + (long long)y * Nx + x;
+      const int j[3] = {x, y, z};
+      const int Nn[3] = {Nx, Ny, Nz};
+      const long long stride[3] = {1, Nx, nxy};
+      R cn = 0, cd = 0, cb[3] = {0, 0, 0};
 #pragma unroll
-    for (int plane = 0; plane < nplanes<DIMS>(); ++plane) {
-      const double2 G = widen(a.pl[plane][cell]);
-      const double n2 = G.x * G.x + G.y * G.y;
-      acc[0] += n2;
-      long long H[3];
+      for (int plane = 0; plane < nplanes<DIMS>(); ++plane) {
+        const C G = a.pl[plane][cell];
+        const R n2 = G.x * G.x + G.y * G.y;
+        cn += n2;
+        long long H[3];
 #pragma unroll
-      for (int ax = 0; ax < 3; ++ax) H[ax] = 2 * j[ax] + plane_off<DIMS>(plane, ax);
-      if (a.dens_axis >= 0 && H[a.dens_axis] >= a.dens_X) acc[4] += n2;
-      if (is_upper<DIMS>(plane)) continue;
-      const int p = sign_class<DIMS>(plane);
+        for (int ax = 0; ax < 3; ++ax) H[ax] = 2 * j[ax] + plane_off<DIMS>(plane, ax);
+        const long long hd = a.dens_axis == 0 ? H[0] : (a.dens_axis == 1 ? H[1] : H[2]);
+        if (a.dens_axis >= 0 && hd >= a.dens_X) cd += n2;
+        if (is_upper<DIMS>(plane)) continue;
+        const int p = sign_class<DIMS>(plane);
 #pragma unroll
-      for (int ax = 0; ax < DIMS; ++ax) {
-        const typename P::cplx* nb = a.pl[partner<DIMS>(plane, ax)];
-        long long jp = j[ax] + nb_shift<DIMS>(plane, ax, +1);
-        long long jm = j[ax] + nb_shift<DIMS>(plane, ax, -1);
-        jp = jp >= Nn[ax] ? jp - Nn[ax] : jp;
-        jm = jm < 0 ? jm + Nn[ax] : jm;
-        long long stride = ax == 0 ? 1 : (ax == 1 ? N0 : N0 * N1);
-        double2 up = widen(nb[cell + (jp - j[ax]) * stride]);
-        double2 dn = widen(nb[cell + (jm - j[ax]) * stride]);
-        if (a.link_mode == LINK_CONST) {
-          double2 u = widen_link(a.L[ax]);
-          up = make_double2(u.x * up.x - u.y * up.y, u.x * up.y + u.y * up.x);
-          dn = make_double2(u.x * dn.x + u.y * dn.y, u.x * dn.y - u.y * dn.x);
-        } else if (a.link_mode == LINK_GENERAL) {
-          up = mul_expm(up, link_phase(a.f, DIMS, H, ax, +1, a.t_links));
-          dn = mul_expm(dn, -link_phase(a.f, DIMS, H, ax, -1, a.t_links));
+        for (int ax = 0; ax < DIMS; ++ax) {
+          const C* nb = a.pl[partner<DIMS>(plane, ax)];
+          int jp = j[ax] + nb_shift<DIMS>(plane, ax, +1);
+          int jm = j[ax] + nb_shift<DIMS>(plane, ax, -1);
+          jp = jp >= Nn[ax] ? jp - Nn[ax] : jp;
+          jm = jm < 0 ? jm + Nn[ax] : jm;
+          C up = nb[cell + (long long)(jp - j[ax]) * stride[ax]];
+          C dn = nb[cell + (long long)(jm - j[ax]) * stride[ax]];
+          R re, im;
+          if (a.link_mode == LINK_GENERAL) {
+            double2 u = mul_expm(widen(up), link_phase(a.f, DIMS, H, ax, +1, a.t_links));
+            double2 v = mul_expm(widen(dn), -link_phase(a.f, DIMS, H, ax, -1, a.t_links));
+            re = (R)(u.x - v.x);
+            im = (R)(u.y - v.y);
+          } else {
+            if (a.link_mode == LINK_CONST) {
+              up = link_mul(a.L[ax], up);
+              dn = link_mulc(a.L[ax], dn);
+            }
+            re = up.x - dn.x;
+            im = up.y - dn.y;
+          }
+          // s_a d: s_x = 1; s_y = -i (p=0) / +i (p=1); s_z = +1 (p=0) / -1 (p=1)
+          R sre = re, sim = im;
+          if (ax == 1) {
+            sre = p ? -im : im;
+            sim = p ? re : -re;
+          }
+          if (ax == 2 && p) {
+            sre = -re;
+            sim = -im;
+          }
+          cb[ax] += G.x * sre + G.y * sim;  // Re(conj(G) s d)
         }
-        double2 d = make_double2(up.x - dn.x, up.y - dn.y);
-        // s_a d: s_x = 1; s_y = -i (p=0) / +i (p=1); s_z = +1 (p=0) / -1 (p=1)
-        double2 sd = d;
-        if (ax == 1) sd = p ? make_double2(-d.y, d.x) : make_double2(d.y, -d.x);
-        if (ax == 2 && p) sd = make_double2(-d.x, -d.y);
-        acc[1 + ax] += G.x * sd.x + G.y * sd.y;  // Re(conj(G) sd)
       }
+      acc[0] += (double)cn;
+      acc[1] += (double)cb[0];
+      acc[2] += (double)cb[1];
+      acc[3] += (double)cb[2];
+      acc[4] += (double)cd;
     }
   }
-  block_reduce_store<kObsSums>(acc, a.partials + (long long)blockIdx.x * kObsSums);
+  const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  block_reduce_store<kObsSums>(acc, a.partials + b * kObsSums);
 }
 
 __global__ void finish_sums_kernel(const double* partials, int nblocks, double* out) {
-  // one block of 32*kObsSums threads? keep it simple: warp k sums column k
+  // warp k sums column k: lane-strided, then a fixed shuffle tree
   const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;
   if (k >= kObsSums) return;
   double x = 0.0;
@@ -124,9 +150,20 @@ __global__ void convert_out_kernel(const float2* __restrict__ src, double2* __re
 
 }  // namespace
 
+int observables_blocks(const int N[3], int dims) {
+  const int gx = (N[0] + 31) / 32, gy = (N[1] + 7) / 8;
+  const int nz = dims == 3 ? N[2] : 1;
+  long long per_z = (long long)gx * gy;
+  long long gz = (152LL * 8 + per_z - 1) / per_z;
+  if (gz > nz) gz = nz;
+  if (gz < 1) gz = 1;
+  return (int)(per_z * gz);
+}
+
 template <class P, int DIMS>
 void launch_observables(const ObsArgs<P>& a, int blocks, cudaStream_t s) {
-  observables_kernel<P, DIMS><<<blocks, 256, 0, s>>>(a);
+  const int gx = (a.N[0] + 31) / 32, gy = (a.N[1] + 7) / 8;
+  observables_kernel<P, DIMS><<<dim3(gx, gy, blocks / (gx * gy)), dim3(32, 8), 0, s>>>(a);
 }
 template void launch_observables<F64, 2>(const ObsArgs<F64>&, int, cudaStream_t);
 template void launch_observables<F64, 3>(const ObsArgs<F64>&, int, cudaStream_t);

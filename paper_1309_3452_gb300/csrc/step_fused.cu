@@ -8,8 +8,10 @@
 // they load and compute like every other thread, so the new upper values the
 // 32 x 13 interior needs from outside the tile exist in shared memory, but
 // they store nothing.  Per z level k the block
-//   1. loads the old A(k+1), C(k+1), D(k+1) and B(k) (B, C sit at z+1/2),
-//   2. publishes the old D(k+1), C(k) in shared memory,
+//   1. has the old A(k+1), C(k+1), D(k+1) and B(k) (B, C sit at z+1/2) in
+//      shared memory, copied there by cp.async while level k-1 was computed,
+//      and starts the copies of level k+1,
+//   2. publishes the old C(k) in shared memory,
 //   3. computes the new A(k+1) and B(k)      (upper half-step, t -> t+dt/2),
 //   4. publishes them,
 //   5. computes the new C(k) and D(k)        (lower half-step, t -> t+dt),
@@ -56,13 +58,28 @@ __device__ __forceinline__ int wrapi(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+constexpr int kSlots = kSmemRows * TW;  // shared-memory slots per plane tile
+// stage[2][8][kSlots] + sC[2] + sB[2] + sA[2][2] tiles
+constexpr size_t kSmem3d = (size_t)(2 * 8 + 2 + 2 + 4) * kSlots * sizeof(float2);
+
 template <class P, int COEF, int LINK>
 __global__ void __launch_bounds__(kThreads3d, 2) fused3d_kernel(const FusedArgs<P> a) {
   using C = typename P::cplx;
-  __shared__ C sC[2][kSmemRows * TW];     // old C(k), both sublattices
-  __shared__ C sD[2][kSmemRows * TW];     // old D(k+1)
-  __shared__ C sB[2][kSmemRows * TW];     // new B(k)
-  __shared__ C sA[2][2][kSmemRows * TW];  // new A, double-buffered by level parity
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // stage[b][p]: the values level k loads (A(k+1), B(k), C(k+1), D(k+1) in
+  // plane order A0 A1 B0 B1 C0 C1 D0 D1), double-buffered by level parity and
+  // filled by cp.async one level ahead
+  C (*stage)[8][kSlots] = reinterpret_cast<C (*)[8][kSlots]>(smem_raw);
+  C (*sC)[kSlots] = reinterpret_cast<C (*)[kSlots]>(smem_raw + 16 * kSlots * sizeof(C));  // old C(k)
+  C (*sB)[kSlots] = sC + 2;                                                              // new B(k)
+  C (*sA)[2][kSlots] = reinterpret_cast<C (*)[2][kSlots]>(sB + 2);  // new A, by level parity
 
   const int t = threadIdx.x;
   const int lx = t % TW, ly = t / TW;
@@ -70,8 +87,8 @@ __global__ void __launch_bounds__(kThreads3d, 2) fused3d_kernel(const FusedArgs<
   const int tiles_x = (Nx + CX - 1) / CX;
   const long long tiles = (long long)tiles_x * ((Ny + CY - 1) / CY);
   const long long items = tiles * ((Nz + a.chunk - 1) / a.chunk);
-  // shared-memory slots of this thread and of its x/y neighbours (clamped at
-  // the tile edge: halo threads then read their own slot, values never used)
+  // shared-memory slots of this thread's x/y neighbours (clamped at the tile
+  // edge: halo threads then read their own slot, values never used)
   const int sxm = lx > 0 ? t - 1 : t, sxp = lx < TW - 1 ? t + 1 : t;
   const int sym = ly > 0 ? t - TW : t, syp = ly < kSmemRows - 1 ? t + TW : t;
   const bool iso = a.iso != 0;
@@ -88,33 +105,50 @@ __global__ void __launch_bounds__(kThreads3d, 2) fused3d_kernel(const FusedArgs<
     const long long cxy = (long long)y * Nx + x;
     const int hx = 2 * x, hy = 2 * y;
 
+    // the loads of level k: A, C, D at level k+1 and B at level k
+    auto prefetch = [&](int k) {
+      const int zk = k < 0 ? k + Nz : k;
+      const int zn = k + 1 >= Nz ? k + 1 - Nz : k + 1;
+      const long long ok = zk * nxy + cxy, on = zn * nxy + cxy;
+      C(*st)[kSlots] = stage[k & 1];
+      cp_async8(&st[0][t], a.in[0] + on);
+      cp_async8(&st[1][t], a.in[1] + on);
+      cp_async8(&st[2][t], a.in[2] + ok);
+      cp_async8(&st[3][t], a.in[3] + ok);
+      cp_async8(&st[4][t], a.in[4] + on);
+      cp_async8(&st[5][t], a.in[5] + on);
+      cp_async8(&st[6][t], a.in[6] + on);
+      cp_async8(&st[7][t], a.in[7] + on);
+      cp_async_commit();
+    };
+
     long long o = (long long)wrapi(z0 - 1, Nz) * nxy + cxy;
     C oC0 = ld(a.in[4] + o), oC1 = ld(a.in[5] + o), oD0 = ld(a.in[6] + o), oD1 = ld(a.in[7] + o);
     C nA0 = oC0, nA1 = oC1, nB0 = oD0, nB1 = oD1;  // placeholders: only feed values never stored
+    prefetch(z0 - 1);
 
     for (int k = z0 - 1; k < z1; ++k) {
       const int zk = k < 0 ? k + Nz : k;
       const int zn = k + 1 >= Nz ? k + 1 - Nz : k + 1;
       const long long ok = zk * nxy + cxy, on = zn * nxy + cxy;
-      const C A0 = ld(a.in[0] + on), A1 = ld(a.in[1] + on);
-      const C C0n = ld(a.in[4] + on), C1n = ld(a.in[5] + on);
-      const C D0n = ld(a.in[6] + on), D1n = ld(a.in[7] + on);
-      const C B0 = ld(a.in[2] + ok), B1 = ld(a.in[3] + ok);
-      sD[0][t] = D0n;
-      sD[1][t] = D1n;
+      cp_async_wait_all();
       sC[0][t] = oC0;
       sC[1][t] = oC1;
-      __syncthreads();
+      __syncthreads();  // level k staged by every thread; old C(k) published
+      if (k + 1 < z1) prefetch(k + 1);
+      C(*st)[kSlots] = stage[k & 1];
+      const C A0 = st[0][t], A1 = st[1][t], B0 = st[2][t], B1 = st[3][t];
+      const C C0n = st[4][t], C1n = st[5][t], D0n = st[6][t], D1n = st[7][t];
 
       // upper half-step: A(k+1) from C(k+1), C(k), D(k+1); B(k) from D(k+1), D(k), C(k)
       C nA0n, nA1n, nB0k, nB1k;
       {
-        C nb[6] = {D0n, sD[0][sxm], D1n, sD[1][sym], C0n, oC0};
+        C nb[6] = {D0n, st[6][sxm], D1n, st[7][sym], C0n, oC0};
         const int H[3] = {hx, hy, 2 * zn};
         nA0n = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 0, A0, nb, H, on, a.pstride);
       }
       {
-        C nb[6] = {sD[1][sxp], D1n, sD[0][syp], D0n, C1n, oC1};
+        C nb[6] = {st[7][sxp], D1n, st[6][syp], D0n, C1n, oC1};
         const int H[3] = {hx + 1, hy + 1, 2 * zn};
         nA1n = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 1, A1, nb, H, on, a.pstride);
       }
@@ -180,6 +214,7 @@ __global__ void __launch_bounds__(kThreads3d, 2) fused3d_kernel(const FusedArgs<
       nB0 = nB0k;
       nB1 = nB1k;
     }
+    __syncthreads();  // every read of this item's stage before the next item's prefetch
   }
 }
 
@@ -281,21 +316,24 @@ int plan_chunk(long long tiles, int levels, long long workers, int min_chunk) {
 }
 
 template <class K>
-int resident_blocks(K kernel, int threads) {
+int resident_blocks(K kernel, int threads, size_t smem = 0) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
   return (per_sm < 1 ? 1 : per_sm) * sm_count();
 }
 
 template <int COEF, int LINK>
 void launch3d(FusedArgs<F32> a, cudaStream_t s) {
   auto k = fused3d_kernel<F32, COEF, LINK>;
-  static int resident = resident_blocks(k, kThreads3d);
+  static int resident = [&] {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem3d);
+    return resident_blocks(k, kThreads3d, kSmem3d);
+  }();
   long long tiles = (long long)((a.N[0] + CX - 1) / CX) * ((a.N[1] + CY - 1) / CY);
   a.chunk = plan_chunk(tiles, a.N[2], resident, 4);
   long long items = tiles * ((a.N[2] + a.chunk - 1) / a.chunk);
   a.workers = (int)(items < resident ? items : resident);
-  k<<<(unsigned)a.workers, kThreads3d, 0, s>>>(a);
+  k<<<(unsigned)a.workers, kThreads3d, kSmem3d, s>>>(a);
 }
 
 template <int COEF, int LINK>
