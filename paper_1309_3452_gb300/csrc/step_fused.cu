@@ -8,15 +8,15 @@
 // they load and compute like every other thread, so the new upper values the
 // 32 x 13 interior needs from outside the tile exist in shared memory, but
 // they store nothing.  Per z level k the block
-//   1. has the old A(k+1), C(k+1), D(k+1) and B(k) (B, C sit at z+1/2) in
-//      shared memory, copied there by cp.async while level k-1 was computed,
-//      and starts the copies of level k+1,
-//   2. publishes the old C(k) in shared memory,
+//   1. holds the old A(k+1), C(k+1), D(k+1) and B(k) (B, C sit at z+1/2) in
+//      registers, loaded while level k-1 was computed, publishes C(k+1) and
+//      D(k+1) in shared memory and starts the loads of level k+1,
+//   2. (the old C(k), D(k) and the new A(k), B(k-1) are in shared memory,
+//      every tile double-buffered by level parity),
 //   3. computes the new A(k+1) and B(k)      (upper half-step, t -> t+dt/2),
 //   4. publishes them,
 //   5. computes the new C(k) and D(k)        (lower half-step, t -> t+dt),
-// keeping old C, D and new A, B of the previous level in registers for the z
-// differences.  A run of levels starts one level early to rebuild that state.
+// A run of levels starts one level early to rebuild that state.
 //
 // (2+1)D: each warp owns a strip of 32 cells in x (30 interior) and marches
 // along y with the same pipeline (u0 ~ A, u1 ~ B, v1 ~ C, v0 ~ D with y as the
@@ -58,28 +58,25 @@ __device__ __forceinline__ int wrapi(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
 constexpr int kSlots = kSmemRows * TW;  // shared-memory slots per plane tile
-// stage[2][8][kSlots] + sC[2] + sB[2] + sA[2][2] tiles
-constexpr size_t kSmem3d = (size_t)(2 * 8 + 2 + 2 + 4) * kSlots * sizeof(float2);
+// sC, sD, sB, sA: [level parity][sublattice][slot]
+constexpr size_t kSmem3d = (size_t)4 * 2 * 2 * kSlots * sizeof(float2);
+
+// The eight values of one level load: A, C, D at level k+1 and B at level k.
+template <class C>
+struct LevelLoad {
+  C A0, A1, B0, B1, C0, C1, D0, D1;
+};
 
 template <class P, int COEF, int LINK>
 __global__ void __launch_bounds__(kThreads3d, 2) fused3d_kernel(const FusedArgs<P> a) {
   using C = typename P::cplx;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // stage[b][p]: the values level k loads (A(k+1), B(k), C(k+1), D(k+1) in
-  // plane order A0 A1 B0 B1 C0 C1 D0 D1), double-buffered by level parity and
-  // filled by cp.async one level ahead
-  C (*stage)[8][kSlots] = reinterpret_cast<C (*)[8][kSlots]>(smem_raw);
-  C (*sC)[kSlots] = reinterpret_cast<C (*)[kSlots]>(smem_raw + 16 * kSlots * sizeof(C));  // old C(k)
-  C (*sB)[kSlots] = sC + 2;                                                              // new B(k)
-  C (*sA)[2][kSlots] = reinterpret_cast<C (*)[2][kSlots]>(sB + 2);  // new A, by level parity
+  // every tile is double-buffered by level parity: slot [k & 1] holds level k
+  C (*sC)[2][kSlots] = reinterpret_cast<C (*)[2][kSlots]>(smem_raw);  // old C(k)
+  C (*sD)[2][kSlots] = sC + 2;                                         // old D(k)
+  C (*sB)[2][kSlots] = sC + 4;                                         // new B(k)
+  C (*sA)[2][kSlots] = sC + 6;                                         // new A(k)
 
   const int t = threadIdx.x;
   const int lx = t % TW, ly = t / TW;
@@ -105,91 +102,97 @@ __global__ void __launch_bounds__(kThreads3d, 2) fused3d_kernel(const FusedArgs<
     const long long cxy = (long long)y * Nx + x;
     const int hx = 2 * x, hy = 2 * y;
 
-    // the loads of level k: A, C, D at level k+1 and B at level k
-    auto prefetch = [&](int k) {
+    auto load = [&](int k) {
       const int zk = k < 0 ? k + Nz : k;
       const int zn = k + 1 >= Nz ? k + 1 - Nz : k + 1;
       const long long ok = zk * nxy + cxy, on = zn * nxy + cxy;
-      C(*st)[kSlots] = stage[k & 1];
-      cp_async8(&st[0][t], a.in[0] + on);
-      cp_async8(&st[1][t], a.in[1] + on);
-      cp_async8(&st[2][t], a.in[2] + ok);
-      cp_async8(&st[3][t], a.in[3] + ok);
-      cp_async8(&st[4][t], a.in[4] + on);
-      cp_async8(&st[5][t], a.in[5] + on);
-      cp_async8(&st[6][t], a.in[6] + on);
-      cp_async8(&st[7][t], a.in[7] + on);
-      cp_async_commit();
+      LevelLoad<C> l;
+      l.A0 = ld(a.in[0] + on);
+      l.A1 = ld(a.in[1] + on);
+      l.B0 = ld(a.in[2] + ok);
+      l.B1 = ld(a.in[3] + ok);
+      l.C0 = ld(a.in[4] + on);
+      l.C1 = ld(a.in[5] + on);
+      l.D0 = ld(a.in[6] + on);
+      l.D1 = ld(a.in[7] + on);
+      return l;
     };
 
-    long long o = (long long)wrapi(z0 - 1, Nz) * nxy + cxy;
-    C oC0 = ld(a.in[4] + o), oC1 = ld(a.in[5] + o), oD0 = ld(a.in[6] + o), oD1 = ld(a.in[7] + o);
-    C nA0 = oC0, nA1 = oC1, nB0 = oD0, nB1 = oD1;  // placeholders: only feed values never stored
-    prefetch(z0 - 1);
+    {  // old C, D of level z0-1 (the z- neighbours of the first level)
+      const int p = (z0 - 1) & 1;
+      const long long o = (long long)wrapi(z0 - 1, Nz) * nxy + cxy;
+      sC[p][0][t] = ld(a.in[4] + o);
+      sC[p][1][t] = ld(a.in[5] + o);
+      sD[p][0][t] = ld(a.in[6] + o);
+      sD[p][1][t] = ld(a.in[7] + o);
+    }
+    LevelLoad<C> cur = load(z0 - 1);
 
     for (int k = z0 - 1; k < z1; ++k) {
       const int zk = k < 0 ? k + Nz : k;
       const int zn = k + 1 >= Nz ? k + 1 - Nz : k + 1;
       const long long ok = zk * nxy + cxy, on = zn * nxy + cxy;
-      cp_async_wait_all();
-      sC[0][t] = oC0;
-      sC[1][t] = oC1;
-      __syncthreads();  // level k staged by every thread; old C(k) published
-      if (k + 1 < z1) prefetch(k + 1);
-      C(*st)[kSlots] = stage[k & 1];
-      const C A0 = st[0][t], A1 = st[1][t], B0 = st[2][t], B1 = st[3][t];
-      const C C0n = st[4][t], C1n = st[5][t], D0n = st[6][t], D1n = st[7][t];
+      const int pk = k & 1, pn = (k + 1) & 1, pm = (k - 1) & 1;
+      sC[pn][0][t] = cur.C0;  // old C(k+1), D(k+1): z+ / x,y neighbours now,
+      sC[pn][1][t] = cur.C1;  // own old values at the next level
+      sD[pn][0][t] = cur.D0;
+      sD[pn][1][t] = cur.D1;
+      // prefetch the next level while this one computes
+      LevelLoad<C> nxt = cur;
+      if (k + 1 < z1) nxt = load(k + 1);
+      __syncthreads();
 
       // upper half-step: A(k+1) from C(k+1), C(k), D(k+1); B(k) from D(k+1), D(k), C(k)
+      const C oC0 = sC[pk][0][t], oC1 = sC[pk][1][t];
       C nA0n, nA1n, nB0k, nB1k;
       {
-        C nb[6] = {D0n, st[6][sxm], D1n, st[7][sym], C0n, oC0};
+        C nb[6] = {cur.D0, sD[pn][0][sxm], cur.D1, sD[pn][1][sym], cur.C0, oC0};
         const int H[3] = {hx, hy, 2 * zn};
-        nA0n = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 0, A0, nb, H, on, a.pstride);
+        nA0n = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 0, cur.A0, nb, H, on, a.pstride);
       }
       {
-        C nb[6] = {st[7][sxp], D1n, st[6][syp], D0n, C1n, oC1};
+        C nb[6] = {sD[pn][1][sxp], cur.D1, sD[pn][0][syp], cur.D0, cur.C1, oC1};
         const int H[3] = {hx + 1, hy + 1, 2 * zn};
-        nA1n = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 1, A1, nb, H, on, a.pstride);
+        nA1n = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 1, cur.A1, nb, H, on, a.pstride);
       }
       {
-        C nb[6] = {sC[0][sxp], oC0, oC1, sC[1][sym], D0n, oD0};
+        C nb[6] = {sC[pk][0][sxp], oC0, oC1, sC[pk][1][sym], cur.D0, sD[pk][0][t]};
         const int H[3] = {hx + 1, hy, 2 * zk + 1};
-        nB0k = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 2, B0, nb, H, ok, a.pstride);
+        nB0k = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 2, cur.B0, nb, H, ok, a.pstride);
       }
       {
-        C nb[6] = {oC1, sC[1][sxm], sC[0][syp], oC0, D1n, oD1};
+        C nb[6] = {oC1, sC[pk][1][sxm], sC[pk][0][syp], oC0, cur.D1, sD[pk][1][t]};
         const int H[3] = {hx, hy + 1, 2 * zk + 1};
-        nB1k = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 3, B1, nb, H, ok, a.pstride);
+        nB1k = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 3, cur.B1, nb, H, ok, a.pstride);
       }
-      const int pn = (k + 1) & 1, pk = k & 1;
-      sB[0][t] = nB0k;
-      sB[1][t] = nB1k;
+      sB[pk][0][t] = nB0k;
+      sB[pk][1][t] = nB1k;
       sA[pn][0][t] = nA0n;
       sA[pn][1][t] = nA1n;
       __syncthreads();
 
       // lower half-step: C(k) from A(k+1), A(k), B(k); D(k) from B(k), B(k-1), A(k)
+      const C nA0 = sA[pk][0][t], nA1 = sA[pk][1][t];
       C nC0, nC1, nD0, nD1;
       {
-        C nb[6] = {nB0k, sB[0][sxm], nB1k, sB[1][sym], nA0n, nA0};
+        C nb[6] = {nB0k, sB[pk][0][sxm], nB1k, sB[pk][1][sym], nA0n, nA0};
         const int H[3] = {hx, hy, 2 * zk + 1};
         nC0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 4, oC0, nb, H, ok, a.pstride);
       }
       {
-        C nb[6] = {sB[1][sxp], nB1k, sB[0][syp], nB0k, nA1n, nA1};
+        C nb[6] = {sB[pk][1][sxp], nB1k, sB[pk][0][syp], nB0k, nA1n, nA1};
         const int H[3] = {hx + 1, hy + 1, 2 * zk + 1};
         nC1 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 5, oC1, nb, H, ok, a.pstride);
       }
       {
-        C nb[6] = {sA[pk][0][sxp], nA0, nA1, sA[pk][1][sym], nB0k, nB0};
+        C nb[6] = {sA[pk][0][sxp], nA0, nA1, sA[pk][1][sym], nB0k, sB[pm][0][t]};
         const int H[3] = {hx + 1, hy, 2 * zk};
-        nD0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 6, oD0, nb, H, ok, a.pstride);
+        nD0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 6, sD[pk][0][t], nb, H, ok, a.pstride);
       }
       {
-        C nb[6] = {nA1, sA[pk][1][sxm], sA[pk][0][syp], nA0, nB1k, nB1};
+        C nb[6] = {nA1, sA[pk][1][sxm], sA[pk][0][syp], nA0, nB1k, sB[pm][1][t]};
         const int H[3] = {hx, hy + 1, 2 * zk};
-        nD1 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 7, oD1, nb, H, ok, a.pstride);
+        nD1 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 7, sD[pk][1][t], nb, H, ok, a.pstride);
       }
       if (core) {
         if (k >= z0) {
@@ -205,16 +208,9 @@ __global__ void __launch_bounds__(kThreads3d, 2) fused3d_kernel(const FusedArgs<
           a.out[1][on] = nA1n;
         }
       }
-      oC0 = C0n;
-      oC1 = C1n;
-      oD0 = D0n;
-      oD1 = D1n;
-      nA0 = nA0n;
-      nA1 = nA1n;
-      nB0 = nB0k;
-      nB1 = nB1k;
+      cur = nxt;
     }
-    __syncthreads();  // every read of this item's stage before the next item's prefetch
+    __syncthreads();  // the next item rewrites the shared tiles
   }
 }
 
@@ -240,12 +236,24 @@ __global__ void __launch_bounds__(32 * kFused2dWarps) fused2d_kernel(const Fused
     long long o = (long long)wrapi(y0 - 1, Ny) * Nx + x;
     C oV0 = ld(a.in[2] + o), oV1 = ld(a.in[3] + o);
     C nU0 = oV0, nU1 = oV1;  // placeholders: only feed values never stored
+    // the loads of row k: u0, v0, v1 at row k+1 and u1 at row k
+    auto load = [&](int k, C& u0, C& v0, C& v1, C& u1) {
+      const int yk = k < 0 ? k + Ny : k;
+      const int yn = k + 1 >= Ny ? k + 1 - Ny : k + 1;
+      const long long okk = (long long)yk * Nx + x, onn = (long long)yn * Nx + x;
+      u0 = ld(a.in[0] + onn);
+      v0 = ld(a.in[2] + onn);
+      v1 = ld(a.in[3] + onn);
+      u1 = ld(a.in[1] + okk);
+    };
+    C U0, V0n, V1n, U1;
+    load(y0 - 1, U0, V0n, V1n, U1);
     for (int k = y0 - 1; k < y1; ++k) {
       const int yk = k < 0 ? k + Ny : k;
       const int yn = k + 1 >= Ny ? k + 1 - Ny : k + 1;
       const long long ok = (long long)yk * Nx + x, on = (long long)yn * Nx + x;
-      const C U0 = ld(a.in[0] + on), V0n = ld(a.in[2] + on), V1n = ld(a.in[3] + on);
-      const C U1 = ld(a.in[1] + ok);
+      C pU0 = U0, pV0 = V0n, pV1 = V1n, pU1 = U1;  // next row, loaded while this one computes
+      if (k + 1 < y1) load(k + 1, pU0, pV0, pV1, pU1);
       // upper: u0(k+1) from v0(k+1) (x), v1(k+1), v1(k) (y); u1(k) from v1(k) (x), v0(k+1), v0(k) (y)
       C nU0n, nU1k;
       {
@@ -282,6 +290,10 @@ __global__ void __launch_bounds__(32 * kFused2dWarps) fused2d_kernel(const Fused
       oV1 = V1n;
       nU0 = nU0n;
       nU1 = nU1k;
+      U0 = pU0;
+      V0n = pV0;
+      V1n = pV1;
+      U1 = pU1;
     }
   }
 }
