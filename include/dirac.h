@@ -179,6 +179,44 @@ const char* dirac_last_error(const dirac_sim* sim);
 /* free all device memory of sim (NULL is ignored); synchronises its stream */
 void dirac_destroy(dirac_sim* sim);
 
+/*
+ * dirac_norm_noalloc: the value of dirac_norm for a state held in the
+ * caller's own device memory, computed without allocating any memory.
+ * The paper has no counterpart; this entry point exists for callers that
+ * cannot call cudaMalloc where they need the norm: a host framework that
+ * owns all device memory through its own pool and forbids other
+ * allocations, or a time-critical loop that cannot afford the implicit
+ * device synchronisation of cudaMalloc/cudaFree.  Such callers cannot hold a
+ * dirac_sim (dirac_create allocates), so this call takes the planes directly.
+ *
+ * planes: dims == 3 ? 8 : 4 device pointers, in the plane order of the
+ *   canonical layout (A0..D1 or u0..v1), each an N[0] x N[1] (x N[2]) array
+ *   [z][y][x] of double2 (DIRAC_FP64) or float2 (DIRAC_FP32), owned and kept
+ *   alive by the caller.  t is the time of the lower sheet (link factors of a
+ *   vector potential are taken at t - dt/2, as in dirac_norm); fields may be
+ *   NULL (only the vector potential matters for the functional).
+ * out_dev: caller-owned device memory for two doubles, written with
+ *   {E, sum |psi|^2}.  The call only enqueues work on cuda_stream (may be
+ *   NULL); synchronise that stream before reading out_dev.
+ * Scratch: the per-block partial sums go to one fixed array in the library's
+ *   device memory (8193 x 5 doubles, about 320 KiB, held by every GPU that
+ *   loads the library until the process exits).  Grids whose reduction needs
+ *   more than 8192 blocks, i.e. ceil(N[0]/32) * ceil(N[1]/8) > 8192, are
+ *   rejected with DIRAC_ERR_UNSUPPORTED before any device work.  Every call
+ *   shares that array and overwrites all of it that it reads, so nothing
+ *   needs clearing between calls; calls that overlap on the GPU (other
+ *   streams, or another host thread) race on it and must be serialised by
+ *   the caller.
+ * Set-up: the first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current); make that first call
+ *   before any stream capture.
+ * Returns DIRAC_ERR_INVALID for bad arguments, DIRAC_ERR_CUDA if the set-up
+ *   or a launch fails.
+ */
+dirac_status dirac_norm_noalloc(int dims, const int N[3], const double dx[3], double dt, double t,
+                                const dirac_fields* fields, dirac_precision precision,
+                                const void* const* planes, double* out_dev, void* cuda_stream);
+
 /* ABI version of this header */
 int dirac_version(void);
 
