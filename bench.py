@@ -116,9 +116,15 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def kernel_source_hash():
+KERNEL_SOURCES = {  # the files that determine each timed kernel's code
+    "step_fp32": ["step_fused.cu", "common.cuh", "kernels.cuh"],
+    "step_fp64": ["step_split.cu", "common.cuh", "kernels.cuh"],
+}
+
+
+def kernel_source_hash(kernel):
     h = hashlib.sha1()
-    for name in sorted(os.listdir(os.path.join(ROOT, "paper_1309_3452_gb300", "csrc"))):
+    for name in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_1309_3452_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]
@@ -133,7 +139,7 @@ def ncu_traffic(kernel, workload_name):
     except Exception:
         return None
     e = d.get(f"{kernel}@{workload_name}")
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 
