@@ -134,6 +134,13 @@ dirac_status dirac_set_spinor(dirac_sim* sim, const double* host);
    synchronises the stream. */
 dirac_status dirac_get_spinor(dirac_sim* sim, double* host);
 
+/* As dirac_set_spinor / dirac_get_spinor, but the canonical complex128
+   state lives in device memory owned by the caller (same layout; 16-byte
+   aligned).  Both only enqueue work on the simulation's stream; the caller's
+   buffer must stay valid until that work has run. */
+dirac_status dirac_set_spinor_device(dirac_sim* sim, const void* dev);
+dirac_status dirac_get_spinor_device(dirac_sim* sim, void* dev);
+
 /* Enqueue nsteps full time steps (both half-steps each; Eq. 3+3Ddis);
    t advances by nsteps*dt.  nsteps >= 0. */
 dirac_status dirac_step(dirac_sim* sim, long nsteps);

@@ -39,8 +39,16 @@ struct dirac_sim {
   int coef_mode = COEF_UNIFORM, link_mode = LINK_NONE;
   int step_X = 0;
   long long launches = 0;     // kernels launched so far
+  // CUDA graphs of kGraphSteps time steps, one per current-buffer parity
+  // (only for fields without time dependence: the launches bake their time)
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  void* graph_state[2] = {nullptr, nullptr};
+  int graph_disabled = 0;
+  int stepped = 0;            // a plain step has run (kernel one-time set-up done)
   std::string err;
 };
+
+static const long kGraphSteps = 64;
 
 static std::string g_create_error;
 
@@ -332,6 +340,8 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
 extern "C" void dirac_destroy(dirac_sim* s) {
   if (!s) return;
   cudaStreamSynchronize(s->stream);
+  for (int k = 0; k < 2; ++k)
+    if (s->graph[k]) cudaGraphExecDestroy(s->graph[k]);
   cudaFree(s->state);
   cudaFree(s->state_alt);
   cudaFree(s->staging);
@@ -383,18 +393,57 @@ extern "C" dirac_status dirac_get_spinor(dirac_sim* s, double* host) {
 
 static double sim_time(const dirac_sim* s) { return s->t0 + (double)s->k * s->dt; }
 
+extern "C" dirac_status dirac_set_spinor_device(dirac_sim* s, const void* dev) {
+  if (!s || !dev) return fail(s, DIRAC_ERR_INVALID, "NULL argument");
+  const double2* src = static_cast<const double2*>(dev);
+  for (int k = 0; k < s->np; ++k) {
+    const double2* plane = src + (long long)k * s->ncell;
+    if (s->prec == DIRAC_FP64) {
+      double2* dst = static_cast<double2*>(s->state) + (long long)k * s->pstride;
+      CK(s, cudaMemcpyAsync(dst, plane, (size_t)s->ncell * sizeof(double2), cudaMemcpyDeviceToDevice,
+                            s->stream));
+    } else {
+      launch_convert_in(plane, static_cast<float2*>(s->state) + (long long)k * s->pstride, s->ncell,
+                        s->stream);
+      s->launches += 1;
+      CK(s, cudaGetLastError());
+    }
+  }
+  return DIRAC_OK;
+}
+
+extern "C" dirac_status dirac_get_spinor_device(dirac_sim* s, void* dev) {
+  if (!s || !dev) return fail(s, DIRAC_ERR_INVALID, "NULL argument");
+  double2* dst = static_cast<double2*>(dev);
+  for (int k = 0; k < s->np; ++k) {
+    double2* plane = dst + (long long)k * s->ncell;
+    if (s->prec == DIRAC_FP64) {
+      const double2* src = static_cast<double2*>(s->state) + (long long)k * s->pstride;
+      CK(s, cudaMemcpyAsync(plane, src, (size_t)s->ncell * sizeof(double2), cudaMemcpyDeviceToDevice,
+                            s->stream));
+    } else {
+      launch_convert_out(static_cast<float2*>(s->state) + (long long)k * s->pstride, plane, s->ncell,
+                         s->stream);
+      s->launches += 1;
+      CK(s, cudaGetLastError());
+    }
+  }
+  return DIRAC_OK;
+}
+
+// n time steps with one launch sequence each, on stream st
 template <class P>
-static dirac_status step_split(dirac_sim* s, long n) {
+static dirac_status steps_split(dirac_sim* s, long n, cudaStream_t st) {
   for (long i = 0; i < n; ++i) {
     double t = sim_time(s);
     HalfStepArgs<P> up = half_args<P>(s, true, t);
     HalfStepArgs<P> lo = half_args<P>(s, false, t + s->dt / 2.0);
     if (s->dims == 3) {
-      launch_half_step<P, 3>(up, true, s->stream);
-      launch_half_step<P, 3>(lo, false, s->stream);
+      launch_half_step<P, 3>(up, true, st);
+      launch_half_step<P, 3>(lo, false, st);
     } else {
-      launch_half_step<P, 2>(up, true, s->stream);
-      launch_half_step<P, 2>(lo, false, s->stream);
+      launch_half_step<P, 2>(up, true, st);
+      launch_half_step<P, 2>(lo, false, st);
     }
     s->launches += 2;
     CK(s, cudaGetLastError());
@@ -404,11 +453,11 @@ static dirac_status step_split(dirac_sim* s, long n) {
 }
 
 template <class P>
-static dirac_status step_fused(dirac_sim* s, long n) {
+static dirac_status steps_fused(dirac_sim* s, long n, cudaStream_t st) {
   for (long i = 0; i < n; ++i) {
     FusedArgs<P> a = fused_args<P>(s, sim_time(s));
-    if (s->dims == 3) launch_fused<P, 3>(a, s->stream);
-    else launch_fused<P, 2>(a, s->stream);
+    if (s->dims == 3) launch_fused<P, 3>(a, st);
+    else launch_fused<P, 2>(a, st);
     s->launches += 1;
     CK(s, cudaGetLastError());
     std::swap(s->state, s->state_alt);
@@ -417,12 +466,80 @@ static dirac_status step_fused(dirac_sim* s, long n) {
   return DIRAC_OK;
 }
 
+static dirac_status steps_plain(dirac_sim* s, long n, cudaStream_t st) {
+  if (s->prec == DIRAC_FP64) return steps_split<F64>(s, n, st);
+  if (s->fused) return steps_fused<F32>(s, n, st);
+  return steps_split<F32>(s, n, st);
+}
+
+static bool time_dependent_fields(const dirac_sim* s) {
+  return (s->Vstatic && s->f.Vmod_amp != 0.0) || (s->f.Apw_amp != 0.0 && s->f.Apw_omega != 0.0);
+}
+
+// Capture kGraphSteps steps starting from the current buffer into a graph
+// (on a private stream, so the simulation's stream may be the legacy one).
+static dirac_status build_graph(dirac_sim* s, int slot) {
+  cudaStream_t cap;
+  CK(s, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  void* state0 = s->state;
+  long long k0 = s->k, l0 = s->launches;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+  dirac_status st = DIRAC_OK;
+  if (e == cudaSuccess) {
+    st = steps_plain(s, kGraphSteps, cap);
+    e = cudaStreamEndCapture(cap, &g);
+  }
+  // capturing did not run anything: restore the bookkeeping
+  s->k = k0;
+  s->launches = l0;
+  if (s->state != state0) std::swap(s->state, s->state_alt);
+  cudaStreamDestroy(cap);
+  if (e != cudaSuccess || st != DIRAC_OK || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    s->graph_disabled = 1;  // fall back to plain launches
+    return DIRAC_OK;
+  }
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    s->graph_disabled = 1;
+    return DIRAC_OK;
+  }
+  s->graph[slot] = ex;
+  s->graph_state[slot] = state0;
+  return DIRAC_OK;
+}
+
 extern "C" dirac_status dirac_step(dirac_sim* s, long nsteps) {
   if (!s) return fail(s, DIRAC_ERR_INVALID, "NULL sim");
   if (nsteps < 0) return fail(s, DIRAC_ERR_INVALID, "nsteps < 0");
-  if (s->prec == DIRAC_FP64) return step_split<F64>(s, nsteps);
-  if (s->fused) return step_fused<F32>(s, nsteps);
-  return step_split<F32>(s, nsteps);
+  const bool graphs = !s->graph_disabled && !time_dependent_fields(s) &&
+                      std::getenv("DIRAC_NO_GRAPHS") == nullptr;
+  if (graphs && !s->stepped && nsteps > kGraphSteps) {
+    dirac_status st = steps_plain(s, 1, s->stream);
+    if (st != DIRAC_OK) return st;
+    --nsteps;
+  }
+  s->stepped = 1;
+  while (graphs && nsteps >= kGraphSteps) {
+    int slot = (s->graph_state[0] == s->state) ? 0 : (s->graph_state[1] == s->state ? 1 : -1);
+    if (slot < 0) {
+      slot = s->graph[0] ? 1 : 0;
+      dirac_status st = build_graph(s, slot);
+      if (st != DIRAC_OK) return st;
+      if (s->graph_disabled) break;
+    }
+    CK(s, cudaGraphLaunch(s->graph[slot], s->stream));
+    s->launches += kGraphSteps * (s->fused ? 1 : 2);
+    s->k += kGraphSteps;
+    if (s->fused && (kGraphSteps & 1)) std::swap(s->state, s->state_alt);
+    nsteps -= kGraphSteps;
+  }
+  return steps_plain(s, nsteps, s->stream);
 }
 
 template <class P>

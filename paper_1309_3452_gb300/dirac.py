@@ -53,6 +53,8 @@ _lib.dirac_create.argtypes = [C.POINTER(_vp), C.c_int, C.POINTER(C.c_int), _dp, 
                               C.c_double, C.POINTER(Fields), C.c_int, C.c_uint, _vp]
 _lib.dirac_set_spinor.argtypes = [_vp, _dp]
 _lib.dirac_get_spinor.argtypes = [_vp, _dp]
+_lib.dirac_set_spinor_device.argtypes = [_vp, _vp]
+_lib.dirac_get_spinor_device.argtypes = [_vp, _vp]
 _lib.dirac_step.argtypes = [_vp, C.c_long]
 _lib.dirac_norm.argtypes = [_vp, _dp, _dp]
 _lib.dirac_partial_density.argtypes = [_vp, C.c_int, C.c_double, _dp]
@@ -68,7 +70,8 @@ _lib.dirac_version.restype = C.c_int
 _lib.dirac_kernel_launches.argtypes = [_vp]
 _lib.dirac_kernel_launches.restype = C.c_longlong
 
-for _name in ("dirac_create", "dirac_set_spinor", "dirac_get_spinor", "dirac_step", "dirac_norm",
+for _name in ("dirac_create", "dirac_set_spinor", "dirac_get_spinor", "dirac_set_spinor_device",
+              "dirac_get_spinor_device", "dirac_step", "dirac_norm",
               "dirac_partial_density", "dirac_get_time", "dirac_set_time"):
     getattr(_lib, _name).restype = C.c_int
 
@@ -147,6 +150,13 @@ class Sim:
     def set_spinor_ptr(self, host_ptr: int):
         """Canonical complex128 state at a raw host address (e.g. pinned memory)."""
         self._check(_lib.dirac_set_spinor(self._h, C.cast(C.c_void_p(host_ptr), _dp)))
+
+    def set_spinor_device(self, dev_ptr: int):
+        """Canonical complex128 state in device memory (e.g. a torch tensor's data_ptr())."""
+        self._check(_lib.dirac_set_spinor_device(self._h, _vp(dev_ptr)))
+
+    def get_spinor_device(self, dev_ptr: int):
+        self._check(_lib.dirac_get_spinor_device(self._h, _vp(dev_ptr)))
 
     def get_spinor(self):
         out = np.empty(self.prob.shape, np.complex128)

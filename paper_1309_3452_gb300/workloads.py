@@ -170,6 +170,40 @@ def gaussian_packet(prob: Problem, sigma: float, k0: Sequence[float], center: Se
     return out
 
 
+def gaussian_packet_torch(prob: Problem, sigma: float, k0: Sequence[float], center: Sequence[float],
+                          device, t: float = 0.0):
+    """The same packet as gaussian_packet, built plane by plane with torch in
+    complex128 on `device` (for grids whose host copy would be tens of GB).
+    Returns a tensor of shape (P, Nz, Ny, Nx)."""
+    import torch
+    dims = prob.dims
+    k = [float(v) for v in k0] + [0.0] * (3 - len(k0))
+    E = math.sqrt(prob.m ** 2 + k[0] ** 2 + k[1] ** 2 + (k[2] ** 2 if dims == 3 else 0.0))
+    w = continuum_spinor(dims, k, prob.m)
+    _, offs, _, comp = plane_tables(dims)
+    L = [prob.N[a] * prob.dx[a] for a in range(3 if dims == 3 else 2)]
+    nz = prob.N[2] if dims == 3 else 1
+    out = torch.empty(prob.shape, dtype=torch.complex128, device=device)
+    axes = [torch.arange(n, dtype=torch.float64, device=device) for n in (prob.N[0], prob.N[1], nz)]
+    for pl in range(prob.n_planes):
+        o = offs[pl]
+        r2 = torch.zeros((nz, prob.N[1], prob.N[0]), dtype=torch.float64, device=device)
+        phase = torch.zeros_like(r2)
+        for a in range(dims):
+            c = (axes[a] + 0.5 * o[a]) * prob.dx[a]
+            d = c - center[a]
+            d = d - L[a] * torch.round(d / L[a])
+            shape = [1, 1, 1]
+            shape[2 - a] = -1
+            r2 = r2 + (d * d).view(shape)
+            phase = phase + (k[a] * c).view(shape)
+        ts = sheet_time(prob, pl, t)
+        amp = torch.exp(-r2 / (2 * sigma * sigma))
+        out[pl] = complex(w[comp[pl]]) * torch.polar(amp, phase - E * ts)
+    out /= math.sqrt(float(torch.sum(torch.abs(out) ** 2)))
+    return out
+
+
 def random_state(prob: Problem, seed: int) -> np.ndarray:
     """Uniformly random complex values (PCG64), normalised to sum |psi|^2 = 1."""
     rng = np.random.default_rng(seed)
