@@ -146,6 +146,21 @@ dirac_status dirac_get_spinor_device(dirac_sim* sim, void* dev);
 dirac_status dirac_step(dirac_sim* sim, long nsteps);
 
 /*
+ * Advance several simulations by nsteps time steps each, together.  FP32
+ * simulations with time-independent fields (no modulated static potential,
+ * no moving plane wave; a static soft core or static array is not batched
+ * either) that share dims and field path run as ONE persistent launch of the
+ * fused kernel per time step: the work items of all of them (tile x level
+ * chunk) are dealt to the resident blocks together, so small grids fill the
+ * GPU jointly.  Other simulations are stepped one after another as by
+ * dirac_step.  The result of every simulation is identical, bit for bit, to
+ * stepping it alone.  All simulations must have been created with the same
+ * stream (else DIRAC_ERR_INVALID).  The call enqueues the work; its small
+ * argument tables are copied synchronously before it returns.
+ */
+dirac_status dirac_batch_step(dirac_sim* const* sims, int nsims, long nsteps);
+
+/*
  * Conserved functional of the stored state (Lemma of Sect. 2, Eq. EPM, and
  * Lemma of Sect. 3), written with every lower value G paired with the
  * difference part S_G of its own update:

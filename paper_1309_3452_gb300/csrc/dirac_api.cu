@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 #include <utility>
+#include <vector>
 #include <string>
 
 #include "../../include/dirac.h"
@@ -540,6 +541,120 @@ extern "C" dirac_status dirac_step(dirac_sim* s, long nsteps) {
     nsteps -= kGraphSteps;
   }
   return steps_plain(s, nsteps, s->stream);
+}
+
+static bool batchable(const dirac_sim* s) {
+  return s->fused && !time_dependent_fields(s) &&
+         (s->coef_mode == COEF_UNIFORM || s->coef_mode == COEF_STEP) &&
+         (s->link_mode == LINK_NONE || s->link_mode == LINK_CONST);
+}
+
+// one group: same dims and field path, all batchable
+static dirac_status batch_group(dirac_sim* const* g, int n, long nsteps) {
+  dirac_sim* s0 = g[0];
+  cudaStream_t st = s0->stream;
+  const size_t args_bytes = (size_t)2 * n * sizeof(FusedArgs<F32>);
+  const size_t first_bytes = (size_t)(n + 1) * sizeof(long long);
+  FusedArgs<F32>* h_args = new (std::nothrow) FusedArgs<F32>[2 * n];
+  long long* h_first = new (std::nothrow) long long[n + 1];
+  if (!h_args || !h_first) {
+    delete[] h_args;
+    delete[] h_first;
+    return fail(s0, DIRAC_ERR_OOM, "host allocation failed");
+  }
+  h_first[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    dirac_sim* s = g[i];
+    const int chunk = fused_chunk(s->dims, s->N);
+    for (int p = 0; p < 2; ++p) {
+      FusedArgs<F32> a = fused_args<F32>(s, sim_time(s));
+      a.chunk = chunk;
+      if (p == 1) {
+        for (int k = 0; k < 8; ++k) {  // the other buffer is the input after an odd step
+          typename F32::cplx* tmp = a.out[k];
+          a.out[k] = const_cast<typename F32::cplx*>(a.in[k]);
+          a.in[k] = tmp;
+        }
+      }
+      h_args[p * n + i] = a;
+    }
+    h_first[i + 1] = h_first[i] + fused_items(s->dims, s->N, chunk);
+  }
+  void* d = nullptr;
+  cudaError_t e = cudaMallocAsync(&d, args_bytes + first_bytes, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d, h_args, args_bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(static_cast<char*>(d) + args_bytes, h_first, first_bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host tables can be freed
+  const long long total = h_first[n];
+  delete[] h_args;
+  delete[] h_first;
+  if (e != cudaSuccess) {
+    if (d) cudaFreeAsync(d, st);
+    return cuda_fail(s0, e, "batch tables");
+  }
+  const FusedArgs<F32>* d_args = static_cast<const FusedArgs<F32>*>(d);
+  BatchArgs<F32> b;
+  b.first_item = reinterpret_cast<const long long*>(static_cast<char*>(d) + args_bytes);
+  b.nsims = n;
+  b.workers = 0;
+  for (long i = 0; i < nsteps; ++i) {
+    b.sims = d_args + (i & 1) * n;
+    if (s0->dims == 3)
+      launch_fused_batch<F32, 3>(b, total, s0->coef_mode, s0->link_mode, st);
+    else
+      launch_fused_batch<F32, 2>(b, total, s0->coef_mode, s0->link_mode, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      cudaFreeAsync(d, st);
+      return cuda_fail(s0, e, "batched fused launch");
+    }
+  }
+  cudaFreeAsync(d, st);
+  for (int i = 0; i < n; ++i) {
+    dirac_sim* s = g[i];
+    if (nsteps & 1) std::swap(s->state, s->state_alt);
+    s->k += nsteps;
+    s->stepped = 1;
+  }
+  g[0]->launches += nsteps;  // one launch per step serves the whole group
+  return DIRAC_OK;
+}
+
+extern "C" dirac_status dirac_batch_step(dirac_sim* const* sims, int nsims, long nsteps) {
+  if (!sims || nsims < 0 || nsteps < 0) return fail(nullptr, DIRAC_ERR_INVALID, "bad batch arguments");
+  for (int i = 0; i < nsims; ++i) {
+    if (!sims[i]) return fail(nullptr, DIRAC_ERR_INVALID, "NULL simulation in batch");
+    if (sims[i]->stream != sims[0]->stream)
+      return fail(sims[i], DIRAC_ERR_INVALID, "batched simulations must share one stream");
+    for (int j = 0; j < i; ++j)
+      if (sims[j] == sims[i]) return fail(sims[i], DIRAC_ERR_INVALID, "simulation listed twice");
+  }
+  if (nsims == 0 || nsteps == 0) return DIRAC_OK;
+  std::vector<int> done(nsims, 0);
+  std::vector<dirac_sim*> grp;
+  for (int i = 0; i < nsims; ++i) {
+    if (done[i]) continue;
+    dirac_sim* s = sims[i];
+    if (!batchable(s)) {
+      done[i] = 1;
+      dirac_status st = dirac_step(s, nsteps);
+      if (st != DIRAC_OK) return st;
+      continue;
+    }
+    grp.clear();
+    for (int j = i; j < nsims; ++j) {
+      dirac_sim* t = sims[j];
+      if (!done[j] && batchable(t) && t->dims == s->dims && t->coef_mode == s->coef_mode &&
+          t->link_mode == s->link_mode) {
+        grp.push_back(t);
+        done[j] = 1;
+      }
+    }
+    dirac_status st = batch_group(grp.data(), (int)grp.size(), nsteps);
+    if (st != DIRAC_OK) return st;
+  }
+  return DIRAC_OK;
 }
 
 template <class P>

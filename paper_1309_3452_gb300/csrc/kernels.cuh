@@ -42,6 +42,22 @@ constexpr int kCore = 30;          // interior lanes of a 32-lane strip
 template <class P, int DIMS>
 void launch_fused(const FusedArgs<P>& a, cudaStream_t s);
 
+// Several simulations (same dims and time-independent field modes) in one
+// persistent launch of the fused kernels.
+template <class P>
+struct BatchArgs {
+  const FusedArgs<P>* sims;      // device array, one entry per simulation (chunk set)
+  const long long* first_item;   // device array [nsims + 1]: prefix sums of the items
+  int nsims;
+  int workers;                   // set by the launcher
+};
+// levels per work item and number of items the fused kernels use for a grid
+int fused_chunk(int dims, const int N[3]);
+long long fused_items(int dims, const int N[3], int chunk);
+template <class P, int DIMS>
+void launch_fused_batch(const BatchArgs<P>& b, long long total_items, int coef_mode, int link_mode,
+                        cudaStream_t s);
+
 // Observables of the stored state: per-block FP64 partial sums of
 // [sum|psi|^2, Bx, By, Bz, sum_{beyond} |psi|^2] with
 // B_a = Re sum_lower conj(G) s_a d_a(G)  (E = naive + r_x Bx + r_y By + r_z Bz).

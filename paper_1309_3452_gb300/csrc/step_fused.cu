@@ -68,30 +68,48 @@ struct LevelLoad {
   C A0, A1, B0, B1, C0, C1, D0, D1;
 };
 
+// thread geometry inside the (3+1)D tile
+struct Thread3d {
+  int t, lx, ly;
+  int sxm, sxp, sym, syp;  // shared-memory slots of the x/y neighbours (clamped
+                           // at the tile edge: halo threads then read their own slot)
+};
+
+__device__ __forceinline__ Thread3d thread3d() {
+  Thread3d th;
+  th.t = threadIdx.x;
+  th.lx = th.t % TW;
+  th.ly = th.t / TW;
+  th.sxm = th.lx > 0 ? th.t - 1 : th.t;
+  th.sxp = th.lx < TW - 1 ? th.t + 1 : th.t;
+  th.sym = th.ly > 0 ? th.t - TW : th.t;
+  th.syp = th.ly < kSmemRows - 1 ? th.t + TW : th.t;
+  return th;
+}
+
+__host__ __device__ __forceinline__ long long items3d(const int (&N)[3], int chunk) {
+  return (long long)((N[0] + CX - 1) / CX) * ((N[1] + CY - 1) / CY) * ((N[2] + chunk - 1) / chunk);
+}
+
+// One work item (one tile over one chunk of z levels) of one simulation.
+// `a` may live in the constant bank (kernel parameter) or in shared memory.
 template <class P, int COEF, int LINK>
-__global__ void __launch_bounds__(kThreads3d, 2) fused3d_kernel(const FusedArgs<P> a) {
+__device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long item, const Thread3d& th,
+                                             unsigned char* smem_raw) {
   using C = typename P::cplx;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   // every tile is double-buffered by level parity: slot [k & 1] holds level k
   C (*sC)[2][kSlots] = reinterpret_cast<C (*)[2][kSlots]>(smem_raw);  // old C(k)
   C (*sD)[2][kSlots] = sC + 2;                                         // old D(k)
   C (*sB)[2][kSlots] = sC + 4;                                         // new B(k)
   C (*sA)[2][kSlots] = sC + 6;                                         // new A(k)
-
-  const int t = threadIdx.x;
-  const int lx = t % TW, ly = t / TW;
+  const int t = th.t, lx = th.lx, ly = th.ly;
+  const int sxm = th.sxm, sxp = th.sxp, sym = th.sym, syp = th.syp;
   const int Nx = a.N[0], Ny = a.N[1], Nz = a.N[2];
   const int tiles_x = (Nx + CX - 1) / CX;
   const long long tiles = (long long)tiles_x * ((Ny + CY - 1) / CY);
-  const long long items = tiles * ((Nz + a.chunk - 1) / a.chunk);
-  // shared-memory slots of this thread's x/y neighbours (clamped at the tile
-  // edge: halo threads then read their own slot, values never used)
-  const int sxm = lx > 0 ? t - 1 : t, sxp = lx < TW - 1 ? t + 1 : t;
-  const int sym = ly > 0 ? t - TW : t, syp = ly < kSmemRows - 1 ? t + TW : t;
   const bool iso = a.iso != 0;
   const long long nxy = (long long)Nx * Ny;
-
-  for (long long item = blockIdx.x; item < items; item += a.workers) {
+  {
     const long long chunk = item / tiles, tile = item - chunk * tiles;
     const int z0 = (int)chunk * a.chunk;
     const int z1 = min(Nz, z0 + a.chunk);
@@ -215,15 +233,69 @@ __global__ void __launch_bounds__(kThreads3d, 2) fused3d_kernel(const FusedArgs<
 }
 
 template <class P, int COEF, int LINK>
-__global__ void __launch_bounds__(32 * kFused2dWarps) fused2d_kernel(const FusedArgs<P> a) {
+__global__ void __launch_bounds__(kThreads3d, 2) fused3d_kernel(const FusedArgs<P> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Thread3d th = thread3d();
+  const long long items = items3d(a.N, a.chunk);
+  for (long long item = blockIdx.x; item < items; item += a.workers)
+    fused3d_item<P, COEF, LINK>(a, item, th, smem_raw);
+}
+
+// simulation of global item g: the last s with first[s] <= g
+__device__ __forceinline__ int find_sim(const long long* first, int nsims, long long g) {
+  int lo = 0, hi = nsims - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(first + mid) <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// copy one simulation's arguments into shared memory (nthreads cooperating)
+template <class P>
+__device__ __forceinline__ void copy_args(FusedArgs<P>* dst, const FusedArgs<P>* src, int tid,
+                                          int nthreads) {
+  static_assert(sizeof(FusedArgs<P>) % 4 == 0, "word copy");
+  const int* s = reinterpret_cast<const int*>(src);
+  int* d = reinterpret_cast<int*>(dst);
+  for (int i = tid; i < (int)(sizeof(FusedArgs<P>) / 4); i += nthreads) d[i] = __ldg(s + i);
+}
+
+// Several simulations in one persistent launch: global items are the
+// simulations' items back to back; each block copies the arguments of the
+// simulation its current item belongs to into shared memory.
+template <class P, int COEF, int LINK>
+__global__ void __launch_bounds__(kThreads3d, 2) fused3d_batch_kernel(const BatchArgs<P> b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ FusedArgs<P> sa;
+  const Thread3d th = thread3d();
+  const long long total = b.first_item[b.nsims];
+  int cur = -1;
+  for (long long g = blockIdx.x; g < total; g += b.workers) {
+    const int s = find_sim(b.first_item, b.nsims, g);
+    if (s != cur) {
+      __syncthreads();  // everyone is done with the previous arguments
+      copy_args(&sa, b.sims + s, th.t, kThreads3d);
+      __syncthreads();
+      cur = s;
+    }
+    fused3d_item<P, COEF, LINK>(sa, g - b.first_item[s], th, smem_raw);
+  }
+}
+
+__host__ __device__ __forceinline__ long long items2d(const int (&N)[3], int chunk) {
+  return (long long)((N[0] + kCore - 1) / kCore) * ((N[1] + chunk - 1) / chunk);
+}
+
+// One work item (one 32-cell strip over one chunk of rows) of one simulation,
+// processed by one warp.
+template <class P, int COEF, int LINK>
+__device__ __forceinline__ void fused2d_item(const FusedArgs<P>& a, long long item, int lane) {
   using C = typename P::cplx;
-  const int lane = threadIdx.x & 31;
-  const long long worker = (long long)blockIdx.x * kFused2dWarps + (threadIdx.x >> 5);
   const int Nx = a.N[0], Ny = a.N[1];
   const int strips = (Nx + kCore - 1) / kCore;
-  const long long items = (long long)strips * ((Ny + a.chunk - 1) / a.chunk);
   const bool iso = a.iso != 0;
-  for (long long item = worker; item < items; item += a.workers) {  // uniform per warp
+  {
     const long long chunk = item / strips;
     const int strip = (int)(item - chunk * strips);
     const int y0 = (int)chunk * a.chunk;
@@ -298,6 +370,34 @@ __global__ void __launch_bounds__(32 * kFused2dWarps) fused2d_kernel(const Fused
   }
 }
 
+template <class P, int COEF, int LINK>
+__global__ void __launch_bounds__(32 * kFused2dWarps) fused2d_kernel(const FusedArgs<P> a) {
+  const int lane = threadIdx.x & 31;
+  const long long worker = (long long)blockIdx.x * kFused2dWarps + (threadIdx.x >> 5);
+  const long long items = items2d(a.N, a.chunk);
+  for (long long item = worker; item < items; item += a.workers)  // uniform per warp
+    fused2d_item<P, COEF, LINK>(a, item, lane);
+}
+
+template <class P, int COEF, int LINK>
+__global__ void __launch_bounds__(32 * kFused2dWarps) fused2d_batch_kernel(const BatchArgs<P> b) {
+  __shared__ FusedArgs<P> sa[kFused2dWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long worker = (long long)blockIdx.x * kFused2dWarps + w;
+  const long long total = b.first_item[b.nsims];
+  int cur = -1;
+  for (long long g = worker; g < total; g += b.workers) {
+    const int s = find_sim(b.first_item, b.nsims, g);
+    if (s != cur) {
+      __syncwarp();
+      copy_args(&sa[w], b.sims + s, lane, 32);
+      __syncwarp();
+      cur = s;
+    }
+    fused2d_item<P, COEF, LINK>(sa[w], g - b.first_item[s], lane);
+  }
+}
+
 int sm_count() {
   int dev = 0, n = 0;
   cudaGetDevice(&dev);
@@ -334,16 +434,27 @@ int resident_blocks(K kernel, int threads, size_t smem = 0) {
   return (per_sm < 1 ? 1 : per_sm) * sm_count();
 }
 
-template <int COEF, int LINK>
-void launch3d(FusedArgs<F32> a, cudaStream_t s) {
-  auto k = fused3d_kernel<F32, COEF, LINK>;
-  static int resident = [&] {
+// resident workers of the fused kernels: blocks ((3+1)D) or warps ((2+1)D)
+template <class K>
+int workers3d(K k) {
+  static int r = [&] {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem3d);
     return resident_blocks(k, kThreads3d, kSmem3d);
   }();
-  long long tiles = (long long)((a.N[0] + CX - 1) / CX) * ((a.N[1] + CY - 1) / CY);
-  a.chunk = plan_chunk(tiles, a.N[2], resident, 4);
-  long long items = tiles * ((a.N[2] + a.chunk - 1) / a.chunk);
+  return r;
+}
+template <class K>
+int workers2d(K k) {
+  static int r = resident_blocks(k, 32 * kFused2dWarps) * kFused2dWarps;
+  return r;
+}
+
+template <int COEF, int LINK>
+void launch3d(FusedArgs<F32> a, cudaStream_t s) {
+  auto k = fused3d_kernel<F32, COEF, LINK>;
+  const int resident = workers3d(k);
+  a.chunk = fused_chunk(3, a.N);
+  const long long items = items3d(a.N, a.chunk);
   a.workers = (int)(items < resident ? items : resident);
   k<<<(unsigned)a.workers, kThreads3d, kSmem3d, s>>>(a);
 }
@@ -351,14 +462,29 @@ void launch3d(FusedArgs<F32> a, cudaStream_t s) {
 template <int COEF, int LINK>
 void launch2d(FusedArgs<F32> a, cudaStream_t s) {
   auto k = fused2d_kernel<F32, COEF, LINK>;
-  static int resident = resident_blocks(k, 32 * kFused2dWarps);
-  long long strips = (a.N[0] + kCore - 1) / kCore;
-  long long warps = (long long)resident * kFused2dWarps;
-  a.chunk = plan_chunk(strips, a.N[1], warps, 16);
-  long long items = strips * ((a.N[1] + a.chunk - 1) / a.chunk);
-  long long w = items < warps ? items : warps;
+  const int warps = workers2d(k);
+  a.chunk = fused_chunk(2, a.N);
+  const long long items = items2d(a.N, a.chunk);
+  const long long w = items < warps ? items : warps;
   a.workers = (int)w;
   k<<<(unsigned)((w + kFused2dWarps - 1) / kFused2dWarps), 32 * kFused2dWarps, 0, s>>>(a);
+}
+
+template <int COEF, int LINK>
+void launch3d_batch(BatchArgs<F32> b, long long total, cudaStream_t s) {
+  auto k = fused3d_batch_kernel<F32, COEF, LINK>;
+  const int resident = workers3d(k);
+  b.workers = (int)(total < resident ? total : resident);
+  k<<<(unsigned)b.workers, kThreads3d, kSmem3d, s>>>(b);
+}
+
+template <int COEF, int LINK>
+void launch2d_batch(BatchArgs<F32> b, long long total, cudaStream_t s) {
+  auto k = fused2d_batch_kernel<F32, COEF, LINK>;
+  const int warps = workers2d(k);
+  const long long w = total < warps ? total : warps;
+  b.workers = (int)w;
+  k<<<(unsigned)((w + kFused2dWarps - 1) / kFused2dWarps), 32 * kFused2dWarps, 0, s>>>(b);
 }
 
 template <int DIMS, int COEF, int LINK>
@@ -377,7 +503,46 @@ void dispatch(const FusedArgs<F32>& a, cudaStream_t s) {
   return launch_dims<DIMS, COEF_STEP, LINK_CONST>(a, s);
 }
 
+template <int DIMS, int COEF, int LINK>
+void batch_dims(const BatchArgs<F32>& b, long long total, cudaStream_t s) {
+  if (DIMS == 3) launch3d_batch<COEF, LINK>(b, total, s);
+  else launch2d_batch<COEF, LINK>(b, total, s);
+}
+
 }  // namespace
+
+int fused_chunk(int dims, const int N[3]) {
+  if (dims == 3) {
+    const int resident = workers3d(fused3d_kernel<F32, COEF_UNIFORM, LINK_NONE>);
+    const long long tiles = (long long)((N[0] + CX - 1) / CX) * ((N[1] + CY - 1) / CY);
+    return plan_chunk(tiles, N[2], resident, 4);
+  }
+  const int warps = workers2d(fused2d_kernel<F32, COEF_UNIFORM, LINK_NONE>);
+  const long long strips = (N[0] + kCore - 1) / kCore;
+  return plan_chunk(strips, N[1], warps, 16);
+}
+
+long long fused_items(int dims, const int N[3], int chunk) {
+  const int n[3] = {N[0], N[1], N[2]};
+  return dims == 3 ? items3d(n, chunk) : items2d(n, chunk);
+}
+
+template <>
+void launch_fused_batch<F32, 3>(const BatchArgs<F32>& b, long long total, int coef, int link,
+                                cudaStream_t s) {
+  if (coef == COEF_UNIFORM && link == LINK_NONE) return batch_dims<3, COEF_UNIFORM, LINK_NONE>(b, total, s);
+  if (coef == COEF_STEP && link == LINK_NONE) return batch_dims<3, COEF_STEP, LINK_NONE>(b, total, s);
+  if (coef == COEF_UNIFORM && link == LINK_CONST) return batch_dims<3, COEF_UNIFORM, LINK_CONST>(b, total, s);
+  return batch_dims<3, COEF_STEP, LINK_CONST>(b, total, s);
+}
+template <>
+void launch_fused_batch<F32, 2>(const BatchArgs<F32>& b, long long total, int coef, int link,
+                                cudaStream_t s) {
+  if (coef == COEF_UNIFORM && link == LINK_NONE) return batch_dims<2, COEF_UNIFORM, LINK_NONE>(b, total, s);
+  if (coef == COEF_STEP && link == LINK_NONE) return batch_dims<2, COEF_STEP, LINK_NONE>(b, total, s);
+  if (coef == COEF_UNIFORM && link == LINK_CONST) return batch_dims<2, COEF_UNIFORM, LINK_CONST>(b, total, s);
+  return batch_dims<2, COEF_STEP, LINK_CONST>(b, total, s);
+}
 
 template <>
 void launch_fused<F32, 3>(const FusedArgs<F32>& a, cudaStream_t s) {

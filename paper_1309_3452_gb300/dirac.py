@@ -56,6 +56,7 @@ _lib.dirac_get_spinor.argtypes = [_vp, _dp]
 _lib.dirac_set_spinor_device.argtypes = [_vp, _vp]
 _lib.dirac_get_spinor_device.argtypes = [_vp, _vp]
 _lib.dirac_step.argtypes = [_vp, C.c_long]
+_lib.dirac_batch_step.argtypes = [C.POINTER(_vp), C.c_int, C.c_long]
 _lib.dirac_norm.argtypes = [_vp, _dp, _dp]
 _lib.dirac_partial_density.argtypes = [_vp, C.c_int, C.c_double, _dp]
 _lib.dirac_get_time.argtypes = [_vp, _dp]
@@ -71,7 +72,7 @@ _lib.dirac_kernel_launches.argtypes = [_vp]
 _lib.dirac_kernel_launches.restype = C.c_longlong
 
 for _name in ("dirac_create", "dirac_set_spinor", "dirac_get_spinor", "dirac_set_spinor_device",
-              "dirac_get_spinor_device", "dirac_step", "dirac_norm",
+              "dirac_get_spinor_device", "dirac_step", "dirac_batch_step", "dirac_norm",
               "dirac_partial_density", "dirac_get_time", "dirac_set_time"):
     getattr(_lib, _name).restype = C.c_int
 
@@ -111,6 +112,16 @@ def _current_stream():
     except Exception:
         pass
     return None
+
+
+def batch_step(sims, nsteps):
+    """Advance several Sim objects together (dirac_batch_step)."""
+    if not sims:
+        return
+    arr = (_vp * len(sims))(*[s._h for s in sims])
+    rc = _lib.dirac_batch_step(arr, len(sims), int(nsteps))
+    if rc != OK:
+        raise DiracError(rc, _lib.dirac_last_error(sims[0]._h).decode())
 
 
 def state_bytes(dims, N, precision):

@@ -1,0 +1,199 @@
+"""Serving loop: continuous batching of many simulations on one GPU.
+
+Requests (a grid, a mass, an optional Klein step, an initial packet and a
+number of time steps) arrive over time.  The server admits a request as soon
+as it has arrived and its device state fits the HBM budget next to the
+simulations already resident, keeps every admitted state resident until its
+steps are done, and advances all resident simulations together with
+dirac_batch_step in quanta of at most `quantum` steps (shortened so the
+request that finishes first finishes exactly).  Between quanta finished
+requests leave (their conserved functional is read and checked) and waiting
+ones join.  Latency = finish - arrival on the wall clock.
+
+The stepping, the norms and the state set-up all run in libdirac; this
+module only schedules.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import math
+import statistics
+import time
+from typing import List, Optional
+
+import numpy as np
+
+from . import dirac as D
+from . import workloads as W
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds after the start of the stream
+    prob: W.Problem
+    sigma: float
+    k0: tuple
+    center: tuple
+    steps: int
+    precision: int = D.FP32
+
+    @property
+    def lups(self) -> float:
+        return float(self.prob.cells) * self.steps
+
+
+def make_requests(n: int, seed: int = 0, rate: float = 1.0, max_side_3d: int = 384,
+                  max_side_2d: int = 4096, min_steps: int = 100, max_steps: int = 5000) -> List[Request]:
+    """Seeded request stream: Poisson arrivals with the given rate (1/s); each
+    request is (2+1)D with probability 1/2 (side ~ U{64..max_side_2d}) else
+    (3+1)D (side ~ U{32..max_side_3d}); m ~ U[0,1]; a Klein step along x
+    with probability 1/2; steps ~ U{min_steps..max_steps}; packet sigma =
+    side/8 at a quarter of the box (Klein) or the centre, k0 as the (3+1)D
+    workload (u*d, d uniform on the sphere, u ~ U[0,1])."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate)
+        dims = 2 if rng.random() < 0.5 else 3
+        side = int(rng.integers(64, max_side_2d + 1)) if dims == 2 else int(rng.integers(32, max_side_3d + 1))
+        m = float(rng.random())
+        klein = rng.random() < 0.5
+        steps = int(rng.integers(min_steps, max_steps + 1))
+        d = rng.standard_normal(3)
+        k0 = tuple(float(v) for v in rng.random() * d / np.linalg.norm(d))
+        N = (side, side, side) if dims == 3 else (side, side, 1)
+        fields = W.Fields()
+        if klein:
+            E = math.sqrt(m * m + k0[0] ** 2)
+            fields = W.Fields(step_axis=0, step_x0=side / 2.0 + 0.25, step_V=2.0 * E + m)
+        prob = W.Problem(dims, N, (1.0, 1.0, 1.0), 0.9 * W.stability_limit(dims), m, fields)
+        c = side / 4.0 if klein else side / 2.0
+        center = (c, side / 2.0, side / 2.0)
+        out.append(Request(i, t, prob, side / 8.0, k0[:dims], center[:dims], steps))
+    return out
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    arrival: float
+    admitted: float
+    finished: float
+    lups: float
+    E0: float
+    E1: float
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+class Server:
+    def __init__(self, hbm_budget: int, quantum: int = 100, stream=None, device="cuda"):
+        import torch
+        self.torch = torch
+        self.budget = int(hbm_budget)
+        self.quantum = int(quantum)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.device = device
+
+    def _admit(self, req: Request):
+        torch = self.torch
+        with torch.cuda.stream(self.stream):
+            psi = W.gaussian_packet_torch(req.prob, req.sigma, req.k0, req.center, self.device)
+        sim = D.Sim(req.prob, req.precision, stream=self.stream.cuda_stream)
+        sim.set_spinor_device(psi.data_ptr())
+        E0, _ = sim.norm()  # synchronises: psi may be released
+        del psi
+        return sim, E0
+
+    def run(self, requests: List[Request], log=None) -> dict:
+        torch = self.torch
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        resident = []  # [req, sim, remaining, admitted, E0, bytes]
+        used = 0
+        results: List[Result] = []
+        launches = 0
+        t0 = time.perf_counter()
+        now = lambda: time.perf_counter() - t0
+        while pending or resident:
+            # admit every arrived request that fits
+            while pending and pending[0].arrival <= now():
+                req = pending[0]
+                need = D.state_bytes(req.prob.dims, req.prob.N, req.precision)
+                if need > self.budget:
+                    raise ValueError(f"request {req.rid} needs {need} B > budget {self.budget} B")
+                if used + need > self.budget:
+                    break
+                pending.popleft()
+                sim, E0 = self._admit(req)
+                resident.append([req, sim, req.steps, now(), E0, need])
+                used += need
+            if not resident:
+                if pending:
+                    time.sleep(max(0.0, min(0.05, pending[0].arrival - now())))
+                continue
+            q = min(self.quantum, min(r[2] for r in resident))
+            sims = [r[1] for r in resident]
+            before = sum(s.launches for s in sims)
+            D.batch_step(sims, q)
+            launches += sum(s.launches for s in sims) - before
+            for r in resident:
+                r[2] -= q
+            done = [r for r in resident if r[2] == 0]
+            if done:
+                for r in done:
+                    req, sim, _, adm, E0, need = r
+                    E1, _ = sim.norm()  # synchronises the stream
+                    results.append(Result(req.rid, req.arrival, adm, now(), req.lups, E0, E1))
+                    sim.close()
+                    used -= need
+                    if log:
+                        log(f"done {req.rid}: {req.prob.dims}D N={req.prob.N[0]} steps={req.steps} "
+                            f"latency {results[-1].latency:.2f}s")
+                resident = [r for r in resident if r[2] > 0]
+            else:
+                self.stream.synchronize()
+        makespan = now()
+        lat = sorted(r.latency for r in results)
+        total = sum(r.lups for r in results)
+        drift = max(abs(r.E1 - r.E0) / abs(r.E0) for r in results)
+        return {"requests": len(results), "makespan_s": makespan, "glups": total / makespan / 1e9,
+                "p50_s": percentile(lat, 50), "p99_s": percentile(lat, 99), "mean_s": statistics.mean(lat),
+                "max_E_drift": drift, "gpu_launches": launches, "total_lups": total,
+                "results": results}
+
+
+def percentile(sorted_vals, p):
+    if not sorted_vals:
+        return float("nan")
+    k = (len(sorted_vals) - 1) * p / 100.0
+    lo, hi = math.floor(k), math.ceil(k)
+    return sorted_vals[lo] + (sorted_vals[hi] - sorted_vals[lo]) * (k - lo)
+
+
+def plain_fp64_glups(requests: List[Request], device="cuda") -> float:
+    """The plain path: each request alone, FP64, one simulation per launch
+    sequence (no batching), back to back; site updates per second."""
+    import torch
+    total, t = 0.0, 0.0
+    stream = torch.cuda.Stream()
+    for req in requests:
+        with torch.cuda.stream(stream):
+            psi = W.gaussian_packet_torch(req.prob, req.sigma, req.k0, req.center, device)
+        with D.Sim(req.prob, D.FP64, stream=stream.cuda_stream) as sim:
+            sim.set_spinor_device(psi.data_ptr())
+            sim.norm()
+            del psi
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sim.step(req.steps)
+            sim.norm()
+            b.record(stream)
+            b.synchronize()
+            t += a.elapsed_time(b) / 1e3
+            total += req.lups
+    return total / t / 1e9

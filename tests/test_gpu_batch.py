@@ -1,0 +1,101 @@
+"""Batched stepping and the serving loop.
+
+* dirac_batch_step packs simulations of different sizes, masses and fields
+  into one persistent launch per time step; every simulation's result must
+  equal, bit for bit, the result of stepping it alone.
+* The serving loop admits requests as they arrive and HBM allows, batches
+  the resident ones and retires them; each result keeps E to FP32 accuracy.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1309_3452_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def D():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1309_3452_gb300 import dirac
+    return dirac
+
+
+def mix():
+    r3 = 0.9 * W.stability_limit(3)
+    r2 = 0.9 * W.stability_limit(2)
+    return [
+        (W.Problem(3, (40, 36, 30), (1.0, 1.0, 1.0), r3, 0.7), 0),
+        (W.Problem(3, (17, 23, 11), (1.0, 1.0, 1.0), r3, 0.2), 0),
+        (W.Problem(3, (64, 64, 64), (1.0, 1.0, 1.0), r3, 1.0,
+                   W.Fields(step_axis=0, step_x0=32.25, step_V=1.3)), 0),
+        (W.Problem(3, (33, 29, 21), (1.0, 1.0, 1.0), r3, 0.4,
+                   W.Fields(step_axis=2, step_x0=8.25, step_V=-0.7)), 0),
+        (W.Problem(2, (130, 97, 1), (1.0, 1.0, 1.0), r2, 0.3), 0),
+        (W.Problem(2, (64, 64, 1), (1.0, 1.0, 1.0), r2, 0.0,
+                   W.Fields(step_axis=0, step_x0=32.25, step_V=0.6)), 0),
+        (W.Problem(2, (301, 45, 1), (1.0, 1.0, 1.0), r2, 0.9), 0),
+        (W.Problem(3, (20, 20, 20), (1.0, 1.0, 1.0), r3, 0.5, W.Fields(q=1.0, A_const=(0.2, 0.1, 0.0))), 0),
+        (W.Problem(3, (19, 18, 17), (1.0, 1.0, 1.0), r3, 0.5), 1),   # FP64: stepped alone
+        (W.Problem(2, (40, 40, 1), (1.0, 1.0, 1.0), r2, 0.5,         # general field path: alone
+                   W.Fields(sc_Z=1.0, sc_a=1.0, sc_center=(20.0, 20.0, 0.0))), 0),
+    ]
+
+
+def test_batch_equals_alone_bitwise(D):
+    probs = mix()
+    states = [W.random_state(p, 100 + i) for i, (p, _) in enumerate(probs)]
+    alone = []
+    for (p, prec), psi in zip(probs, states):
+        with D.Sim(p, D.FP64 if prec else D.FP32) as s:
+            s.set_spinor(psi)
+            s.step(23)
+            s.step(40)
+            alone.append(s.get_spinor())
+    sims = []
+    try:
+        for (p, prec), psi in zip(probs, states):
+            s = D.Sim(p, D.FP64 if prec else D.FP32)
+            s.set_spinor(psi)
+            sims.append(s)
+        D.batch_step(sims, 23)
+        D.batch_step(sims[::-1], 40)  # another order, odd then even step counts
+        for s, want in zip(sims, alone):
+            assert abs(s.time - 63 * s.prob.dt) < 1e-12
+            assert np.array_equal(s.get_spinor(), want)
+    finally:
+        for s in sims:
+            s.close()
+
+
+def test_batch_rejects_mixed_streams_and_duplicates(D):
+    import torch
+    p = W.Problem(2, (32, 32, 1), (1.0, 1.0, 1.0), 0.5, 0.1)
+    st = torch.cuda.Stream()
+    a = D.Sim(p, D.FP32)
+    b = D.Sim(p, D.FP32, stream=st.cuda_stream)
+    try:
+        with pytest.raises(D.DiracError):
+            D.batch_step([a, b], 3)
+        with pytest.raises(D.DiracError):
+            D.batch_step([a, a], 3)
+    finally:
+        a.close()
+        b.close()
+
+
+def test_serving_loop_small_stream(D):
+    from paper_1309_3452_gb300 import serve
+    reqs = serve.make_requests(12, seed=3, rate=20.0, max_side_3d=48, max_side_2d=256,
+                               min_steps=20, max_steps=200)
+    srv = serve.Server(hbm_budget=2 << 30, quantum=50)
+    out = srv.run(reqs)
+    assert out["requests"] == len(reqs)
+    assert out["max_E_drift"] < 1e-6
+    assert out["p99_s"] >= out["p50_s"] > 0.0
+    for r in out["results"]:
+        assert r.finished >= r.admitted >= r.arrival - 1e-9
