@@ -197,13 +197,68 @@ def run_reference(args, prob, psi, n, desc, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def run_serve(args, rank, world):
+    """Serving stream: seeded Poisson requests of mixed (2+1)D / (3+1)D sizes,
+    masses, Klein steps and step counts, FP32, admitted by free HBM and
+    continuously batched (paper_1309_3452_gb300/serve.py)."""
+    import torch
+    from paper_1309_3452_gb300 import serve
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.6 * free)
+    # calibration: a burst (all arrive at t = 0) of the stream's first requests
+    cal = serve.make_requests(12, seed=args.seed, rate=1e9)
+    srv = serve.Server(budget, quantum=args.quantum)
+    c = srv.run(cal)
+    glups_sat = c["glups"]
+    stream = serve.make_requests(args.requests, seed=args.seed, rate=1.0)
+    mean_lups = sum(r.lups for r in stream) / len(stream)
+    rate = 0.8 * glups_sat * 1e9 / mean_lups
+    reqs = serve.make_requests(args.requests, seed=args.seed, rate=rate)
+    with Clocks(local) as clk:
+        out = srv.run(reqs)
+    # the plain FP64 path (one simulation per launch sequence) on a subsample
+    sub = []
+    for r in reqs[:8]:
+        r2 = serve.Request(r.rid, 0.0, r.prob, r.sigma, r.k0, r.center, min(r.steps, 200))
+        sub.append(r2)
+    fp64 = serve.plain_fp64_glups(sub)
+    res = {"metric": METRIC, "value": out["glups"], "unit": "GLUPS", "n_gpus": world,
+           "steps": out["requests"], "warmup": 12, "ms_per_step": 1000.0 * out["makespan_s"] / out["requests"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": "serving stream: seeded Poisson arrivals; each request (2+1)D side "
+                                  "U{64..4096} or (3+1)D side U{32..384} (p = 1/2), m ~ U[0,1], Klein step "
+                                  "p = 1/2, 100..5000 steps, FP32; admitted by free HBM, continuously "
+                                  "batched in quanta",
+                      "requests": out["requests"], "seed": args.seed, "rate_per_s": rate,
+                      "rate_rule": "0.8 x (burst-measured GLUPS / mean site updates per request)",
+                      "burst_glups": glups_sat, "quantum_steps": args.quantum, "hbm_budget_bytes": budget,
+                      "parallelism": f"replicas x{world}"},
+           "serving": {"p50_latency_s": out["p50_s"], "p99_latency_s": out["p99_s"],
+                       "mean_latency_s": out["mean_s"], "makespan_s": out["makespan_s"],
+                       "max_E_rel_drift": out["max_E_drift"], "total_site_updates": out["total_lups"]},
+           "fp64_plain": {"value": fp64, "unit": "GLUPS",
+                          "sample": "the stream's first 8 requests, min(steps, 200) each, one FP64 "
+                                    "simulation at a time"},
+           "ratio_served_fp32_vs_plain_fp64": out["glups"] / fp64,
+           "gpu_launches": out["gpu_launches"], "clocks": clk.summary(), "roofline": None,
+           "cpu_baseline": None, "e2e": None}
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="3d128", choices=["3d128", "3d512", "2d4096", "2d64"])
+    ap.add_argument("--workload", default="3d128", choices=["3d128", "3d512", "2d4096", "2d64", "serve"])
+    ap.add_argument("--requests", type=int, default=40, help="serve: requests in the stream")
+    ap.add_argument("--quantum", type=int, default=100, help="serve: steps per batching quantum")
+    ap.add_argument("--seed", type=int, default=0, help="serve: request stream seed")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison line")
@@ -214,6 +269,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload == "serve":
+        return run_serve(args, rank, world)
     prob, psi, n, desc = workload(args.workload)
 
     if args.impl == "reference":
