@@ -156,7 +156,8 @@ dirac_status dirac_step(dirac_sim* sim, long nsteps);
  * dirac_step.  The result of every simulation is identical, bit for bit, to
  * stepping it alone.  All simulations must have been created with the same
  * stream (else DIRAC_ERR_INVALID).  The call enqueues the work; its small
- * argument tables are copied synchronously before it returns.
+ * argument tables are copied synchronously before it returns.  On failure
+ * dirac_last_error(NULL) describes the cause.
  */
 dirac_status dirac_batch_step(dirac_sim* const* sims, int nsims, long nsteps);
 

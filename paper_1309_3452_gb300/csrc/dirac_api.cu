@@ -621,7 +621,20 @@ static dirac_status batch_group(dirac_sim* const* g, int n, long nsteps) {
   return DIRAC_OK;
 }
 
+static dirac_status batch_step_impl(dirac_sim* const* sims, int nsims, long nsteps);
+
 extern "C" dirac_status dirac_batch_step(dirac_sim* const* sims, int nsims, long nsteps) {
+  g_create_error.clear();
+  dirac_status st = batch_step_impl(sims, nsims, nsteps);
+  if (st != DIRAC_OK && g_create_error.empty() && sims) {
+    // report the failing simulation's message through dirac_last_error(NULL)
+    for (int i = 0; i < nsims; ++i)
+      if (sims[i] && !sims[i]->err.empty()) g_create_error = sims[i]->err;
+  }
+  return st;
+}
+
+static dirac_status batch_step_impl(dirac_sim* const* sims, int nsims, long nsteps) {
   if (!sims || nsims < 0 || nsteps < 0) return fail(nullptr, DIRAC_ERR_INVALID, "bad batch arguments");
   for (int i = 0; i < nsims; ++i) {
     if (!sims[i]) return fail(nullptr, DIRAC_ERR_INVALID, "NULL simulation in batch");

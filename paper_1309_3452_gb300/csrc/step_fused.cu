@@ -434,25 +434,27 @@ int resident_blocks(K kernel, int threads, size_t smem = 0) {
   return (per_sm < 1 ? 1 : per_sm) * sm_count();
 }
 
-// resident workers of the fused kernels: blocks ((3+1)D) or warps ((2+1)D)
-template <class K>
-int workers3d(K k) {
-  static int r = [&] {
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem3d);
-    return resident_blocks(k, kThreads3d, kSmem3d);
+// resident workers of the fused kernels: blocks ((3+1)D) or warps ((2+1)D);
+// computed once per kernel (the template argument is the kernel itself), the
+// (3+1)D kernels also get their dynamic shared-memory limit raised once
+template <auto K>
+int workers3d() {
+  static int r = [] {
+    cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem3d);
+    return resident_blocks(K, kThreads3d, kSmem3d);
   }();
   return r;
 }
-template <class K>
-int workers2d(K k) {
-  static int r = resident_blocks(k, 32 * kFused2dWarps) * kFused2dWarps;
+template <auto K>
+int workers2d() {
+  static int r = resident_blocks(K, 32 * kFused2dWarps) * kFused2dWarps;
   return r;
 }
 
 template <int COEF, int LINK>
 void launch3d(FusedArgs<F32> a, cudaStream_t s) {
   auto k = fused3d_kernel<F32, COEF, LINK>;
-  const int resident = workers3d(k);
+  const int resident = workers3d<fused3d_kernel<F32, COEF, LINK>>();
   a.chunk = fused_chunk(3, a.N);
   const long long items = items3d(a.N, a.chunk);
   a.workers = (int)(items < resident ? items : resident);
@@ -462,7 +464,7 @@ void launch3d(FusedArgs<F32> a, cudaStream_t s) {
 template <int COEF, int LINK>
 void launch2d(FusedArgs<F32> a, cudaStream_t s) {
   auto k = fused2d_kernel<F32, COEF, LINK>;
-  const int warps = workers2d(k);
+  const int warps = workers2d<fused2d_kernel<F32, COEF, LINK>>();
   a.chunk = fused_chunk(2, a.N);
   const long long items = items2d(a.N, a.chunk);
   const long long w = items < warps ? items : warps;
@@ -473,7 +475,7 @@ void launch2d(FusedArgs<F32> a, cudaStream_t s) {
 template <int COEF, int LINK>
 void launch3d_batch(BatchArgs<F32> b, long long total, cudaStream_t s) {
   auto k = fused3d_batch_kernel<F32, COEF, LINK>;
-  const int resident = workers3d(k);
+  const int resident = workers3d<fused3d_batch_kernel<F32, COEF, LINK>>();
   b.workers = (int)(total < resident ? total : resident);
   k<<<(unsigned)b.workers, kThreads3d, kSmem3d, s>>>(b);
 }
@@ -481,7 +483,7 @@ void launch3d_batch(BatchArgs<F32> b, long long total, cudaStream_t s) {
 template <int COEF, int LINK>
 void launch2d_batch(BatchArgs<F32> b, long long total, cudaStream_t s) {
   auto k = fused2d_batch_kernel<F32, COEF, LINK>;
-  const int warps = workers2d(k);
+  const int warps = workers2d<fused2d_batch_kernel<F32, COEF, LINK>>();
   const long long w = total < warps ? total : warps;
   b.workers = (int)w;
   k<<<(unsigned)((w + kFused2dWarps - 1) / kFused2dWarps), 32 * kFused2dWarps, 0, s>>>(b);
@@ -513,11 +515,11 @@ void batch_dims(const BatchArgs<F32>& b, long long total, cudaStream_t s) {
 
 int fused_chunk(int dims, const int N[3]) {
   if (dims == 3) {
-    const int resident = workers3d(fused3d_kernel<F32, COEF_UNIFORM, LINK_NONE>);
+    const int resident = workers3d<fused3d_kernel<F32, COEF_UNIFORM, LINK_NONE>>();
     const long long tiles = (long long)((N[0] + CX - 1) / CX) * ((N[1] + CY - 1) / CY);
     return plan_chunk(tiles, N[2], resident, 4);
   }
-  const int warps = workers2d(fused2d_kernel<F32, COEF_UNIFORM, LINK_NONE>);
+  const int warps = workers2d<fused2d_kernel<F32, COEF_UNIFORM, LINK_NONE>>();
   const long long strips = (N[0] + kCore - 1) / kCore;
   return plan_chunk(strips, N[1], warps, 16);
 }

@@ -121,7 +121,7 @@ def batch_step(sims, nsteps):
     arr = (_vp * len(sims))(*[s._h for s in sims])
     rc = _lib.dirac_batch_step(arr, len(sims), int(nsteps))
     if rc != OK:
-        raise DiracError(rc, _lib.dirac_last_error(sims[0]._h).decode())
+        raise DiracError(rc, _lib.dirac_last_error(None).decode())
 
 
 def state_bytes(dims, N, precision):
