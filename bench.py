@@ -45,8 +45,15 @@ def workload(name):
         desc = ("(3+1)D 128^3 periodic, m=1, no fields, Gaussian packet sigma=10 at the centre, "
                 "seeded k0 (|k0|<=1), dt=0.9/sqrt(3), 1000 time steps + E per step")
     elif name == "3d512":
-        prob, psi, n = W.workload_3d(N=512, steps=200, sigma=24.0)
+        prob, _, n = W.workload_3d(N=512, steps=200, sigma=24.0)
+        psi = ("device", 24.0, tuple(W.random_k0(0)), (256.0, 256.0, 256.0))
         desc = "(3+1)D 512^3 periodic, m=1, no fields, packet sigma=24, 200 time steps + E per step"
+    elif name == "3d512laser":
+        prob, _, _ = W.workload_laser(N=512, steps=2000)
+        n = 100
+        psi = ("device", 24.0, tuple(W.random_k0(1)), (256.0, 256.0, 256.0))
+        desc = ("(3+1)D 512^3, m=1, soft core -1/sqrt(|x-c|^2+1) at the centre + A_x = 0.5 cos(2 pi z/64 - "
+                "omega t), packet sigma=24 seeded k0; 100 of the workload's 2000 time steps + E per step")
     elif name == "2d4096":
         prob, psi, n = W.workload_klein(N=4096, steps=500)
         desc = ("(2+1)D 4096^2 Klein step (V0 = 2E+m at x0 = N/2+1/4), m=0.2, packet sigma=40, "
@@ -255,7 +262,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="3d128", choices=["3d128", "3d512", "2d4096", "2d64", "serve"])
+    ap.add_argument("--workload", default="3d128", choices=["3d128", "3d512", "3d512laser", "2d4096", "2d64", "serve"])
     ap.add_argument("--requests", type=int, default=40, help="serve: requests in the stream")
     ap.add_argument("--quantum", type=int, default=100, help="serve: steps per batching quantum")
     ap.add_argument("--seed", type=int, default=0, help="serve: request stream seed")
@@ -296,10 +303,18 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    on_device = isinstance(psi, tuple)
     with torch.cuda.stream(stream):
         sim = D.Sim(prob, prec, stream=stream.cuda_stream)
-    sim.set_spinor(psi)
+        if on_device:  # built on the GPU: the host copy would be tens of GB
+            from paper_1309_3452_gb300 import workloads as W
+            dpsi = W.gaussian_packet_torch(prob, psi[1], psi[2], psi[3], "cuda")
+            sim.set_spinor_device(dpsi.data_ptr())
+        else:
+            sim.set_spinor(psi)
     E_start, _ = sim.norm()
+    if on_device:
+        del dpsi
 
     def one_step():
         sim.step(n)
@@ -356,10 +371,13 @@ def main():
 
     # end to end through the C ABI with host buffers
     nbytes = int(np.prod(prob.shape)) * 16
-    h_in = torch.from_numpy(psi.view(np.float64).reshape(-1).copy()).pin_memory()
-    h_out = torch.empty_like(h_in).pin_memory()
+    if on_device:
+        psi = np.zeros(1, np.complex128)  # e2e and the CPU baseline need a host state: skipped
+    if not on_device:
+        h_in = torch.from_numpy(psi.view(np.float64).reshape(-1).copy()).pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
     e2e_ms = []
-    for i in range(max(1, min(3, args.steps))):
+    for i in range(0 if on_device else max(1, min(3, args.steps))):
         flush.fill_(float(i))
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -371,18 +389,18 @@ def main():
         b.record(stream)
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
-    e2e_ms_step = statistics.median(e2e_ms)
+    e2e_ms_step = statistics.median(e2e_ms) if e2e_ms else float("nan")
     if dist is not None:
         tt = torch.tensor([e2e_ms_step], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_ms_step = float(tt.item())
-    e2e = {"value": world * lups / (e2e_ms_step / 1e3) / 1e9, "unit": "GLUPS",
-           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 8 * 5,
-           "ms_per_step": e2e_ms_step}
+    e2e = None if on_device else {"value": world * lups / (e2e_ms_step / 1e3) / 1e9, "unit": "GLUPS",
+                                  "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 8 * 5,
+                                  "ms_per_step": e2e_ms_step}
 
     # the plain FP64 one-simulation-per-launch path on the same workload
     fp64 = None
-    if not args.no_fp64 and args.precision == "fp32":
+    if not args.no_fp64 and args.precision == "fp32" and not on_device:
         with D.Sim(prob, D.FP64, stream=stream.cuda_stream) as s64:
             s64.set_spinor(psi)
             n64 = max(1, n // 10)
@@ -407,7 +425,7 @@ def main():
             dist.destroy_process_group()
         return
     cpu = None
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and not on_device:
         cpu = cpu_baseline(prob, psi)
     out = {"metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,

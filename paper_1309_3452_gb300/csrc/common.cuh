@@ -9,6 +9,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <climits>
 
 namespace dirac {
 
@@ -195,8 +196,13 @@ __device__ __forceinline__ float2 apply(const F32::Coef& c, float2 F, float2 S) 
 }
 
 // ------------------------------------------------------------------ fields
-enum CoefMode { COEF_UNIFORM = 0, COEF_STEP = 1, COEF_GENERAL = 2 };
-enum LinkMode { LINK_NONE = 0, LINK_CONST = 1, LINK_GENERAL = 2 };
+// COEF_SOFTCORE: V0 + Klein step + soft core, evaluated per site in
+// double-float arithmetic (FP32 kernels).  LINK_PLANE: a plane-wave vector
+// potential whose wave vector lies along one axis other than its
+// polarisation; its link factors come from a per-half-step table indexed by
+// the half-lattice coordinate along that axis.  GENERAL: per-site FP64.
+enum CoefMode { COEF_UNIFORM = 0, COEF_STEP = 1, COEF_GENERAL = 2, COEF_SOFTCORE = 3 };
+enum LinkMode { LINK_NONE = 0, LINK_CONST = 1, LINK_GENERAL = 2, LINK_PLANE = 3 };
 
 // Analytic field description, FP64, for the per-site (general) paths.
 struct FieldDesc {
@@ -257,6 +263,63 @@ __device__ __forceinline__ double link_phase(const FieldDesc& f, int dims, const
   return f.q * A * f.dx[axis] * 0.5;
 }
 
+// ------------------------------------------------------------------ double-float
+// Unevaluated sums hi + lo of two floats, with error-free transformations:
+// TwoSum (Knuth, TAOCP vol. 2), FastTwoSum and TwoProduct via FMA (Dekker
+// 1971; Ogita, Rump, Oishi 2005).  About 44 significant bits.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = radd(a, b);
+  return DF{s, rsub(b, rsub(s, a))};
+}
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = radd(a, b);
+  const float bb = rsub(s, a);
+  return DF{s, radd(rsub(a, rsub(s, bb)), rsub(b, bb))};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const DF s = df_two_sum(a.hi, b.hi);
+  return df_fast_two_sum(s.hi, radd(s.lo, radd(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = rmul(a.hi, b.hi);
+  const float e = rfma(a.hi, b.hi, -p);
+  return df_fast_two_sum(p, rfma(a.hi, b.lo, rfma(a.lo, b.hi, e)));
+}
+__device__ __forceinline__ DF df_mulf(DF a, float b) {
+  const float p = rmul(a.hi, b);
+  const float e = rfma(a.hi, b, -p);
+  return df_fast_two_sum(p, rfma(a.lo, b, e));
+}
+// 1/sqrt(s) for s > 0: float estimate plus one Newton step on the residual
+// 1 - s y^2 formed in double-float
+__device__ __forceinline__ DF df_rsqrt(DF s) {
+  const float y = rsqrtf(s.hi);
+  const DF sy = df_mulf(s, y);                        // s y
+  const DF syy = df_mulf(sy, y);                      // s y^2
+  const float r = radd(rsub(1.0f, syy.hi), -syy.lo);  // 1 - s y^2 (small)
+  return df_fast_two_sum(y, rmul(rmul(0.5f, y), r));
+}
+// 1/q for q >= 1: float estimate plus one Newton step
+__device__ __forceinline__ DF df_rcp(DF q) {
+  const float y = __frcp_rn(q.hi);
+  const DF qy = df_mulf(q, y);
+  const float r = radd(rsub(1.0f, qy.hi), -qy.lo);    // 1 - q y (small)
+  return df_fast_two_sum(y, rmul(y, r));
+}
+
+// Per-simulation constants of the double-float soft-core path.
+struct SoftCore {
+  float h_hi[3], h_lo[3];  // dx_a / 2
+  float c_hi[3], c_lo[3];  // centre
+  float a2_hi, a2_lo;      // sc_a^2
+  float mz_hi, mz_lo;      // -sc_Z dt / 2
+  float rx_hi, rx_lo;      // r_x
+  int exact;               // positions, centre and r^2 are exact in FP32
+};
+
 // ------------------------------------------------------------------ site update
 // FP64 -> coefficient / link of the working precision
 __device__ __forceinline__ F64::Coef coef_from(const double2& a, const double2& g, F64*) {
@@ -302,7 +365,66 @@ struct HalfFields {
   typename P::Link L[3];    // constant link factors exp(-i q A_a dx_a/2)
   double t;                 // field time of this half-step
   double beta;              // +1 upper (A,B,u), -1 lower (C,D,v)
+  // COEF_SOFTCORE: dt/2 (beta m + V0 [+ V_step]) before / beyond the step
+  float th0_hi[2], th0_lo[2];
+  SoftCore sc;
+  // LINK_PLANE: table of exp(-i phi) for this half-step, indexed by the
+  // half-lattice coordinate along ltab_axis; applies on axis lpol only
+  const typename P::Link* ltab;
+  int ltab_axis, lpol;
 };
+
+// The soft-core update in double-float (F32 only):
+//   theta = dt/2 (beta m + V0 [+ V_step]) - Z dt/2 / sqrt(|x - c|^2 + a^2)
+//   F+ = kappa (1 - i theta) [(1 - i theta) F - r_x S'],  kappa = 1/(1 + theta^2)
+// which is ((1 - i theta) F - S) / (1 + i theta) with every coefficient carried
+// to ~1e-13, so its rounding does not accumulate over steps.
+template <class P>
+__device__ __forceinline__ typename P::cplx apply_softcore(const HalfFields<P>& h, typename P::cplx F,
+                                                           typename P::cplx S, const int (&H)[3]);
+template <>
+__device__ __forceinline__ double2 apply_softcore<F64>(const HalfFields<F64>&, double2 F, double2,
+                                                       const int (&)[3]) {
+  return F;  // not used: FP64 kernels take the general path
+}
+template <>
+__device__ __forceinline__ float2 apply_softcore<F32>(const HalfFields<F32>& h, float2 F, float2 S,
+                                                      const int (&H)[3]) {
+  const SoftCore& c = h.sc;
+  DF r2;
+  if (c.exact) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float d = rsub(rmul((float)H[a], c.h_hi[a]), c.c_hi[a]);
+      acc = rfma(d, d, acc);
+    }
+    r2 = DF{acc, 0.0f};
+  } else {
+    r2 = DF{0.0f, 0.0f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const DF x = df_mulf(DF{c.h_hi[a], c.h_lo[a]}, (float)H[a]);
+      const DF d = df_add(x, DF{-c.c_hi[a], -c.c_lo[a]});
+      r2 = df_add(r2, df_mul(d, d));
+    }
+  }
+  const DF y = df_rsqrt(df_add(r2, DF{c.a2_hi, c.a2_lo}));
+  const int hs = h.step_axis == 0 ? H[0] : (h.step_axis == 1 ? H[1] : H[2]);
+  const int side = (h.coef_mode == COEF_SOFTCORE && h.step_X != INT_MIN && hs >= h.step_X) ? 1 : 0;
+  const DF th = df_add(DF{h.th0_hi[side], h.th0_lo[side]}, df_mul(DF{c.mz_hi, c.mz_lo}, y));
+  const DF q = df_add(DF{1.0f, 0.0f}, df_mul(th, th));
+  const DF k = df_rcp(q);
+  // w = (1 - i th) F - r_x S'
+  float wr = rfma(th.hi, F.y, rfma(th.lo, F.y, F.x));
+  float wi = rfma(-th.hi, F.x, rfma(-th.lo, F.x, F.y));
+  wr = rfma(-c.rx_hi, S.x, rfma(-c.rx_lo, S.x, wr));
+  wi = rfma(-c.rx_hi, S.y, rfma(-c.rx_lo, S.y, wi));
+  // v = (1 - i th) w ; F+ = kappa v
+  const float vr = rfma(th.hi, wi, rfma(th.lo, wi, wr));
+  const float vi = rfma(-th.hi, wr, rfma(-th.lo, wr, wi));
+  return make_float2(rfma(k.hi, vr, rmul(k.lo, vr)), rfma(k.hi, vi, rmul(k.lo, vi)));
+}
 
 // Field-path selectors for site_update: a fixed CoefMode / LinkMode compiles
 // only that path; kAnyMode reads h.coef_mode / h.link_mode at run time and
@@ -330,7 +452,14 @@ __device__ __forceinline__ typename P::cplx site_update(
     if (link == LINK_CONST) {
       up = link_mul(h.L[ax], up);
       dn = link_mulc(h.L[ax], dn);
-    } else if (LINK == kAnyMode && link == LINK_GENERAL) {
+    } else if (LINK == LINK_PLANE) {
+      if (ax == h.lpol) {
+        const int hk = h.ltab_axis == 0 ? H[0] : (h.ltab_axis == 1 ? H[1] : H[2]);
+        const typename P::Link U = h.ltab[hk];
+        up = link_mul(U, up);
+        dn = link_mulc(U, dn);
+      }
+    } else if (LINK == kAnyMode && (link == LINK_GENERAL || link == LINK_PLANE)) {
       long long HH[3] = {H[0], H[1], H[2]};
       up = link_mul(link_from(link_phase(f, DIMS, HH, ax, +1, h.t), (P*)nullptr), up);
       // exp(+i phi-) = conj(exp(-i phi-))
@@ -345,6 +474,7 @@ __device__ __forceinline__ typename P::cplx site_update(
     const int hs = h.step_axis == 0 ? H[0] : (h.step_axis == 1 ? H[1] : H[2]);
     return hs >= h.step_X ? apply(h.c_out, F, S) : apply(h.c_in, F, S);
   }
+  if (COEF == COEF_SOFTCORE) return apply_softcore(h, F, S, H);
   double V = potential_at(f, DIMS, H[0], H[1], H[2], site, pstride, plane, h.t);
   double th = f.dt * (h.beta * f.m + V) * 0.5;
   double2 al, ga;

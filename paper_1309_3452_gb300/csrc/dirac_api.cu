@@ -39,6 +39,8 @@ struct dirac_sim {
   int iso = 1;
   int coef_mode = COEF_UNIFORM, link_mode = LINK_NONE;
   int step_X = 0;
+  void* ltab = nullptr;       // LINK_PLANE: link-factor table of the current step
+  int ltab_axis = 0, ltab_n = 0;
   long long launches = 0;     // kernels launched so far
   // CUDA graphs of kGraphSteps time steps, one per current-buffer parity
   // (only for fields without time dependence: the launches bake their time)
@@ -181,6 +183,24 @@ static void plane_ptrs(dirac_sim* s, typename P::cplx* (&pl)[8]) {
   for (int k = 0; k < 8; ++k) pl[k] = k < s->np ? base + (long long)k * s->pstride : nullptr;
 }
 
+// Positions, centre and |x - c|^2 of the soft core are exact in FP32: equal
+// lattice constants whose half is a power of two, a centre on the half
+// lattice, and |x - c|^2 / (dx/2)^2 < 2^24 everywhere.
+static int softcore_exact(const dirac_sim* s) {
+  if (!s->iso) return 0;
+  const double h = s->dx[0] / 2.0;
+  int e = 0;
+  if (std::frexp(h, &e) != 0.5) return 0;
+  double sum = 0.0;
+  for (int a = 0; a < s->dims; ++a) {
+    const double n = s->f.sc_center[a] / h;
+    if (n != std::floor(n) || std::fabs(n) > 1e6) return 0;
+    const double far = std::fmax(std::fabs(n), std::fabs(2.0 * s->N[a] - n));
+    sum += far * far;
+  }
+  return sum < 16777216.0 ? 1 : 0;
+}
+
 template <class P>
 static HalfFields<P> half_fields(const dirac_sim* s, bool upper, double t) {
   HalfFields<P> h;
@@ -196,6 +216,27 @@ static HalfFields<P> half_fields(const dirac_sim* s, bool upper, double t) {
   for (int k = 0; k < 3; ++k) h.L[k] = make_link<P>(s->f.q * s->f.A_const[k] * s->dx[k] / 2.0);
   h.t = t;
   h.beta = beta;
+  // soft core (double-float path)
+  const double th_in = s->dt * (beta * s->m + s->f.V0) / 2.0;
+  const double th_out = s->f.step_axis >= 0 ? s->dt * (beta * s->m + (s->f.V0 + s->f.step_V)) / 2.0 : th_in;
+  split(th_in, h.th0_hi[0], h.th0_lo[0]);
+  split(th_out, h.th0_hi[1], h.th0_lo[1]);
+  SoftCore& c = h.sc;
+  for (int a = 0; a < 3; ++a) {
+    const double hh = a < s->dims ? s->dx[a] / 2.0 : 0.0;
+    const double cc = a < s->dims ? s->f.sc_center[a] : 0.0;
+    split(hh, c.h_hi[a], c.h_lo[a]);
+    split(cc, c.c_hi[a], c.c_lo[a]);
+  }
+  split(s->f.sc_a * s->f.sc_a, c.a2_hi, c.a2_lo);
+  split(-s->f.sc_Z * s->dt / 2.0, c.mz_hi, c.mz_lo);
+  split(s->dt / s->dx[0], c.rx_hi, c.rx_lo);
+  c.exact = softcore_exact(s);
+  if (s->link_mode == LINK_PLANE) {
+    h.ltab = static_cast<typename P::Link*>(s->ltab) + (upper ? 0 : s->ltab_n);
+    h.ltab_axis = s->ltab_axis;
+    h.lpol = s->f.Apw_pol;
+  }
   return h;
 }
 
@@ -291,11 +332,27 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
   s->np = dims == 3 ? 8 : 4;
   s->elem = precision == DIRAC_FP32 ? sizeof(float2) : sizeof(double2);
   s->iso = (dx[0] == dx[1]) && (dims == 2 || dx[0] == dx[2]);
-  bool general_V = f.sc_Z != 0.0 || fields && fields->V_static;
-  s->coef_mode = general_V ? COEF_GENERAL : (f.step_axis >= 0 ? COEF_STEP : COEF_UNIFORM);
+  if (fields && fields->V_static) s->coef_mode = COEF_GENERAL;
+  else if (f.sc_Z != 0.0) s->coef_mode = COEF_SOFTCORE;
+  else s->coef_mode = f.step_axis >= 0 ? COEF_STEP : COEF_UNIFORM;
   if (f.step_axis >= 0) s->step_X = threshold_index(f.step_x0, s->dx[f.step_axis]);
   bool any_A = f.A_const[0] != 0.0 || f.A_const[1] != 0.0 || f.A_const[2] != 0.0;
   s->link_mode = f.Apw_amp != 0.0 ? LINK_GENERAL : (any_A ? LINK_CONST : LINK_NONE);
+  if (f.Apw_amp != 0.0) {
+    // a plane wave along one axis other than its polarisation (and no constant
+    // A across it) is tabulated per time step along that axis
+    int along = -1, count = 0;
+    for (int a = 0; a < dims; ++a)
+      if (f.Apw_k[a] != 0.0) { along = a; ++count; }
+    bool others_zero = true;
+    for (int a = 0; a < 3; ++a)
+      if (a != f.Apw_pol && f.A_const[a] != 0.0) others_zero = false;
+    if (count == 1 && along != f.Apw_pol && others_zero) {
+      s->link_mode = LINK_PLANE;
+      s->ltab_axis = along;
+      s->ltab_n = 2 * s->N[along];
+    }
+  }
 
   auto cleanup_fail = [&](dirac_status st) {
     std::string msg = s->err;
@@ -325,6 +382,10 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
       if (e != cudaSuccess) return cleanup_fail(cuda_fail(s, e, "cudaMemcpyAsync(V)"));
     }
   }
+  if (s->link_mode == LINK_PLANE) {
+    size_t tb = (size_t)2 * s->ltab_n * (precision == DIRAC_FP32 ? sizeof(F32::Link) : sizeof(F64::Link));
+    if ((e = cudaMalloc(&s->ltab, tb)) != cudaSuccess) return cleanup_fail(cuda_fail(s, e, "cudaMalloc(link table)"));
+  }
   s->red_blocks = observables_blocks(s->N, dims);
   if ((e = cudaMalloc(&s->partials, (size_t)s->red_blocks * kObsSums * sizeof(double))) != cudaSuccess)
     return cleanup_fail(cuda_fail(s, e, "cudaMalloc(partials)"));
@@ -347,6 +408,7 @@ extern "C" void dirac_destroy(dirac_sim* s) {
   cudaFree(s->state_alt);
   cudaFree(s->staging);
   cudaFree(s->Vstatic);
+  cudaFree(s->ltab);
   cudaFree(s->partials);
   cudaFree(s->sums_dev);
   if (s->sums_host) cudaFreeHost(s->sums_host);
@@ -433,10 +495,20 @@ extern "C" dirac_status dirac_get_spinor_device(dirac_sim* s, void* dev) {
 }
 
 // n time steps with one launch sequence each, on stream st
+// LINK_PLANE: tabulate this step's link factors (both half-steps)
+template <class P>
+static void link_table(dirac_sim* s, double t, cudaStream_t st) {
+  if (s->link_mode != LINK_PLANE) return;
+  launch_link_table<P>(static_cast<typename P::Link*>(s->ltab), s->ltab_n, field_desc(s), s->dims,
+                       s->ltab_axis, s->f.Apw_pol, t, t + s->dt / 2.0, st);
+  s->launches += 1;
+}
+
 template <class P>
 static dirac_status steps_split(dirac_sim* s, long n, cudaStream_t st) {
   for (long i = 0; i < n; ++i) {
     double t = sim_time(s);
+    link_table<P>(s, t, st);
     HalfStepArgs<P> up = half_args<P>(s, true, t);
     HalfStepArgs<P> lo = half_args<P>(s, false, t + s->dt / 2.0);
     if (s->dims == 3) {
@@ -456,6 +528,7 @@ static dirac_status steps_split(dirac_sim* s, long n, cudaStream_t st) {
 template <class P>
 static dirac_status steps_fused(dirac_sim* s, long n, cudaStream_t st) {
   for (long i = 0; i < n; ++i) {
+    link_table<P>(s, sim_time(s), st);
     FusedArgs<P> a = fused_args<P>(s, sim_time(s));
     if (s->dims == 3) launch_fused<P, 3>(a, st);
     else launch_fused<P, 2>(a, st);

@@ -82,6 +82,12 @@ void launch_observables(const ObsArgs<P>& a, int blocks, cudaStream_t s);
 // fixed-order sum of partials[nblocks][5] into out[5]
 void launch_finish_sums(const double* partials, int nblocks, double* out, cudaStream_t s);
 
+// table of plane-wave link factors exp(-i phi) for both half-steps of one time
+// step: tab[half * n + H], H = half-lattice coordinate along `axis`, n = 2 N_axis
+template <class P>
+void launch_link_table(typename P::Link* tab, int n, const FieldDesc& f, int dims, int axis, int pol,
+                       double t_up, double t_lo, cudaStream_t s);
+
 // canonical complex128 plane <-> device plane of the simulation precision
 void launch_convert_in(const double2* src, float2* dst, long long n, cudaStream_t s);
 void launch_convert_out(const float2* src, double2* dst, long long n, cudaStream_t s);

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) observables_kernel(const ObsArgs<P> a) {
           C up = nb[cell + (long long)(jp - j[ax]) * stride[ax]];
           C dn = nb[cell + (long long)(jm - j[ax]) * stride[ax]];
           R re, im;
-          if (a.link_mode == LINK_GENERAL) {
+          if (a.link_mode == LINK_GENERAL || a.link_mode == LINK_PLANE) {
             double2 u = mul_expm(widen(up), link_phase(a.f, DIMS, H, ax, +1, a.t_links));
             double2 v = mul_expm(widen(dn), -link_phase(a.f, DIMS, H, ax, -1, a.t_links));
             re = (R)(u.x - v.x);
@@ -122,6 +122,18 @@ __global__ void __launch_bounds__(256) observables_kernel(const ObsArgs<P> a) {
   }
   const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   block_reduce_store<kObsSums>(acc, a.partials + b * kObsSums);
+}
+
+template <class P>
+__global__ void link_table_kernel(typename P::Link* tab, int n, const FieldDesc f, int dims, int axis,
+                                  int pol, double t_up, double t_lo) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * n) return;
+  const int half = i / n;
+  long long HH[3] = {0, 0, 0};
+  HH[axis] = i - half * n;
+  // the same phase function and conversion as the per-link FP64 path
+  tab[i] = link_from(link_phase(f, dims, HH, pol, +1, half ? t_lo : t_up), (P*)nullptr);
 }
 
 __global__ void finish_sums_kernel(const double* partials, int nblocks, double* out) {
@@ -169,6 +181,16 @@ template void launch_observables<F64, 2>(const ObsArgs<F64>&, int, cudaStream_t)
 template void launch_observables<F64, 3>(const ObsArgs<F64>&, int, cudaStream_t);
 template void launch_observables<F32, 2>(const ObsArgs<F32>&, int, cudaStream_t);
 template void launch_observables<F32, 3>(const ObsArgs<F32>&, int, cudaStream_t);
+
+template <class P>
+void launch_link_table(typename P::Link* tab, int n, const FieldDesc& f, int dims, int axis, int pol,
+                       double t_up, double t_lo, cudaStream_t s) {
+  link_table_kernel<P><<<(2 * n + 127) / 128, 128, 0, s>>>(tab, n, f, dims, axis, pol, t_up, t_lo);
+}
+template void launch_link_table<F64>(F64::Link*, int, const FieldDesc&, int, int, int, double, double,
+                                     cudaStream_t);
+template void launch_link_table<F32>(F32::Link*, int, const FieldDesc&, int, int, int, double, double,
+                                     cudaStream_t);
 
 void launch_finish_sums(const double* partials, int nblocks, double* out, cudaStream_t s) {
   finish_sums_kernel<<<1, 32 * kObsSums, 0, s>>>(partials, nblocks, out);

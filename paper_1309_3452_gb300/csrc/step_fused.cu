@@ -499,6 +499,11 @@ template <int DIMS>
 void dispatch(const FusedArgs<F32>& a, cudaStream_t s) {
   const int c = a.hu.coef_mode, l = a.hu.link_mode;
   if (c == COEF_GENERAL || l == LINK_GENERAL) return launch_dims<DIMS, kAnyMode, kAnyMode>(a, s);
+  if (c == COEF_SOFTCORE && l == LINK_NONE) return launch_dims<DIMS, COEF_SOFTCORE, LINK_NONE>(a, s);
+  if (c == COEF_SOFTCORE && l == LINK_PLANE) return launch_dims<DIMS, COEF_SOFTCORE, LINK_PLANE>(a, s);
+  if (c == COEF_SOFTCORE) return launch_dims<DIMS, kAnyMode, kAnyMode>(a, s);
+  if (c == COEF_UNIFORM && l == LINK_PLANE) return launch_dims<DIMS, COEF_UNIFORM, LINK_PLANE>(a, s);
+  if (c == COEF_STEP && l == LINK_PLANE) return launch_dims<DIMS, COEF_STEP, LINK_PLANE>(a, s);
   if (c == COEF_UNIFORM && l == LINK_NONE) return launch_dims<DIMS, COEF_UNIFORM, LINK_NONE>(a, s);
   if (c == COEF_STEP && l == LINK_NONE) return launch_dims<DIMS, COEF_STEP, LINK_NONE>(a, s);
   if (c == COEF_UNIFORM && l == LINK_CONST) return launch_dims<DIMS, COEF_UNIFORM, LINK_CONST>(a, s);

@@ -53,10 +53,19 @@ void launch_one(const HalfStepArgs<P>& a, cudaStream_t s) {
   dim3 block(32, 4);
   dim3 grid((a.N[0] + 31) / 32, (a.N[1] + 3) / 4, DIMS == 3 ? a.N[2] : 1);
   const int c = a.h.coef_mode, l = a.h.link_mode;
+  constexpr bool f32 = sizeof(typename P::real) == 4;
   if (c == COEF_UNIFORM && l == LINK_NONE)
     half_step_kernel<P, DIMS, UPPER, COEF_UNIFORM, LINK_NONE><<<grid, block, 0, s>>>(a);
   else if (c == COEF_STEP && l == LINK_NONE)
     half_step_kernel<P, DIMS, UPPER, COEF_STEP, LINK_NONE><<<grid, block, 0, s>>>(a);
+  else if (f32 && c == COEF_SOFTCORE && l == LINK_NONE)  // the FP32 double-float paths
+    half_step_kernel<P, DIMS, UPPER, COEF_SOFTCORE, LINK_NONE><<<grid, block, 0, s>>>(a);
+  else if (f32 && c == COEF_SOFTCORE && l == LINK_PLANE)
+    half_step_kernel<P, DIMS, UPPER, COEF_SOFTCORE, LINK_PLANE><<<grid, block, 0, s>>>(a);
+  else if (f32 && c == COEF_UNIFORM && l == LINK_PLANE)
+    half_step_kernel<P, DIMS, UPPER, COEF_UNIFORM, LINK_PLANE><<<grid, block, 0, s>>>(a);
+  else if (f32 && c == COEF_STEP && l == LINK_PLANE)
+    half_step_kernel<P, DIMS, UPPER, COEF_STEP, LINK_PLANE><<<grid, block, 0, s>>>(a);
   else
     half_step_kernel<P, DIMS, UPPER, kAnyMode, kAnyMode><<<grid, block, 0, s>>>(a);
 }

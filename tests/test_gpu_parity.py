@@ -63,13 +63,20 @@ def field_cases(dims, N):
                            else (0, 2 * math.pi / L[1], 0), Apw_omega=0.3, Apw_pol=0),
         "A_wave_long": W.Fields(q=1.0, Apw_amp=0.4, Apw_k=(2 * math.pi / L[0], 0, 0),
                                 Apw_omega=0.0, Apw_pol=0, Apw_phase=0.3),
+        # soft core off the half lattice: the double-float |x - c|^2 branch
+        "softcore_offgrid": W.Fields(sc_Z=0.8, sc_a=1.3, sc_center=(c[0] - 0.37, c[1] + 0.61, 2.13),
+                                     V0=-0.1, step_axis=1, step_x0=N[1] / 2 + 0.25, step_V=0.3),
+        # the laser workload's fields: soft core plus a moving plane wave
+        "laser": W.Fields(sc_Z=1.0, sc_a=1.0, sc_center=tuple(c), q=1.0, Apw_amp=0.5,
+                          Apw_k=(0, 0, 2 * math.pi / L[dims - 1]) if dims == 3 else (0, 2 * math.pi / L[1], 0),
+                          Apw_omega=0.4, Apw_pol=0),
     }
     return cases
 
 
 @pytest.mark.parametrize("dims,N", [(2, (37, 29)), (3, (13, 11, 9))])
 @pytest.mark.parametrize("case", ["free", "V0", "klein", "klein_y", "softcore", "A_const", "A_wave",
-                                  "A_wave_long", "Vstatic_mod"])
+                                  "A_wave_long", "Vstatic_mod", "softcore_offgrid", "laser"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_parity_fields(D, dims, N, case, precision):
     full = tuple(N) + ((1,) if dims == 2 else ())
@@ -96,7 +103,7 @@ def test_parity_fields(D, dims, N, case, precision):
         assert abs(naive - ob1["naive"]) < 1e-12 * ob1["naive"]
     else:
         assert abs(E1 - ob1["E"]) < 1e-5 * abs(ob1["E"])
-        if case != "A_wave":  # time-dependent A: E is not conserved
+        if case not in ("A_wave", "laser"):  # time-dependent A: E is not conserved
             assert abs(E1 - E0) < FP32_EDRIFT * abs(E0)
 
 
@@ -210,7 +217,7 @@ def test_unstable_is_rejected_and_diverges_when_forced(D):
 @pytest.mark.parametrize("dims,N", [(2, (37, 29)), (2, (64, 70)), (3, (13, 11, 9)), (3, (33, 17, 20)),
                                     (3, (2, 3, 2))])
 @pytest.mark.parametrize("case", ["free", "klein", "klein_y", "softcore", "A_const", "A_wave",
-                                  "Vstatic_mod"])
+                                  "Vstatic_mod", "softcore_offgrid", "laser"])
 def test_fused_kernel_bit_identical_to_reference_kernels(D, dims, N, case):
     """The fused time-step kernel (out of place, tiles with recomputed halos,
     z/y marching) uses the same per-value arithmetic as the one-kernel-per-
