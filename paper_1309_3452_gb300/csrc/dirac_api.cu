@@ -28,6 +28,7 @@ struct dirac_sim {
   void* state = nullptr;      // np * pstride values: the current state
   void* state_alt = nullptr;  // second buffer for the out-of-place fused kernels
   int fused = 0;              // one kernel per time step (FP32 without the reference flag)
+  int tblock = 1;             // (2+1)D fused path: two time steps per pass when possible
   double2* staging = nullptr; // one canonical plane (FP32 conversions)
   double* Vstatic = nullptr;  // one real per site (plane-major, pstride)
   double* partials = nullptr;
@@ -495,6 +496,10 @@ extern "C" dirac_status dirac_get_spinor_device(dirac_sim* s, void* dev) {
 }
 
 // n time steps with one launch sequence each, on stream st
+static bool time_dependent_fields(const dirac_sim* s) {
+  return (s->Vstatic && s->f.Vmod_amp != 0.0) || (s->f.Apw_amp != 0.0 && s->f.Apw_omega != 0.0);
+}
+
 // LINK_PLANE: tabulate this step's link factors (both half-steps)
 template <class P>
 static void link_table(dirac_sim* s, double t, cudaStream_t st) {
@@ -527,6 +532,18 @@ static dirac_status steps_split(dirac_sim* s, long n, cudaStream_t st) {
 
 template <class P>
 static dirac_status steps_fused(dirac_sim* s, long n, cudaStream_t st) {
+  // (2+1)D, time-independent fields: two steps per pass while pairs remain
+  const bool tb = s->dims == 2 && s->tblock && !time_dependent_fields(s) &&
+                  std::getenv("DIRAC_NO_TEMPORAL_BLOCKING") == nullptr;
+  while (tb && n >= 2) {
+    FusedArgs<P> a = fused_args<P>(s, sim_time(s));
+    if (!launch_fused2d_tb2(a, st)) break;
+    s->launches += 1;
+    CK(s, cudaGetLastError());
+    std::swap(s->state, s->state_alt);
+    s->k += 2;
+    n -= 2;
+  }
   for (long i = 0; i < n; ++i) {
     link_table<P>(s, sim_time(s), st);
     FusedArgs<P> a = fused_args<P>(s, sim_time(s));
@@ -546,9 +563,6 @@ static dirac_status steps_plain(dirac_sim* s, long n, cudaStream_t st) {
   return steps_split<F32>(s, n, st);
 }
 
-static bool time_dependent_fields(const dirac_sim* s) {
-  return (s->Vstatic && s->f.Vmod_amp != 0.0) || (s->f.Apw_amp != 0.0 && s->f.Apw_omega != 0.0);
-}
 
 // Capture kGraphSteps steps starting from the current buffer into a graph
 // (on a private stream, so the simulation's stream may be the legacy one).

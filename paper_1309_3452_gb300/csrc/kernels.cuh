@@ -42,6 +42,11 @@ constexpr int kCore = 30;          // interior lanes of a 32-lane strip
 template <class P, int DIMS>
 void launch_fused(const FusedArgs<P>& a, cudaStream_t s);
 
+// Two time steps per pass of the (2+1)D fused kernel (fields without time
+// dependence: uniform / Klein-step / soft-core coefficients, no or constant
+// links).  Returns false, launching nothing, for other field paths.
+bool launch_fused2d_tb2(const FusedArgs<F32>& a, cudaStream_t s);
+
 // Several simulations (same dims and time-independent field modes) in one
 // persistent launch of the fused kernels.
 template <class P>

@@ -287,6 +287,43 @@ __host__ __device__ __forceinline__ long long items2d(const int (&N)[3], int chu
   return (long long)((N[0] + kCore - 1) / kCore) * ((N[1] + chunk - 1) / chunk);
 }
 
+// One row of the (2+1)D pipeline at march position k.  In: the old u0, v0, v1
+// of row k+1 and u1 of row k (the loads of row k), the old v0, v1 of row k,
+// the new u0 of row k and the new u1 of row k-1.  Out: the new u0 of row k+1,
+// u1, v1, v0 of row k.  Planes: 0 u0 (0,0)  1 u1 (1,1)  2 v0 (1,0)  3 v1 (0,1).
+template <class P, int COEF, int LINK>
+__device__ __forceinline__ void row2d(const FusedArgs<P>& a, bool iso, int hx, int yk, int yn,
+                                      long long ok, long long on, typename P::cplx U0,
+                                      typename P::cplx V0n, typename P::cplx V1n, typename P::cplx U1,
+                                      typename P::cplx oV0, typename P::cplx oV1, typename P::cplx nU0,
+                                      typename P::cplx nU1, typename P::cplx& nU0n,
+                                      typename P::cplx& nU1k, typename P::cplx& nV1,
+                                      typename P::cplx& nV0) {
+  using C = typename P::cplx;
+  // upper: u0(k+1) from v0(k+1) (x), v1(k+1), v1(k) (y); u1(k) from v1(k) (x), v0(k+1), v0(k) (y)
+  {
+    C nb[6] = {V0n, shfl_up1(V0n), V1n, oV1, V0n, V0n};
+    const int H[3] = {hx, 2 * yn, 0};
+    nU0n = site_update<P, 2, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 0, U0, nb, H, on, a.pstride);
+  }
+  {
+    C nb[6] = {shfl_down1(oV1), oV1, V0n, oV0, oV1, oV1};
+    const int H[3] = {hx + 1, 2 * yk + 1, 0};
+    nU1k = site_update<P, 2, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 1, U1, nb, H, ok, a.pstride);
+  }
+  // lower: v1(k) from u1(k) (x), u0(k+1), u0(k) (y); v0(k) from u0(k) (x), u1(k), u1(k-1) (y)
+  {
+    C nb[6] = {nU1k, shfl_up1(nU1k), nU0n, nU0, nU1k, nU1k};
+    const int H[3] = {hx, 2 * yk + 1, 0};
+    nV1 = site_update<P, 2, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 3, oV1, nb, H, ok, a.pstride);
+  }
+  {
+    C nb[6] = {shfl_down1(nU0), nU0, nU1k, nU1, nU0, nU0};
+    const int H[3] = {hx + 1, 2 * yk, 0};
+    nV0 = site_update<P, 2, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 2, oV0, nb, H, ok, a.pstride);
+  }
+}
+
 // One work item (one 32-cell strip over one chunk of rows) of one simulation,
 // processed by one warp.
 template <class P, int COEF, int LINK>
@@ -295,78 +332,131 @@ __device__ __forceinline__ void fused2d_item(const FusedArgs<P>& a, long long it
   const int Nx = a.N[0], Ny = a.N[1];
   const int strips = (Nx + kCore - 1) / kCore;
   const bool iso = a.iso != 0;
-  {
-    const long long chunk = item / strips;
-    const int strip = (int)(item - chunk * strips);
-    const int y0 = (int)chunk * a.chunk;
-    const int y1 = min(Ny, y0 + a.chunk);
-    const int gx = strip * kCore + lane - 1;
-    const int x = wrapi(gx, Nx);
-    const bool core = lane >= 1 && lane <= kCore && gx < Nx;
-    const int hx = 2 * x;
-    // planes: 0 u0 (0,0)  1 u1 (1,1)  2 v0 (1,0)  3 v1 (0,1)
-    long long o = (long long)wrapi(y0 - 1, Ny) * Nx + x;
-    C oV0 = ld(a.in[2] + o), oV1 = ld(a.in[3] + o);
-    C nU0 = oV0, nU1 = oV1;  // placeholders: only feed values never stored
-    // the loads of row k: u0, v0, v1 at row k+1 and u1 at row k
-    auto load = [&](int k, C& u0, C& v0, C& v1, C& u1) {
-      const int yk = k < 0 ? k + Ny : k;
-      const int yn = k + 1 >= Ny ? k + 1 - Ny : k + 1;
-      const long long okk = (long long)yk * Nx + x, onn = (long long)yn * Nx + x;
-      u0 = ld(a.in[0] + onn);
-      v0 = ld(a.in[2] + onn);
-      v1 = ld(a.in[3] + onn);
-      u1 = ld(a.in[1] + okk);
-    };
-    C U0, V0n, V1n, U1;
-    load(y0 - 1, U0, V0n, V1n, U1);
-    for (int k = y0 - 1; k < y1; ++k) {
-      const int yk = k < 0 ? k + Ny : k;
-      const int yn = k + 1 >= Ny ? k + 1 - Ny : k + 1;
-      const long long ok = (long long)yk * Nx + x, on = (long long)yn * Nx + x;
-      C pU0 = U0, pV0 = V0n, pV1 = V1n, pU1 = U1;  // next row, loaded while this one computes
-      if (k + 1 < y1) load(k + 1, pU0, pV0, pV1, pU1);
-      // upper: u0(k+1) from v0(k+1) (x), v1(k+1), v1(k) (y); u1(k) from v1(k) (x), v0(k+1), v0(k) (y)
-      C nU0n, nU1k;
-      {
-        C nb[6] = {V0n, shfl_up1(V0n), V1n, oV1, V0n, V0n};
-        const int H[3] = {hx, 2 * yn, 0};
-        nU0n = site_update<P, 2, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 0, U0, nb, H, on, a.pstride);
+  const long long chunk = item / strips;
+  const int strip = (int)(item - chunk * strips);
+  const int y0 = (int)chunk * a.chunk;
+  const int y1 = min(Ny, y0 + a.chunk);
+  const int gx = strip * kCore + lane - 1;
+  const int x = wrapi(gx, Nx);
+  const bool core = lane >= 1 && lane <= kCore && gx < Nx;
+  const int hx = 2 * x;
+  long long o = (long long)wrapi(y0 - 1, Ny) * Nx + x;
+  C oV0 = ld(a.in[2] + o), oV1 = ld(a.in[3] + o);
+  C nU0 = oV0, nU1 = oV1;  // placeholders: only feed values never stored
+  // the loads of row k: u0, v0, v1 at row k+1 and u1 at row k
+  auto load = [&](int k, C& u0, C& v0, C& v1, C& u1) {
+    const int yk = k < 0 ? k + Ny : (k >= Ny ? k - Ny : k);
+    const int yn = k + 1 >= Ny ? k + 1 - Ny : (k + 1 < 0 ? k + 1 + Ny : k + 1);
+    const long long okk = (long long)yk * Nx + x, onn = (long long)yn * Nx + x;
+    u0 = ld(a.in[0] + onn);
+    v0 = ld(a.in[2] + onn);
+    v1 = ld(a.in[3] + onn);
+    u1 = ld(a.in[1] + okk);
+  };
+  C U0, V0n, V1n, U1;
+  load(y0 - 1, U0, V0n, V1n, U1);
+  for (int k = y0 - 1; k < y1; ++k) {
+    const int yk = k < 0 ? k + Ny : k;
+    const int yn = k + 1 >= Ny ? k + 1 - Ny : k + 1;
+    const long long ok = (long long)yk * Nx + x, on = (long long)yn * Nx + x;
+    C pU0 = U0, pV0 = V0n, pV1 = V1n, pU1 = U1;  // next row, loaded while this one computes
+    if (k + 1 < y1) load(k + 1, pU0, pV0, pV1, pU1);
+    C nU0n, nU1k, nV1, nV0;
+    row2d<P, COEF, LINK>(a, iso, hx, yk, yn, ok, on, U0, V0n, V1n, U1, oV0, oV1, nU0, nU1, nU0n, nU1k,
+                         nV1, nV0);
+    if (core) {
+      if (k >= y0) {
+        a.out[1][ok] = nU1k;
+        a.out[2][ok] = nV0;
+        a.out[3][ok] = nV1;
       }
-      {
-        C nb[6] = {shfl_down1(oV1), oV1, V0n, oV0, oV1, oV1};
-        const int H[3] = {hx + 1, 2 * yk + 1, 0};
-        nU1k = site_update<P, 2, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 1, U1, nb, H, ok, a.pstride);
-      }
-      // lower: v1(k) from u1(k) (x), u0(k+1), u0(k) (y); v0(k) from u0(k) (x), u1(k), u1(k-1) (y)
-      C nV0, nV1;
-      {
-        C nb[6] = {nU1k, shfl_up1(nU1k), nU0n, nU0, nU1k, nU1k};
-        const int H[3] = {hx, 2 * yk + 1, 0};
-        nV1 = site_update<P, 2, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 3, oV1, nb, H, ok, a.pstride);
-      }
-      {
-        C nb[6] = {shfl_down1(nU0), nU0, nU1k, nU1, nU0, nU0};
-        const int H[3] = {hx + 1, 2 * yk, 0};
-        nV0 = site_update<P, 2, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 2, oV0, nb, H, ok, a.pstride);
-      }
-      if (core) {
-        if (k >= y0) {
-          a.out[1][ok] = nU1k;
-          a.out[2][ok] = nV0;
-          a.out[3][ok] = nV1;
-        }
-        if (k + 1 < y1) a.out[0][on] = nU0n;
-      }
-      oV0 = V0n;
-      oV1 = V1n;
-      nU0 = nU0n;
-      nU1 = nU1k;
-      U0 = pU0;
-      V0n = pV0;
-      V1n = pV1;
-      U1 = pU1;
+      if (k + 1 < y1) a.out[0][on] = nU0n;
     }
+    oV0 = V0n;
+    oV1 = V1n;
+    nU0 = nU0n;
+    nU1 = nU1k;
+    U0 = pU0;
+    V0n = pV0;
+    V1n = pV1;
+    U1 = pU1;
+  }
+}
+
+// Two time steps per pass ((2+1)D, fields without time dependence).  Step 1
+// runs the row pipeline on the old state; step 2 runs it one row behind on
+// step 1's results, which never leave registers.  A strip keeps 28 interior
+// lanes (lanes 2..29): step 1 is valid on lanes 1..30, step 2 on 2..29.
+// Step 1 starts two rows and step 2 one row before the chunk.
+constexpr int kCoreTb = 28;
+
+template <class P, int COEF, int LINK>
+__device__ __forceinline__ void fused2d_tb2_item(const FusedArgs<P>& a, long long item, int lane) {
+  using C = typename P::cplx;
+  const int Nx = a.N[0], Ny = a.N[1];
+  const int strips = (Nx + kCoreTb - 1) / kCoreTb;
+  const bool iso = a.iso != 0;
+  const long long chunk = item / strips;
+  const int strip = (int)(item - chunk * strips);
+  const int y0 = (int)chunk * a.chunk;
+  const int y1 = min(Ny, y0 + a.chunk);
+  const int gx = strip * kCoreTb + lane - 2;
+  const int x = wrapi(gx, Nx);
+  const bool core = lane >= 2 && lane <= kCoreTb + 1 && gx < Nx;
+  const int hx = 2 * x;
+  auto wrapy = [&](int k) { return k < 0 ? k + Ny : (k >= Ny ? k - Ny : k); };
+  auto load = [&](int k, C& u0, C& v0, C& v1, C& u1) {
+    const long long okk = (long long)wrapy(k) * Nx + x, onn = (long long)wrapy(k + 1) * Nx + x;
+    u0 = ld(a.in[0] + onn);
+    v0 = ld(a.in[2] + onn);
+    v1 = ld(a.in[3] + onn);
+    u1 = ld(a.in[1] + okk);
+  };
+  // step-1 pipeline state (old v0, v1 of row k; new u0 of row k; new u1 of row k-1)
+  long long o = (long long)wrapy(y0 - 2) * Nx + x;
+  C oV0 = ld(a.in[2] + o), oV1 = ld(a.in[3] + o);
+  C nU0 = oV0, nU1 = oV1;  // placeholders: only feed values never stored
+  // step-2 pipeline state: step-1 v0, v1 of row k-1; step-2 u0 of row k-1, u1 of row k-2
+  C qV0 = oV0, qV1 = oV1, mU0 = oV0, mU1 = oV1;
+  C U0, V0n, V1n, U1;
+  load(y0 - 2, U0, V0n, V1n, U1);
+  for (int k = y0 - 2; k <= y1; ++k) {
+    const int yk = wrapy(k), yn = wrapy(k + 1);
+    const long long ok = (long long)yk * Nx + x, on = (long long)yn * Nx + x;
+    C pU0 = U0, pV0 = V0n, pV1 = V1n, pU1 = U1;
+    if (k + 1 <= y1) load(k + 1, pU0, pV0, pV1, pU1);
+    // step 1 at row k
+    C sU0n, sU1k, sV1, sV0;
+    row2d<P, COEF, LINK>(a, iso, hx, yk, yn, ok, on, U0, V0n, V1n, U1, oV0, oV1, nU0, nU1, sU0n, sU1k,
+                         sV1, sV0);
+    if (k >= y0) {
+      // step 2 at row k-1: its loads are step 1's u0, v0, v1 of row k and u1 of row k-1
+      const int ym = wrapy(k - 1);
+      const long long om = (long long)ym * Nx + x;
+      C tU0n, tU1k, tV1, tV0;
+      row2d<P, COEF, LINK>(a, iso, hx, ym, yk, om, ok, nU0, sV0, sV1, nU1, qV0, qV1, mU0, mU1, tU0n, tU1k,
+                           tV1, tV0);
+      if (core) {
+        if (k - 1 >= y0) {
+          a.out[1][om] = tU1k;
+          a.out[2][om] = tV0;
+          a.out[3][om] = tV1;
+        }
+        if (k < y1) a.out[0][ok] = tU0n;
+      }
+      mU0 = tU0n;
+      mU1 = tU1k;
+    }
+    qV0 = sV0;  // step-1 v0, v1 of row k become step 2's old row
+    qV1 = sV1;
+    oV0 = V0n;
+    oV1 = V1n;
+    nU0 = sU0n;
+    nU1 = sU1k;
+    U0 = pU0;
+    V0n = pV0;
+    V1n = pV1;
+    U1 = pU1;
   }
 }
 
@@ -377,6 +467,15 @@ __global__ void __launch_bounds__(32 * kFused2dWarps) fused2d_kernel(const Fused
   const long long items = items2d(a.N, a.chunk);
   for (long long item = worker; item < items; item += a.workers)  // uniform per warp
     fused2d_item<P, COEF, LINK>(a, item, lane);
+}
+
+template <class P, int COEF, int LINK>
+__global__ void __launch_bounds__(32 * kFused2dWarps) fused2d_tb2_kernel(const FusedArgs<P> a) {
+  const int lane = threadIdx.x & 31;
+  const long long worker = (long long)blockIdx.x * kFused2dWarps + (threadIdx.x >> 5);
+  const long long items = (long long)((a.N[0] + kCoreTb - 1) / kCoreTb) * ((a.N[1] + a.chunk - 1) / a.chunk);
+  for (long long item = worker; item < items; item += a.workers)  // uniform per warp
+    fused2d_tb2_item<P, COEF, LINK>(a, item, lane);
 }
 
 template <class P, int COEF, int LINK>
@@ -510,6 +609,18 @@ void dispatch(const FusedArgs<F32>& a, cudaStream_t s) {
   return launch_dims<DIMS, COEF_STEP, LINK_CONST>(a, s);
 }
 
+template <int COEF, int LINK>
+void launch2d_tb2(FusedArgs<F32> a, cudaStream_t s) {
+  auto k = fused2d_tb2_kernel<F32, COEF, LINK>;
+  const int warps = workers2d<fused2d_tb2_kernel<F32, COEF, LINK>>();
+  const long long strips = (a.N[0] + kCoreTb - 1) / kCoreTb;
+  a.chunk = plan_chunk(strips, a.N[1], warps, 32);
+  const long long items = strips * ((a.N[1] + a.chunk - 1) / a.chunk);
+  const long long w = items < warps ? items : warps;
+  a.workers = (int)w;
+  k<<<(unsigned)((w + kFused2dWarps - 1) / kFused2dWarps), 32 * kFused2dWarps, 0, s>>>(a);
+}
+
 template <int DIMS, int COEF, int LINK>
 void batch_dims(const BatchArgs<F32>& b, long long total, cudaStream_t s) {
   if (DIMS == 3) launch3d_batch<COEF, LINK>(b, total, s);
@@ -517,6 +628,17 @@ void batch_dims(const BatchArgs<F32>& b, long long total, cudaStream_t s) {
 }
 
 }  // namespace
+
+bool launch_fused2d_tb2(const FusedArgs<F32>& a, cudaStream_t s) {
+  const int c = a.hu.coef_mode, l = a.hu.link_mode;
+  if (c == COEF_UNIFORM && l == LINK_NONE) launch2d_tb2<COEF_UNIFORM, LINK_NONE>(a, s);
+  else if (c == COEF_STEP && l == LINK_NONE) launch2d_tb2<COEF_STEP, LINK_NONE>(a, s);
+  else if (c == COEF_UNIFORM && l == LINK_CONST) launch2d_tb2<COEF_UNIFORM, LINK_CONST>(a, s);
+  else if (c == COEF_STEP && l == LINK_CONST) launch2d_tb2<COEF_STEP, LINK_CONST>(a, s);
+  else if (c == COEF_SOFTCORE && l == LINK_NONE) launch2d_tb2<COEF_SOFTCORE, LINK_NONE>(a, s);
+  else return false;
+  return true;
+}
 
 int fused_chunk(int dims, const int N[3]) {
   if (dims == 3) {

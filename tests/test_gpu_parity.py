@@ -265,3 +265,25 @@ def test_graph_replay_bit_identical_to_plain_launches(D, dims, precision, monkey
             outs.append(s.get_spinor())
         monkeypatch.delenv("DIRAC_NO_GRAPHS", raising=False)
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("N", [(70, 50), (29, 31), (5, 9), (129, 64)])
+@pytest.mark.parametrize("case", ["free", "klein", "klein_y", "A_const", "softcore", "softcore_offgrid"])
+def test_temporal_blocking_2d_bit_identical(D, N, case, monkeypatch):
+    """(2+1)D: two time steps per pass (step 2 runs one row behind step 1 in
+    registers) equal two single-step passes bit for bit; odd step counts
+    finish with a single-step pass."""
+    prob = W.Problem(2, (N[0], N[1], 1), (1.0, 1.0, 1.0), 0.9 * W.stability_limit(2), 0.45,
+                     field_cases(2, N)[case])
+    psi = W.random_state(prob, 9)
+    outs = []
+    for off in (False, True):
+        if off:
+            monkeypatch.setenv("DIRAC_NO_TEMPORAL_BLOCKING", "1")
+        with D.Sim(prob, D.FP32) as s:
+            s.set_spinor(psi)
+            s.step(21)
+            s.step(6)
+            outs.append(s.get_spinor())
+        monkeypatch.delenv("DIRAC_NO_TEMPORAL_BLOCKING", raising=False)
+    assert np.array_equal(outs[0], outs[1])
