@@ -68,22 +68,39 @@ struct LevelLoad {
   C A0, A1, B0, B1, C0, C1, D0, D1;
 };
 
-// thread geometry inside the (3+1)D tile
+// Thread geometry inside the (3+1)D tile.  Warps 0..12 hold the 13 interior
+// rows, one aligned row of 32 cells each (lane -> x).  Warps 13..15 hold the
+// 94 halo cells (rows 0 and 14, columns 0 and 33) and two spare threads; they
+// only take part in the upper half-step, whose values the interior needs.
 struct Thread3d {
-  int t, lx, ly;
-  int sxm, sxp, sym, syp;  // shared-memory slots of the x/y neighbours (clamped
-                           // at the tile edge: halo threads then read their own slot)
+  int slot;                // this cell's shared-memory slot, ly * TW + lx
+  int lx, ly;              // position in the 34 x 15 tile
+  int sxm, sxp, sym, syp;  // slots of the x/y neighbours (clamped at the tile
+                           // edge: halo cells then read their own slot, values never used)
+  bool halo;               // warp-uniform
 };
 
 __device__ __forceinline__ Thread3d thread3d() {
   Thread3d th;
-  th.t = threadIdx.x;
-  th.lx = th.t % TW;
-  th.ly = th.t / TW;
-  th.sxm = th.lx > 0 ? th.t - 1 : th.t;
-  th.sxp = th.lx < TW - 1 ? th.t + 1 : th.t;
-  th.sym = th.ly > 0 ? th.t - TW : th.t;
-  th.syp = th.ly < kSmemRows - 1 ? th.t + TW : th.t;
+  const int t = threadIdx.x, w = t >> 5;
+  if (w < CY) {
+    th.lx = (t & 31) + 1;
+    th.ly = w + 1;
+    th.halo = false;
+  } else {
+    const int h = t - 32 * CY;
+    th.halo = true;
+    if (h < TW) { th.lx = h; th.ly = 0; }
+    else if (h < 2 * TW) { th.lx = h - TW; th.ly = TH - 1; }
+    else if (h < 2 * TW + CY) { th.lx = 0; th.ly = h - 2 * TW + 1; }
+    else if (h < 2 * TW + 2 * CY) { th.lx = TW - 1; th.ly = h - 2 * TW - CY + 1; }
+    else { th.lx = h - 2 * TW - 2 * CY; th.ly = kSmemRows - 1; }  // spare: a row of its own
+  }
+  th.slot = th.ly * TW + th.lx;
+  th.sxm = th.lx > 0 ? th.slot - 1 : th.slot;
+  th.sxp = th.lx < TW - 1 ? th.slot + 1 : th.slot;
+  th.sym = th.ly > 0 ? th.slot - TW : th.slot;
+  th.syp = th.ly < kSmemRows - 1 ? th.slot + TW : th.slot;
   return th;
 }
 
@@ -102,7 +119,7 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
   C (*sD)[2][kSlots] = sC + 2;                                         // old D(k)
   C (*sB)[2][kSlots] = sC + 4;                                         // new B(k)
   C (*sA)[2][kSlots] = sC + 6;                                         // new A(k)
-  const int t = th.t, lx = th.lx, ly = th.ly;
+  const int t = th.slot, lx = th.lx, ly = th.ly;
   const int sxm = th.sxm, sxp = th.sxp, sym = th.sym, syp = th.syp;
   const int Nx = a.N[0], Ny = a.N[1], Nz = a.N[2];
   const int tiles_x = (Nx + CX - 1) / CX;
@@ -190,6 +207,8 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
       __syncthreads();
 
       // lower half-step: C(k) from A(k+1), A(k), B(k); D(k) from B(k), B(k-1), A(k)
+      // (interior warps only: nothing needs the halo's lower values)
+      if (!th.halo) {
       const C nA0 = sA[pk][0][t], nA1 = sA[pk][1][t];
       C nC0, nC1, nD0, nD1;
       {
@@ -225,6 +244,7 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
           a.out[0][on] = nA0n;
           a.out[1][on] = nA1n;
         }
+      }
       }
       cur = nxt;
     }
@@ -275,7 +295,7 @@ __global__ void __launch_bounds__(kThreads3d, 2) fused3d_batch_kernel(const Batc
     const int s = find_sim(b.first_item, b.nsims, g);
     if (s != cur) {
       __syncthreads();  // everyone is done with the previous arguments
-      copy_args(&sa, b.sims + s, th.t, kThreads3d);
+      copy_args(&sa, b.sims + s, (int)threadIdx.x, kThreads3d);
       __syncthreads();
       cur = s;
     }
