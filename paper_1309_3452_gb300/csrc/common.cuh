@@ -441,7 +441,7 @@ template <class P, int DIMS, int COEF, int LINK>
 __device__ __forceinline__ typename P::cplx site_update(
     const HalfFields<P>& h, const FieldDesc& f, bool iso, const typename P::Ratio& ry,
     const typename P::Ratio& rz, int plane, typename P::cplx F, typename P::cplx (&nb)[6],
-    const int (&H)[3], long long site, long long pstride) {
+    const int (&H)[3], long long site, long long pstride, typename P::cplx* S_out = nullptr) {
   using C = typename P::cplx;
   const int link = LINK == kAnyMode ? h.link_mode : LINK;
   const int coef = COEF == kAnyMode ? h.coef_mode : COEF;
@@ -469,6 +469,7 @@ __device__ __forceinline__ typename P::cplx site_update(
   }
   if (DIMS == 2) d[2] = d[0];
   const C S = combine<P, DIMS>(d[0], d[1], d[2], sign_class<DIMS>(plane), iso, ry, rz);
+  if (S_out) *S_out = S;  // the difference part S' (S = r_x S'), for the conserved functional
   if (coef == COEF_UNIFORM) return apply(h.c_in, F, S);
   if (coef == COEF_STEP) {
     const int hs = h.step_axis == 0 ? H[0] : (h.step_axis == 1 ? H[1] : H[2]);

@@ -49,6 +49,10 @@ struct dirac_sim {
   void* graph_state[2] = {nullptr, nullptr};
   int graph_disabled = 0;
   int stepped = 0;            // a plain step has run (kernel one-time set-up done)
+  // conserved functional accumulated by the last fused launch of a dirac_step
+  double* e_partials = nullptr;  // [kFusedEMaxBlocks][2]
+  double* e_sums = nullptr;      // [2]: sum |psi|^2, Re sum_lower conj(G) S'_G
+  long long e_valid_at = -1;     // value of k for which e_sums describe the state
   std::string err;
 };
 
@@ -387,6 +391,11 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
     size_t tb = (size_t)2 * s->ltab_n * (precision == DIRAC_FP32 ? sizeof(F32::Link) : sizeof(F64::Link));
     if ((e = cudaMalloc(&s->ltab, tb)) != cudaSuccess) return cleanup_fail(cuda_fail(s, e, "cudaMalloc(link table)"));
   }
+  if (s->fused) {
+    if ((e = cudaMalloc(&s->e_partials, (size_t)kFusedEMaxBlocks * 2 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&s->e_sums, 2 * sizeof(double))) != cudaSuccess)
+      return cleanup_fail(cuda_fail(s, e, "cudaMalloc(functional partials)"));
+  }
   s->red_blocks = observables_blocks(s->N, dims);
   if ((e = cudaMalloc(&s->partials, (size_t)s->red_blocks * kObsSums * sizeof(double))) != cudaSuccess)
     return cleanup_fail(cuda_fail(s, e, "cudaMalloc(partials)"));
@@ -410,6 +419,8 @@ extern "C" void dirac_destroy(dirac_sim* s) {
   cudaFree(s->staging);
   cudaFree(s->Vstatic);
   cudaFree(s->ltab);
+  cudaFree(s->e_partials);
+  cudaFree(s->e_sums);
   cudaFree(s->partials);
   cudaFree(s->sums_dev);
   if (s->sums_host) cudaFreeHost(s->sums_host);
@@ -418,6 +429,7 @@ extern "C" void dirac_destroy(dirac_sim* s) {
 
 extern "C" dirac_status dirac_set_spinor(dirac_sim* s, const double* host) {
   if (!s || !host) return fail(s, DIRAC_ERR_INVALID, "NULL argument");
+  s->e_valid_at = -1;
   for (int k = 0; k < s->np; ++k) {
     const double* src = host + 2LL * k * s->ncell;
     size_t bytes = (size_t)s->ncell * sizeof(double2);
@@ -459,6 +471,7 @@ static double sim_time(const dirac_sim* s) { return s->t0 + (double)s->k * s->dt
 
 extern "C" dirac_status dirac_set_spinor_device(dirac_sim* s, const void* dev) {
   if (!s || !dev) return fail(s, DIRAC_ERR_INVALID, "NULL argument");
+  s->e_valid_at = -1;
   const double2* src = static_cast<const double2*>(dev);
   for (int k = 0; k < s->np; ++k) {
     const double2* plane = src + (long long)k * s->ncell;
@@ -530,14 +543,21 @@ static dirac_status steps_split(dirac_sim* s, long n, cudaStream_t st) {
   return DIRAC_OK;
 }
 
+// want_e: the last launch also accumulates the conserved functional of the
+// new state (dirac_norm then needs no reduction pass over the state)
 template <class P>
-static dirac_status steps_fused(dirac_sim* s, long n, cudaStream_t st) {
+static dirac_status steps_fused(dirac_sim* s, long n, cudaStream_t st, bool want_e) {
+  want_e = want_e && n > 0 && std::getenv("DIRAC_NO_FUSED_NORM") == nullptr;
+  int e_blocks = 0;
   // (2+1)D, time-independent fields: two steps per pass while pairs remain
   const bool tb = s->dims == 2 && s->tblock && !time_dependent_fields(s) &&
                   std::getenv("DIRAC_NO_TEMPORAL_BLOCKING") == nullptr;
   while (tb && n >= 2) {
     FusedArgs<P> a = fused_args<P>(s, sim_time(s));
-    if (!launch_fused2d_tb2(a, st)) break;
+    if (want_e && n == 2) a.e_partials = s->e_partials;
+    const int blocks = launch_fused2d_tb2(a, st);
+    if (!blocks) break;
+    if (a.e_partials) e_blocks = blocks;
     s->launches += 1;
     CK(s, cudaGetLastError());
     std::swap(s->state, s->state_alt);
@@ -547,19 +567,26 @@ static dirac_status steps_fused(dirac_sim* s, long n, cudaStream_t st) {
   for (long i = 0; i < n; ++i) {
     link_table<P>(s, sim_time(s), st);
     FusedArgs<P> a = fused_args<P>(s, sim_time(s));
-    if (s->dims == 3) launch_fused<P, 3>(a, st);
-    else launch_fused<P, 2>(a, st);
+    if (want_e && i == n - 1) a.e_partials = s->e_partials;
+    const int blocks = s->dims == 3 ? launch_fused<P, 3>(a, st) : launch_fused<P, 2>(a, st);
+    if (a.e_partials) e_blocks = blocks;
     s->launches += 1;
     CK(s, cudaGetLastError());
     std::swap(s->state, s->state_alt);
     s->k += 1;
   }
+  if (e_blocks > 0 && e_blocks <= kFusedEMaxBlocks) {
+    launch_finish_sums2(s->e_partials, e_blocks, s->e_sums, st);
+    s->launches += 1;
+    CK(s, cudaGetLastError());
+    s->e_valid_at = s->k;
+  }
   return DIRAC_OK;
 }
 
-static dirac_status steps_plain(dirac_sim* s, long n, cudaStream_t st) {
+static dirac_status steps_plain(dirac_sim* s, long n, cudaStream_t st, bool want_e = false) {
   if (s->prec == DIRAC_FP64) return steps_split<F64>(s, n, st);
-  if (s->fused) return steps_fused<F32>(s, n, st);
+  if (s->fused) return steps_fused<F32>(s, n, st, want_e);
   return steps_split<F32>(s, n, st);
 }
 
@@ -613,7 +640,7 @@ extern "C" dirac_status dirac_step(dirac_sim* s, long nsteps) {
     --nsteps;
   }
   s->stepped = 1;
-  while (graphs && nsteps >= kGraphSteps) {
+  while (graphs && nsteps > kGraphSteps) {  // the last step is always a plain launch
     int slot = (s->graph_state[0] == s->state) ? 0 : (s->graph_state[1] == s->state ? 1 : -1);
     if (slot < 0) {
       slot = s->graph[0] ? 1 : 0;
@@ -627,7 +654,7 @@ extern "C" dirac_status dirac_step(dirac_sim* s, long nsteps) {
     if (s->fused && (kGraphSteps & 1)) std::swap(s->state, s->state_alt);
     nsteps -= kGraphSteps;
   }
-  return steps_plain(s, nsteps, s->stream);
+  return steps_plain(s, nsteps, s->stream, true);
 }
 
 static bool batchable(const dirac_sim* s) {
@@ -791,11 +818,19 @@ static dirac_status observe_any(dirac_sim* s, int dens_axis, int dens_X) {
 
 extern "C" dirac_status dirac_norm(dirac_sim* s, double* E, double* naive) {
   if (!s || !E) return fail(s, DIRAC_ERR_INVALID, "NULL argument");
-  dirac_status st = observe_any(s, -1, 0);
-  if (st != DIRAC_OK) return st;
+  double e;
   const double* v = s->sums_host;
-  double e = v[0];
-  for (int a = 0; a < s->dims; ++a) e += (s->dt / s->dx[a]) * v[1 + a];
+  if (s->e_valid_at == s->k && s->e_sums && std::getenv("DIRAC_NO_FUSED_NORM") == nullptr) {
+    // accumulated by the last step's kernel: E = sum |psi|^2 + r_x Re sum conj(G) S'_G
+    CK(s, cudaMemcpyAsync(s->sums_host, s->e_sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    e = v[0] + (s->dt / s->dx[0]) * v[1];
+  } else {
+    dirac_status st = observe_any(s, -1, 0);
+    if (st != DIRAC_OK) return st;
+    e = v[0];
+    for (int a = 0; a < s->dims; ++a) e += (s->dt / s->dx[a]) * v[1 + a];
+  }
   *E = e;
   if (naive) *naive = v[0];
   if (!std::isfinite(e)) return fail(s, DIRAC_ERR_DIVERGED, "conserved functional is not finite");
@@ -823,5 +858,6 @@ extern "C" dirac_status dirac_set_time(dirac_sim* s, double t) {
   if (!s || !std::isfinite(t)) return fail(s, DIRAC_ERR_INVALID, "bad time");
   s->t0 = t;
   s->k = 0;
+  s->e_valid_at = -1;
   return DIRAC_OK;
 }

@@ -34,18 +34,24 @@ struct FusedArgs {
   typename P::Ratio ry, rz;
   HalfFields<P> hu, hl;     // upper / lower half-step fields
   FieldDesc f;
+  // non-null: accumulate the conserved functional of the new state (per block
+  // [sum |psi|^2, Re sum_lower conj(G) S'_G]; E = first + r_x second)
+  double* e_partials;
 };
+constexpr int kFusedEMaxBlocks = 4096;  // capacity of the per-block E partials
 // (2+1)D fused kernel geometry
 constexpr int kFused2dWarps = 8;   // independent x strips per block
 constexpr int kCore = 30;          // interior lanes of a 32-lane strip
 
+// returns the number of blocks launched
 template <class P, int DIMS>
-void launch_fused(const FusedArgs<P>& a, cudaStream_t s);
+int launch_fused(const FusedArgs<P>& a, cudaStream_t s);
 
 // Two time steps per pass of the (2+1)D fused kernel (fields without time
 // dependence: uniform / Klein-step / soft-core coefficients, no or constant
-// links).  Returns false, launching nothing, for other field paths.
-bool launch_fused2d_tb2(const FusedArgs<F32>& a, cudaStream_t s);
+// links).  Returns the number of blocks launched, or 0, launching nothing,
+// for other field paths.
+int launch_fused2d_tb2(const FusedArgs<F32>& a, cudaStream_t s);
 
 // Several simulations (same dims and time-independent field modes) in one
 // persistent launch of the fused kernels.
@@ -86,6 +92,8 @@ template <class P, int DIMS>
 void launch_observables(const ObsArgs<P>& a, int blocks, cudaStream_t s);
 // fixed-order sum of partials[nblocks][5] into out[5]
 void launch_finish_sums(const double* partials, int nblocks, double* out, cudaStream_t s);
+// fixed-order sum of partials[nblocks][2] into out[2]
+void launch_finish_sums2(const double* partials, int nblocks, double* out, cudaStream_t s);
 
 // table of plane-wave link factors exp(-i phi) for both half-steps of one time
 // step: tab[half * n + H], H = half-lattice coordinate along `axis`, n = 2 N_axis

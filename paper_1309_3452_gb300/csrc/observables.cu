@@ -124,6 +124,16 @@ __global__ void __launch_bounds__(256) observables_kernel(const ObsArgs<P> a) {
   block_reduce_store<kObsSums>(acc, a.partials + b * kObsSums);
 }
 
+__global__ void finish_sums2_kernel(const double* partials, int nblocks, double* out) {
+  const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;
+  if (k >= 2) return;
+  double x = 0.0;
+  for (int b = lane; b < nblocks; b += 32) x += partials[2LL * b + k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  if (lane == 0) out[k] = x;
+}
+
 template <class P>
 __global__ void link_table_kernel(typename P::Link* tab, int n, const FieldDesc f, int dims, int axis,
                                   int pol, double t_up, double t_lo) {
@@ -191,6 +201,10 @@ template void launch_link_table<F64>(F64::Link*, int, const FieldDesc&, int, int
                                      cudaStream_t);
 template void launch_link_table<F32>(F32::Link*, int, const FieldDesc&, int, int, int, double, double,
                                      cudaStream_t);
+
+void launch_finish_sums2(const double* partials, int nblocks, double* out, cudaStream_t s) {
+  finish_sums2_kernel<<<1, 64, 0, s>>>(partials, nblocks, out);
+}
 
 void launch_finish_sums(const double* partials, int nblocks, double* out, cudaStream_t s) {
   finish_sums_kernel<<<1, 32 * kObsSums, 0, s>>>(partials, nblocks, out);

@@ -112,7 +112,7 @@ __host__ __device__ __forceinline__ long long items3d(const int (&N)[3], int chu
 // `a` may live in the constant bank (kernel parameter) or in shared memory.
 template <class P, int COEF, int LINK>
 __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long item, const Thread3d& th,
-                                             unsigned char* smem_raw) {
+                                             unsigned char* smem_raw, float& e_n, float& e_c) {
   using C = typename P::cplx;
   // every tile is double-buffered by level parity: slot [k & 1] holds level k
   C (*sC)[2][kSlots] = reinterpret_cast<C (*)[2][kSlots]>(smem_raw);  // old C(k)
@@ -126,6 +126,7 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
   const long long tiles = (long long)tiles_x * ((Ny + CY - 1) / CY);
   const bool iso = a.iso != 0;
   const long long nxy = (long long)Nx * Ny;
+  const bool want_e = a.e_partials != nullptr;
   {
     const long long chunk = item / tiles, tile = item - chunk * tiles;
     const int z0 = (int)chunk * a.chunk;
@@ -210,26 +211,38 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
       // (interior warps only: nothing needs the halo's lower values)
       if (!th.halo) {
       const C nA0 = sA[pk][0][t], nA1 = sA[pk][1][t];
-      C nC0, nC1, nD0, nD1;
+      C nC0, nC1, nD0, nD1, S;
+      const bool acc = want_e && core && k >= z0;  // this cell's new values count towards E
       {
         C nb[6] = {nB0k, sB[pk][0][sxm], nB1k, sB[pk][1][sym], nA0n, nA0};
         const int H[3] = {hx, hy, 2 * zk + 1};
-        nC0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 4, oC0, nb, H, ok, a.pstride);
+        nC0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 4, oC0, nb, H, ok, a.pstride, &S);
+        if (acc) e_c = fmaf(nC0.x, S.x, fmaf(nC0.y, S.y, e_c));
       }
       {
         C nb[6] = {sB[pk][1][sxp], nB1k, sB[pk][0][syp], nB0k, nA1n, nA1};
         const int H[3] = {hx + 1, hy + 1, 2 * zk + 1};
-        nC1 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 5, oC1, nb, H, ok, a.pstride);
+        nC1 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 5, oC1, nb, H, ok, a.pstride, &S);
+        if (acc) e_c = fmaf(nC1.x, S.x, fmaf(nC1.y, S.y, e_c));
       }
       {
         C nb[6] = {sA[pk][0][sxp], nA0, nA1, sA[pk][1][sym], nB0k, sB[pm][0][t]};
         const int H[3] = {hx + 1, hy, 2 * zk};
-        nD0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 6, sD[pk][0][t], nb, H, ok, a.pstride);
+        nD0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 6, sD[pk][0][t], nb, H, ok, a.pstride,
+                                            &S);
+        if (acc) e_c = fmaf(nD0.x, S.x, fmaf(nD0.y, S.y, e_c));
       }
       {
         C nb[6] = {nA1, sA[pk][1][sxm], sA[pk][0][syp], nA0, nB1k, sB[pm][1][t]};
         const int H[3] = {hx, hy + 1, 2 * zk};
-        nD1 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 7, sD[pk][1][t], nb, H, ok, a.pstride);
+        nD1 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 7, sD[pk][1][t], nb, H, ok, a.pstride,
+                                            &S);
+        if (acc) e_c = fmaf(nD1.x, S.x, fmaf(nD1.y, S.y, e_c));
+      }
+      if (want_e && core) {
+        auto n2 = [](C v) { return fmaf(v.x, v.x, v.y * v.y); };
+        if (k >= z0) e_n += ((n2(nB0k) + n2(nB1k)) + (n2(nC0) + n2(nC1))) + (n2(nD0) + n2(nD1));
+        if (k + 1 < z1) e_n += n2(nA0n) + n2(nA1n);
       }
       if (core) {
         if (k >= z0) {
@@ -252,13 +265,47 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
   }
 }
 
+// FP64 block reduction of the two conserved-functional accumulators into
+// out[blockIdx.x][2] (all threads of the block call it)
+__device__ __forceinline__ void block_store_e(float e_n, float e_c, double* out) {
+  __shared__ double red[32][2];
+  double n = e_n, c = e_c;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n += __shfl_down_sync(0xffffffffu, n, o);
+    c += __shfl_down_sync(0xffffffffu, c, o);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    red[w][0] = n;
+    red[w][1] = c;
+  }
+  __syncthreads();
+  if (w == 0) {
+    n = lane < nw ? red[lane][0] : 0.0;
+    c = lane < nw ? red[lane][1] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      n += __shfl_down_sync(0xffffffffu, n, o);
+      c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    if (lane == 0) {
+      out[2LL * blockIdx.x] = n;
+      out[2LL * blockIdx.x + 1] = c;
+    }
+  }
+}
+
 template <class P, int COEF, int LINK>
 __global__ void __launch_bounds__(kThreads3d, 2) fused3d_kernel(const FusedArgs<P> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Thread3d th = thread3d();
   const long long items = items3d(a.N, a.chunk);
+  float e_n = 0.0f, e_c = 0.0f;
   for (long long item = blockIdx.x; item < items; item += a.workers)
-    fused3d_item<P, COEF, LINK>(a, item, th, smem_raw);
+    fused3d_item<P, COEF, LINK>(a, item, th, smem_raw, e_n, e_c);
+  if (a.e_partials) block_store_e(e_n, e_c, a.e_partials);
 }
 
 // simulation of global item g: the last s with first[s] <= g
@@ -299,7 +346,8 @@ __global__ void __launch_bounds__(kThreads3d, 2) fused3d_batch_kernel(const Batc
       __syncthreads();
       cur = s;
     }
-    fused3d_item<P, COEF, LINK>(sa, g - b.first_item[s], th, smem_raw);
+    float e_n = 0.0f, e_c = 0.0f;  // (batched launches never accumulate the functional)
+    fused3d_item<P, COEF, LINK>(sa, g - b.first_item[s], th, smem_raw, e_n, e_c);
   }
 }
 
@@ -318,7 +366,8 @@ __device__ __forceinline__ void row2d(const FusedArgs<P>& a, bool iso, int hx, i
                                       typename P::cplx oV0, typename P::cplx oV1, typename P::cplx nU0,
                                       typename P::cplx nU1, typename P::cplx& nU0n,
                                       typename P::cplx& nU1k, typename P::cplx& nV1,
-                                      typename P::cplx& nV0) {
+                                      typename P::cplx& nV0, typename P::cplx* SV1 = nullptr,
+                                      typename P::cplx* SV0 = nullptr) {
   using C = typename P::cplx;
   // upper: u0(k+1) from v0(k+1) (x), v1(k+1), v1(k) (y); u1(k) from v1(k) (x), v0(k+1), v0(k) (y)
   {
@@ -335,19 +384,20 @@ __device__ __forceinline__ void row2d(const FusedArgs<P>& a, bool iso, int hx, i
   {
     C nb[6] = {nU1k, shfl_up1(nU1k), nU0n, nU0, nU1k, nU1k};
     const int H[3] = {hx, 2 * yk + 1, 0};
-    nV1 = site_update<P, 2, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 3, oV1, nb, H, ok, a.pstride);
+    nV1 = site_update<P, 2, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 3, oV1, nb, H, ok, a.pstride, SV1);
   }
   {
     C nb[6] = {shfl_down1(nU0), nU0, nU1k, nU1, nU0, nU0};
     const int H[3] = {hx + 1, 2 * yk, 0};
-    nV0 = site_update<P, 2, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 2, oV0, nb, H, ok, a.pstride);
+    nV0 = site_update<P, 2, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 2, oV0, nb, H, ok, a.pstride, SV0);
   }
 }
 
 // One work item (one 32-cell strip over one chunk of rows) of one simulation,
 // processed by one warp.
 template <class P, int COEF, int LINK>
-__device__ __forceinline__ void fused2d_item(const FusedArgs<P>& a, long long item, int lane) {
+__device__ __forceinline__ void fused2d_item(const FusedArgs<P>& a, long long item, int lane, float& e_n,
+                                             float& e_c) {
   using C = typename P::cplx;
   const int Nx = a.N[0], Ny = a.N[1];
   const int strips = (Nx + kCore - 1) / kCore;
@@ -381,16 +431,24 @@ __device__ __forceinline__ void fused2d_item(const FusedArgs<P>& a, long long it
     const long long ok = (long long)yk * Nx + x, on = (long long)yn * Nx + x;
     C pU0 = U0, pV0 = V0n, pV1 = V1n, pU1 = U1;  // next row, loaded while this one computes
     if (k + 1 < y1) load(k + 1, pU0, pV0, pV1, pU1);
-    C nU0n, nU1k, nV1, nV0;
+    C nU0n, nU1k, nV1, nV0, S1, S0;
     row2d<P, COEF, LINK>(a, iso, hx, yk, yn, ok, on, U0, V0n, V1n, U1, oV0, oV1, nU0, nU1, nU0n, nU1k,
-                         nV1, nV0);
+                         nV1, nV0, &S1, &S0);
     if (core) {
       if (k >= y0) {
         a.out[1][ok] = nU1k;
         a.out[2][ok] = nV0;
         a.out[3][ok] = nV1;
+        if (a.e_partials) {
+          e_n += (fmaf(nU1k.x, nU1k.x, nU1k.y * nU1k.y) + fmaf(nV0.x, nV0.x, nV0.y * nV0.y)) +
+                 fmaf(nV1.x, nV1.x, nV1.y * nV1.y);
+          e_c = fmaf(nV1.x, S1.x, fmaf(nV1.y, S1.y, fmaf(nV0.x, S0.x, fmaf(nV0.y, S0.y, e_c))));
+        }
       }
-      if (k + 1 < y1) a.out[0][on] = nU0n;
+      if (k + 1 < y1) {
+        a.out[0][on] = nU0n;
+        if (a.e_partials) e_n += fmaf(nU0n.x, nU0n.x, nU0n.y * nU0n.y);
+      }
     }
     oV0 = V0n;
     oV1 = V1n;
@@ -411,7 +469,8 @@ __device__ __forceinline__ void fused2d_item(const FusedArgs<P>& a, long long it
 constexpr int kCoreTb = 28;
 
 template <class P, int COEF, int LINK>
-__device__ __forceinline__ void fused2d_tb2_item(const FusedArgs<P>& a, long long item, int lane) {
+__device__ __forceinline__ void fused2d_tb2_item(const FusedArgs<P>& a, long long item, int lane,
+                                                 float& e_n, float& e_c) {
   using C = typename P::cplx;
   const int Nx = a.N[0], Ny = a.N[1];
   const int strips = (Nx + kCoreTb - 1) / kCoreTb;
@@ -453,16 +512,24 @@ __device__ __forceinline__ void fused2d_tb2_item(const FusedArgs<P>& a, long lon
       // step 2 at row k-1: its loads are step 1's u0, v0, v1 of row k and u1 of row k-1
       const int ym = wrapy(k - 1);
       const long long om = (long long)ym * Nx + x;
-      C tU0n, tU1k, tV1, tV0;
+      C tU0n, tU1k, tV1, tV0, S1, S0;
       row2d<P, COEF, LINK>(a, iso, hx, ym, yk, om, ok, nU0, sV0, sV1, nU1, qV0, qV1, mU0, mU1, tU0n, tU1k,
-                           tV1, tV0);
+                           tV1, tV0, &S1, &S0);
       if (core) {
         if (k - 1 >= y0) {
           a.out[1][om] = tU1k;
           a.out[2][om] = tV0;
           a.out[3][om] = tV1;
+          if (a.e_partials) {
+            e_n += (fmaf(tU1k.x, tU1k.x, tU1k.y * tU1k.y) + fmaf(tV0.x, tV0.x, tV0.y * tV0.y)) +
+                   fmaf(tV1.x, tV1.x, tV1.y * tV1.y);
+            e_c = fmaf(tV1.x, S1.x, fmaf(tV1.y, S1.y, fmaf(tV0.x, S0.x, fmaf(tV0.y, S0.y, e_c))));
+          }
         }
-        if (k < y1) a.out[0][ok] = tU0n;
+        if (k < y1) {
+          a.out[0][ok] = tU0n;
+          if (a.e_partials) e_n += fmaf(tU0n.x, tU0n.x, tU0n.y * tU0n.y);
+        }
       }
       mU0 = tU0n;
       mU1 = tU1k;
@@ -485,8 +552,10 @@ __global__ void __launch_bounds__(32 * kFused2dWarps) fused2d_kernel(const Fused
   const int lane = threadIdx.x & 31;
   const long long worker = (long long)blockIdx.x * kFused2dWarps + (threadIdx.x >> 5);
   const long long items = items2d(a.N, a.chunk);
+  float e_n = 0.0f, e_c = 0.0f;
   for (long long item = worker; item < items; item += a.workers)  // uniform per warp
-    fused2d_item<P, COEF, LINK>(a, item, lane);
+    fused2d_item<P, COEF, LINK>(a, item, lane, e_n, e_c);
+  if (a.e_partials) block_store_e(e_n, e_c, a.e_partials);
 }
 
 template <class P, int COEF, int LINK>
@@ -494,8 +563,10 @@ __global__ void __launch_bounds__(32 * kFused2dWarps) fused2d_tb2_kernel(const F
   const int lane = threadIdx.x & 31;
   const long long worker = (long long)blockIdx.x * kFused2dWarps + (threadIdx.x >> 5);
   const long long items = (long long)((a.N[0] + kCoreTb - 1) / kCoreTb) * ((a.N[1] + a.chunk - 1) / a.chunk);
+  float e_n = 0.0f, e_c = 0.0f;
   for (long long item = worker; item < items; item += a.workers)  // uniform per warp
-    fused2d_tb2_item<P, COEF, LINK>(a, item, lane);
+    fused2d_tb2_item<P, COEF, LINK>(a, item, lane, e_n, e_c);
+  if (a.e_partials) block_store_e(e_n, e_c, a.e_partials);
 }
 
 template <class P, int COEF, int LINK>
@@ -513,7 +584,8 @@ __global__ void __launch_bounds__(32 * kFused2dWarps) fused2d_batch_kernel(const
       __syncwarp();
       cur = s;
     }
-    fused2d_item<P, COEF, LINK>(sa[w], g - b.first_item[s], lane);
+    float e_n = 0.0f, e_c = 0.0f;  // (batched launches never accumulate the functional)
+    fused2d_item<P, COEF, LINK>(sa[w], g - b.first_item[s], lane, e_n, e_c);
   }
 }
 
@@ -571,24 +643,27 @@ int workers2d() {
 }
 
 template <int COEF, int LINK>
-void launch3d(FusedArgs<F32> a, cudaStream_t s) {
+int launch3d(FusedArgs<F32> a, cudaStream_t s) {
   auto k = fused3d_kernel<F32, COEF, LINK>;
   const int resident = workers3d<fused3d_kernel<F32, COEF, LINK>>();
   a.chunk = fused_chunk(3, a.N);
   const long long items = items3d(a.N, a.chunk);
   a.workers = (int)(items < resident ? items : resident);
   k<<<(unsigned)a.workers, kThreads3d, kSmem3d, s>>>(a);
+  return a.workers;
 }
 
 template <int COEF, int LINK>
-void launch2d(FusedArgs<F32> a, cudaStream_t s) {
+int launch2d(FusedArgs<F32> a, cudaStream_t s) {
   auto k = fused2d_kernel<F32, COEF, LINK>;
   const int warps = workers2d<fused2d_kernel<F32, COEF, LINK>>();
   a.chunk = fused_chunk(2, a.N);
   const long long items = items2d(a.N, a.chunk);
   const long long w = items < warps ? items : warps;
   a.workers = (int)w;
-  k<<<(unsigned)((w + kFused2dWarps - 1) / kFused2dWarps), 32 * kFused2dWarps, 0, s>>>(a);
+  const int blocks = (int)((w + kFused2dWarps - 1) / kFused2dWarps);
+  k<<<(unsigned)blocks, 32 * kFused2dWarps, 0, s>>>(a);
+  return blocks;
 }
 
 template <int COEF, int LINK>
@@ -609,13 +684,13 @@ void launch2d_batch(BatchArgs<F32> b, long long total, cudaStream_t s) {
 }
 
 template <int DIMS, int COEF, int LINK>
-void launch_dims(const FusedArgs<F32>& a, cudaStream_t s) {
-  if (DIMS == 3) launch3d<COEF, LINK>(a, s);
-  else launch2d<COEF, LINK>(a, s);
+int launch_dims(const FusedArgs<F32>& a, cudaStream_t s) {
+  if (DIMS == 3) return launch3d<COEF, LINK>(a, s);
+  return launch2d<COEF, LINK>(a, s);
 }
 
 template <int DIMS>
-void dispatch(const FusedArgs<F32>& a, cudaStream_t s) {
+int dispatch(const FusedArgs<F32>& a, cudaStream_t s) {
   const int c = a.hu.coef_mode, l = a.hu.link_mode;
   if (c == COEF_GENERAL || l == LINK_GENERAL) return launch_dims<DIMS, kAnyMode, kAnyMode>(a, s);
   if (c == COEF_SOFTCORE && l == LINK_NONE) return launch_dims<DIMS, COEF_SOFTCORE, LINK_NONE>(a, s);
@@ -630,7 +705,7 @@ void dispatch(const FusedArgs<F32>& a, cudaStream_t s) {
 }
 
 template <int COEF, int LINK>
-void launch2d_tb2(FusedArgs<F32> a, cudaStream_t s) {
+int launch2d_tb2(FusedArgs<F32> a, cudaStream_t s) {
   auto k = fused2d_tb2_kernel<F32, COEF, LINK>;
   const int warps = workers2d<fused2d_tb2_kernel<F32, COEF, LINK>>();
   const long long strips = (a.N[0] + kCoreTb - 1) / kCoreTb;
@@ -638,7 +713,9 @@ void launch2d_tb2(FusedArgs<F32> a, cudaStream_t s) {
   const long long items = strips * ((a.N[1] + a.chunk - 1) / a.chunk);
   const long long w = items < warps ? items : warps;
   a.workers = (int)w;
-  k<<<(unsigned)((w + kFused2dWarps - 1) / kFused2dWarps), 32 * kFused2dWarps, 0, s>>>(a);
+  const int blocks = (int)((w + kFused2dWarps - 1) / kFused2dWarps);
+  k<<<(unsigned)blocks, 32 * kFused2dWarps, 0, s>>>(a);
+  return blocks;
 }
 
 template <int DIMS, int COEF, int LINK>
@@ -649,15 +726,14 @@ void batch_dims(const BatchArgs<F32>& b, long long total, cudaStream_t s) {
 
 }  // namespace
 
-bool launch_fused2d_tb2(const FusedArgs<F32>& a, cudaStream_t s) {
+int launch_fused2d_tb2(const FusedArgs<F32>& a, cudaStream_t s) {
   const int c = a.hu.coef_mode, l = a.hu.link_mode;
-  if (c == COEF_UNIFORM && l == LINK_NONE) launch2d_tb2<COEF_UNIFORM, LINK_NONE>(a, s);
-  else if (c == COEF_STEP && l == LINK_NONE) launch2d_tb2<COEF_STEP, LINK_NONE>(a, s);
-  else if (c == COEF_UNIFORM && l == LINK_CONST) launch2d_tb2<COEF_UNIFORM, LINK_CONST>(a, s);
-  else if (c == COEF_STEP && l == LINK_CONST) launch2d_tb2<COEF_STEP, LINK_CONST>(a, s);
-  else if (c == COEF_SOFTCORE && l == LINK_NONE) launch2d_tb2<COEF_SOFTCORE, LINK_NONE>(a, s);
-  else return false;
-  return true;
+  if (c == COEF_UNIFORM && l == LINK_NONE) return launch2d_tb2<COEF_UNIFORM, LINK_NONE>(a, s);
+  if (c == COEF_STEP && l == LINK_NONE) return launch2d_tb2<COEF_STEP, LINK_NONE>(a, s);
+  if (c == COEF_UNIFORM && l == LINK_CONST) return launch2d_tb2<COEF_UNIFORM, LINK_CONST>(a, s);
+  if (c == COEF_STEP && l == LINK_CONST) return launch2d_tb2<COEF_STEP, LINK_CONST>(a, s);
+  if (c == COEF_SOFTCORE && l == LINK_NONE) return launch2d_tb2<COEF_SOFTCORE, LINK_NONE>(a, s);
+  return 0;
 }
 
 int fused_chunk(int dims, const int N[3]) {
@@ -694,12 +770,12 @@ void launch_fused_batch<F32, 2>(const BatchArgs<F32>& b, long long total, int co
 }
 
 template <>
-void launch_fused<F32, 3>(const FusedArgs<F32>& a, cudaStream_t s) {
-  dispatch<3>(a, s);
+int launch_fused<F32, 3>(const FusedArgs<F32>& a, cudaStream_t s) {
+  return dispatch<3>(a, s);
 }
 template <>
-void launch_fused<F32, 2>(const FusedArgs<F32>& a, cudaStream_t s) {
-  dispatch<2>(a, s);
+int launch_fused<F32, 2>(const FusedArgs<F32>& a, cudaStream_t s) {
+  return dispatch<2>(a, s);
 }
 
 }  // namespace dirac

@@ -287,3 +287,25 @@ def test_temporal_blocking_2d_bit_identical(D, N, case, monkeypatch):
             outs.append(s.get_spinor())
         monkeypatch.delenv("DIRAC_NO_TEMPORAL_BLOCKING", raising=False)
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("dims,N", [(3, (33, 29, 21)), (2, (70, 45))])
+@pytest.mark.parametrize("case", ["free", "klein", "A_const", "softcore", "laser"])
+@pytest.mark.parametrize("nsteps", [7, 10])
+def test_fused_functional_matches_reduction(D, dims, N, case, nsteps, monkeypatch):
+    """The last fused launch of dirac_step accumulates E of the new state
+    (sum |psi|^2 + r_x Re sum_lower conj(G) S'_G, with the S' its own lower
+    half-step formed); it must equal the separate reduction of that state."""
+    full = tuple(N) + ((1,) if dims == 2 else ())
+    prob = W.Problem(dims, full, (1.0, 1.0, 1.0), 0.9 * W.stability_limit(dims), 0.45,
+                     field_cases(dims, N)[case])
+    psi = W.random_state(prob, 12)
+    with D.Sim(prob, D.FP32) as s:
+        s.set_spinor(psi)
+        s.step(nsteps)
+        E_fused, n_fused = s.norm()
+        monkeypatch.setenv("DIRAC_NO_FUSED_NORM", "1")
+        E_red, n_red = s.norm()
+        monkeypatch.delenv("DIRAC_NO_FUSED_NORM")
+    assert abs(E_fused - E_red) <= 2e-7 * abs(E_red)
+    assert abs(n_fused - n_red) <= 2e-7 * n_red
