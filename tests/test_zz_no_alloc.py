@@ -64,8 +64,12 @@ def test_noalloc_norm_matches_dirac_norm_twice(env, dims, precision):
             tstate, ptrs = device_planes(torch, prob, s.get_spinor(), prec, D)
             E, naive = noalloc_norm(torch, L, D, prob, ptrs, s.time, prec)
             del tstate
-            assert abs(E - E_ref) <= 1e-13 * abs(E_ref)
-            assert abs(naive - naive_ref) <= 1e-13 * naive_ref
+            # FP64: the same reduction on both sides; FP32: after steps dirac_norm
+            # returns the functional accumulated by the last step's kernel (another
+            # summation order), the tolerance of the fused-functional tests
+            tol = 1e-13 if prec == D.FP64 else 2e-7
+            assert abs(E - E_ref) <= tol * abs(E_ref)
+            assert abs(naive - naive_ref) <= tol * naive_ref
             s.step(13)
 
 
