@@ -129,6 +129,23 @@ KERNEL_SOURCES = {  # the files that determine each timed kernel's code
 }
 
 
+def max_over_ranks(value, dist, device=None):
+    """The maximum of a per-rank float over all ranks (the slowest rank's
+    time); returns the local value when not distributed."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_glups(lups_per_rank, world, seconds):
+    """Replicas: every rank advances its own simulation, so the job's
+    throughput is world x the per-rank site updates over the slowest rank's time."""
+    return world * lups_per_rank / seconds / 1e9
+
+
 def kernel_source_hash(kernel):
     h = hashlib.sha1()
     for name in KERNEL_SOURCES[kernel]:
@@ -342,14 +359,10 @@ def main():
     launches = sim.launches - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     norm_ms = [a.elapsed_time(b) for a, b in norm_ev]
-    total_ms = sum(step_ms)
-    if dist is not None:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     ms_per_step = total_ms / args.steps
     lups = prob.cells * n
-    value = world * lups / (ms_per_step / 1e3) / 1e9
+    value = whole_job_glups(lups, world, ms_per_step / 1e3)
 
     # dominant kernel: the time-step kernels; per launch = one full time step
     stencil_ms = (sum(step_ms) - sum(norm_ms)) / args.steps / n
@@ -390,11 +403,8 @@ def main():
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
     e2e_ms_step = statistics.median(e2e_ms) if e2e_ms else float("nan")
-    if dist is not None:
-        tt = torch.tensor([e2e_ms_step], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms_step = float(tt.item())
-    e2e = None if on_device else {"value": world * lups / (e2e_ms_step / 1e3) / 1e9, "unit": "GLUPS",
+    e2e_ms_step = max_over_ranks(e2e_ms_step, dist, "cuda")
+    e2e = None if on_device else {"value": whole_job_glups(lups, world, e2e_ms_step / 1e3), "unit": "GLUPS",
                                   "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 8 * 5,
                                   "ms_per_step": e2e_ms_step}
 
