@@ -98,10 +98,47 @@ __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b)
 __device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
+// Packed pairs of FP32 (the .f32x2 forms of sm_100 and later): one
+// instruction rounds both lanes exactly as two scalar instructions would.
+__device__ __forceinline__ unsigned long long pbits(float2 v) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+  return r;
+}
+__device__ __forceinline__ float2 punbits(unsigned long long r) {
+  float2 v;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+  return v;
+}
+__device__ __forceinline__ float2 padd(float2 a, float2 b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pbits(a)), "l"(pbits(b)));
+  return punbits(r);
+}
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pbits(a)), "l"(pbits(b)));
+  return punbits(r);
+}
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pbits(a)), "l"(pbits(b)));
+  return punbits(r);
+}
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(pbits(a)), "l"(pbits(b)), "l"(pbits(c)));
+  return punbits(r);
+}
+
 template <class C>
 __device__ __forceinline__ C csub(C a, C b) { return cmk(rsub(a.x, b.x), rsub(a.y, b.y)); }
 template <class C>
 __device__ __forceinline__ C cadd(C a, C b) { return cmk(radd(a.x, b.x), radd(a.y, b.y)); }
+template <>
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return psub(a, b); }
+template <>
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return padd(a, b); }
 
 // ------------------------------------------------------------------ links
 __device__ __forceinline__ double2 link_mul(const F64::Link& L, double2 v) {
@@ -158,25 +195,29 @@ __device__ __forceinline__ double2 combine<F64, 2>(double2 dx, double2 dy, doubl
   return cadd(dx, ty);
 }
 __device__ __forceinline__ float2 ratio_mul(const F32::Ratio& r, float2 t) {
-  return cmk(rfma(r.hi, t.x, rmul(r.lo, t.x)), rfma(r.hi, t.y, rmul(r.lo, t.y)));
+  return pfma(make_float2(r.hi, r.hi), t, pmul(make_float2(r.lo, r.lo), t));
 }
+// (dx + s_y dy) + s_z dz; with iso the y term is two scalar adds (the factor
+// +-i swaps the lanes) and the z term one packed add
 template <>
 __device__ __forceinline__ float2 combine<F32, 3>(float2 dx, float2 dy, float2 dz, int p, bool iso,
                                                   const F32::Ratio& ry, const F32::Ratio& rz) {
-  float2 ty = p ? cmk(-dy.y, dy.x) : cmk(dy.y, -dy.x);
-  float2 tz = p ? cmk(-dz.x, -dz.y) : dz;
   if (!iso) {
-    ty = ratio_mul(ry, ty);
-    tz = ratio_mul(rz, tz);
+    float2 ty = p ? cmk(-dy.y, dy.x) : cmk(dy.y, -dy.x);
+    float2 tz = p ? cmk(-dz.x, -dz.y) : dz;
+    return padd(padd(dx, ratio_mul(ry, ty)), ratio_mul(rz, tz));
   }
-  return cadd(cadd(dx, ty), tz);
+  const float2 u = p ? cmk(rsub(dx.x, dy.y), radd(dx.y, dy.x)) : cmk(radd(dx.x, dy.y), rsub(dx.y, dy.x));
+  return p ? psub(u, dz) : padd(u, dz);
 }
 template <>
 __device__ __forceinline__ float2 combine<F32, 2>(float2 dx, float2 dy, float2, int p, bool iso,
                                                   const F32::Ratio& ry, const F32::Ratio&) {
-  float2 ty = p ? cmk(-dy.y, dy.x) : cmk(dy.y, -dy.x);
-  if (!iso) ty = ratio_mul(ry, ty);
-  return cadd(dx, ty);
+  if (!iso) {
+    float2 ty = p ? cmk(-dy.y, dy.x) : cmk(dy.y, -dy.x);
+    return padd(dx, ratio_mul(ry, ty));
+  }
+  return p ? cmk(rsub(dx.x, dy.y), radd(dx.y, dy.x)) : cmk(radd(dx.x, dy.y), rsub(dx.y, dy.x));
 }
 
 // F+ = alpha F - gamma S'  (the Cayley form of Eqs. ss1-ss4:
@@ -187,12 +228,16 @@ __device__ __forceinline__ double2 apply(const F64::Coef& c, double2 F, double2 
   return cmk(re, im);
 }
 __device__ __forceinline__ float2 apply(const F32::Coef& c, float2 F, float2 S) {
-  // small (lo) products first, then the hi products on top
-  float re = rfma(c.a_lo.x, F.x, rfma(-c.a_lo.y, F.y, rfma(-c.g_lo.x, S.x, rmul(c.g_lo.y, S.y))));
-  float im = rfma(c.a_lo.x, F.y, rfma(c.a_lo.y, F.x, rfma(-c.g_lo.x, S.y, -rmul(c.g_lo.y, S.x))));
-  re = rfma(c.a_hi.x, F.x, rfma(-c.a_hi.y, F.y, rfma(-c.g_hi.x, S.x, rfma(c.g_hi.y, S.y, re))));
-  im = rfma(c.a_hi.x, F.y, rfma(c.a_hi.y, F.x, rfma(-c.g_hi.x, S.y, rfma(-c.g_hi.y, S.x, im))));
-  return cmk(re, im);
+  // small (lo) products first, then the hi products on top; lane 0 = re, 1 = im
+  const float2 Fs = make_float2(F.y, F.x), Ss = make_float2(S.y, S.x);
+  float2 t = pmul(make_float2(c.g_lo.y, -c.g_lo.y), Ss);
+  t = pfma(make_float2(-c.g_lo.x, -c.g_lo.x), S, t);
+  t = pfma(make_float2(-c.a_lo.y, c.a_lo.y), Fs, t);
+  t = pfma(make_float2(c.a_lo.x, c.a_lo.x), F, t);
+  t = pfma(make_float2(c.g_hi.y, -c.g_hi.y), Ss, t);
+  t = pfma(make_float2(-c.g_hi.x, -c.g_hi.x), S, t);
+  t = pfma(make_float2(-c.a_hi.y, c.a_hi.y), Fs, t);
+  return pfma(make_float2(c.a_hi.x, c.a_hi.x), F, t);
 }
 
 // ------------------------------------------------------------------ fields

@@ -16,7 +16,8 @@
 //   3. computes the new A(k+1) and B(k)      (upper half-step, t -> t+dt/2),
 //   4. publishes them,
 //   5. computes the new C(k) and D(k)        (lower half-step, t -> t+dt),
-// A run of levels starts one level early to rebuild that state.
+// A run of levels starts one level early to rebuild that state (the upper
+// half-step of that level only).
 //
 // (2+1)D: each warp owns a strip of 32 cells in x (30 interior) and marches
 // along y with the same pipeline (u0 ~ A, u1 ~ B, v1 ~ C, v0 ~ D with y as the
@@ -208,56 +209,55 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
       __syncthreads();
 
       // lower half-step: C(k) from A(k+1), A(k), B(k); D(k) from B(k), B(k-1), A(k)
-      // (interior warps only: nothing needs the halo's lower values)
+      // (interior warps only: nothing needs the halo's lower values; the
+      // first level of a run only rebuilds A(z0) and B(z0-1))
       if (!th.halo) {
-      const C nA0 = sA[pk][0][t], nA1 = sA[pk][1][t];
-      C nC0, nC1, nD0, nD1, S;
-      const bool acc = want_e && core && k >= z0;  // this cell's new values count towards E
-      {
-        C nb[6] = {nB0k, sB[pk][0][sxm], nB1k, sB[pk][1][sym], nA0n, nA0};
-        const int H[3] = {hx, hy, 2 * zk + 1};
-        nC0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 4, oC0, nb, H, ok, a.pstride, &S);
-        if (acc) e_c = fmaf(nC0.x, S.x, fmaf(nC0.y, S.y, e_c));
-      }
-      {
-        C nb[6] = {sB[pk][1][sxp], nB1k, sB[pk][0][syp], nB0k, nA1n, nA1};
-        const int H[3] = {hx + 1, hy + 1, 2 * zk + 1};
-        nC1 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 5, oC1, nb, H, ok, a.pstride, &S);
-        if (acc) e_c = fmaf(nC1.x, S.x, fmaf(nC1.y, S.y, e_c));
-      }
-      {
-        C nb[6] = {sA[pk][0][sxp], nA0, nA1, sA[pk][1][sym], nB0k, sB[pm][0][t]};
-        const int H[3] = {hx + 1, hy, 2 * zk};
-        nD0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 6, sD[pk][0][t], nb, H, ok, a.pstride,
-                                            &S);
-        if (acc) e_c = fmaf(nD0.x, S.x, fmaf(nD0.y, S.y, e_c));
-      }
-      {
-        C nb[6] = {nA1, sA[pk][1][sxm], sA[pk][0][syp], nA0, nB1k, sB[pm][1][t]};
-        const int H[3] = {hx, hy + 1, 2 * zk};
-        nD1 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 7, sD[pk][1][t], nb, H, ok, a.pstride,
-                                            &S);
-        if (acc) e_c = fmaf(nD1.x, S.x, fmaf(nD1.y, S.y, e_c));
-      }
-      if (want_e && core) {
         auto n2 = [](C v) { return fmaf(v.x, v.x, v.y * v.y); };
-        if (k >= z0) e_n += ((n2(nB0k) + n2(nB1k)) + (n2(nC0) + n2(nC1))) + (n2(nD0) + n2(nD1));
-        if (k + 1 < z1) e_n += n2(nA0n) + n2(nA1n);
-      }
-      if (core) {
         if (k >= z0) {
-          a.out[2][ok] = nB0k;
-          a.out[3][ok] = nB1k;
-          a.out[4][ok] = nC0;
-          a.out[5][ok] = nC1;
-          a.out[6][ok] = nD0;
-          a.out[7][ok] = nD1;
+          const C nA0 = sA[pk][0][t], nA1 = sA[pk][1][t];
+          C nC0, nC1, nD0, nD1, S;
+          const bool acc = want_e && core;  // this cell's new values count towards E
+          {
+            C nb[6] = {nB0k, sB[pk][0][sxm], nB1k, sB[pk][1][sym], nA0n, nA0};
+            const int H[3] = {hx, hy, 2 * zk + 1};
+            nC0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 4, oC0, nb, H, ok, a.pstride, &S);
+            if (acc) e_c = fmaf(nC0.x, S.x, fmaf(nC0.y, S.y, e_c));
+          }
+          {
+            C nb[6] = {sB[pk][1][sxp], nB1k, sB[pk][0][syp], nB0k, nA1n, nA1};
+            const int H[3] = {hx + 1, hy + 1, 2 * zk + 1};
+            nC1 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 5, oC1, nb, H, ok, a.pstride, &S);
+            if (acc) e_c = fmaf(nC1.x, S.x, fmaf(nC1.y, S.y, e_c));
+          }
+          {
+            C nb[6] = {sA[pk][0][sxp], nA0, nA1, sA[pk][1][sym], nB0k, sB[pm][0][t]};
+            const int H[3] = {hx + 1, hy, 2 * zk};
+            nD0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 6, sD[pk][0][t], nb, H, ok,
+                                                a.pstride, &S);
+            if (acc) e_c = fmaf(nD0.x, S.x, fmaf(nD0.y, S.y, e_c));
+          }
+          {
+            C nb[6] = {nA1, sA[pk][1][sxm], sA[pk][0][syp], nA0, nB1k, sB[pm][1][t]};
+            const int H[3] = {hx, hy + 1, 2 * zk};
+            nD1 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 7, sD[pk][1][t], nb, H, ok,
+                                                a.pstride, &S);
+            if (acc) e_c = fmaf(nD1.x, S.x, fmaf(nD1.y, S.y, e_c));
+          }
+          if (acc) e_n += ((n2(nB0k) + n2(nB1k)) + (n2(nC0) + n2(nC1))) + (n2(nD0) + n2(nD1));
+          if (core) {
+            a.out[2][ok] = nB0k;
+            a.out[3][ok] = nB1k;
+            a.out[4][ok] = nC0;
+            a.out[5][ok] = nC1;
+            a.out[6][ok] = nD0;
+            a.out[7][ok] = nD1;
+          }
         }
-        if (k + 1 < z1) {
+        if (k + 1 < z1 && core) {
+          if (want_e) e_n += n2(nA0n) + n2(nA1n);
           a.out[0][on] = nA0n;
           a.out[1][on] = nA1n;
         }
-      }
       }
       cur = nxt;
     }
@@ -598,8 +598,9 @@ int sm_count() {
 
 // Chunk length (levels per item) for `tiles` items per level chunk, `levels`
 // levels and `workers` persistent workers: maximise the busy fraction of the
-// rounds times the useful fraction chunk/(chunk+1) of each item.
-int plan_chunk(long long tiles, int levels, long long workers, int min_chunk) {
+// rounds times the useful fraction chunk/(chunk+restart) of each item, where
+// `restart` is the cost of an item's extra first level in levels.
+int plan_chunk(long long tiles, int levels, long long workers, int min_chunk, double restart) {
   int best = levels;
   double best_eff = -1.0;
   for (int c = 1; c <= levels; ++c) {
@@ -608,8 +609,8 @@ int plan_chunk(long long tiles, int levels, long long workers, int min_chunk) {
     int chunks = (levels + len - 1) / len;
     long long items = tiles * chunks;
     long long rounds = (items + workers - 1) / workers;
-    // work of a round ~ len + 1 levels; total time ~ rounds * (len + 1)
-    double eff = (double)tiles * levels / ((double)rounds * workers * (len + 1));
+    // work of a round ~ len + restart levels; total time ~ rounds * (len + restart)
+    double eff = (double)tiles * levels / ((double)rounds * workers * (len + restart));
     if (eff > best_eff * 1.0001) {
       best_eff = eff;
       best = len;
@@ -709,7 +710,7 @@ int launch2d_tb2(FusedArgs<F32> a, cudaStream_t s) {
   auto k = fused2d_tb2_kernel<F32, COEF, LINK>;
   const int warps = workers2d<fused2d_tb2_kernel<F32, COEF, LINK>>();
   const long long strips = (a.N[0] + kCoreTb - 1) / kCoreTb;
-  a.chunk = plan_chunk(strips, a.N[1], warps, 32);
+  a.chunk = plan_chunk(strips, a.N[1], warps, 32, 1.0);
   const long long items = strips * ((a.N[1] + a.chunk - 1) / a.chunk);
   const long long w = items < warps ? items : warps;
   a.workers = (int)w;
@@ -740,11 +741,11 @@ int fused_chunk(int dims, const int N[3]) {
   if (dims == 3) {
     const int resident = workers3d<fused3d_kernel<F32, COEF_UNIFORM, LINK_NONE>>();
     const long long tiles = (long long)((N[0] + CX - 1) / CX) * ((N[1] + CY - 1) / CY);
-    return plan_chunk(tiles, N[2], resident, 4);
+    return plan_chunk(tiles, N[2], resident, 4, 0.5);
   }
   const int warps = workers2d<fused2d_kernel<F32, COEF_UNIFORM, LINK_NONE>>();
   const long long strips = (N[0] + kCore - 1) / kCore;
-  return plan_chunk(strips, N[1], warps, 16);
+  return plan_chunk(strips, N[1], warps, 16, 1.0);
 }
 
 long long fused_items(int dims, const int N[3], int chunk) {
