@@ -286,6 +286,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison line")
+    ap.add_argument("--plan", default="autotune", choices=["autotune", "rule"],
+                    help="launch plan: timed by dirac_autotune before the warm-up, or the built-in rule")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -332,6 +334,8 @@ def main():
     E_start, _ = sim.norm()
     if on_device:
         del dpsi
+    # launch plan (chunk lengths, one or two steps per pass): measured on this state, untimed
+    plan = dict(sim.autotune() if args.plan == "autotune" else sim.plan, source=args.plan)
 
     def one_step():
         sim.step(n)
@@ -446,7 +450,7 @@ def main():
                                                      if args.precision == "fp32" else ""),
                       "l2": f"flushed between timed steps (write of {2 * L2_BYTES >> 20} MiB); "
                             f"state {D.state_bytes(prob.dims, prob.N, prec) >> 20} MiB",
-                      "parallelism": f"replicas x{world}"},
+                      "parallelism": f"replicas x{world}", "plan": plan},
            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": launches, "clocks": clocks, "fp64_plain": fp64,
            "E_rel_drift": E_drift}

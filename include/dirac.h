@@ -190,6 +190,50 @@ dirac_status dirac_set_time(dirac_sim* sim, double t);
    (every launch of every call counts once) */
 long long dirac_kernel_launches(const dirac_sim* sim);
 
+/*
+ * Launch plan of a simulation's FP32 fused kernels (the paper has no
+ * counterpart: it only fixes what one time step computes, not how the work
+ * is cut).  Plans change the speed only, never a value of the state; the
+ * conserved functional fused into a call's last step is summed in another
+ * order and may differ in the last bits.
+ *   chunk       z levels ((3+1)D) or y rows ((2+1)D) per work item of the
+ *               one-step kernel; 0 = the built-in rule
+ *   two_step    (2+1)D: 1 = two time steps per pass whenever the fields do
+ *               not depend on time (the default), 0 = one step per pass
+ *   chunk2      rows per work item of the two-step kernel; 0 = the rule
+ *   us_per_step time per step that dirac_autotune measured for this plan
+ *               (0 when it was not measured)
+ */
+typedef struct {
+  int chunk;
+  int two_step;
+  int chunk2;
+  double us_per_step;
+} dirac_plan;
+
+/* current plan of sim (a zero plan for DIRAC_FP64 and reference-kernel
+   simulations, which have none) */
+dirac_status dirac_get_plan(const dirac_sim* sim, dirac_plan* out);
+
+/* Set the plan (us_per_step is ignored).  DIRAC_ERR_INVALID for a negative
+   chunk or chunk2, a chunk beyond the marching extent (N[2] in (3+1)D, N[1]
+   in (2+1)D), two_step other than 0/1 or two_step in (3+1)D, or any
+   non-zero plan on a simulation without fused kernels.  Synchronises the
+   simulation's stream (recorded step graphs are rebuilt). */
+dirac_status dirac_set_plan(dirac_sim* sim, const dirac_plan* plan);
+
+/*
+ * Autotuner: time the candidate plans of this simulation's fused kernels on
+ * its current state (the best chunk lengths by the built-in model, for one-
+ * and, in (2+1)D with time-independent fields, two-step passes), keep the
+ * fastest, remember it for later simulations with the same grid, field path
+ * and device (dirac_create applies a remembered plan), and copy it to *out
+ * (may be NULL).  The state and the time are unchanged; the spare state
+ * buffer is overwritten.  Synchronises the simulation's stream.  A
+ * simulation without fused kernels keeps its zero plan (DIRAC_OK).
+ */
+dirac_status dirac_autotune(dirac_sim* sim, dirac_plan* out);
+
 /* device bytes a simulation of this shape and precision allocates (without
    the optional static potential): the state, plus for DIRAC_FP32 a second
    state buffer and one complex128 conversion plane */

@@ -3,6 +3,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <utility>
 #include <vector>
@@ -29,6 +31,8 @@ struct dirac_sim {
   void* state_alt = nullptr;  // second buffer for the out-of-place fused kernels
   int fused = 0;              // one kernel per time step (FP32 without the reference flag)
   int tblock = 1;             // (2+1)D fused path: two time steps per pass when possible
+  int chunk1 = 0, chunk2 = 0; // launch plan: levels per item (one-step / two-step kernel), 0 = rule
+  double plan_us = 0;         // time per step the autotuner measured for the plan
   double2* staging = nullptr; // one canonical plane (FP32 conversions)
   double* Vstatic = nullptr;  // one real per site (plane-major, pstride)
   double* partials = nullptr;
@@ -289,6 +293,63 @@ static FusedArgs<P> fused_args(dirac_sim* s, double t) {
   return a;
 }
 
+// ------------------------------------------------------------------ launch plans
+// Plans found by dirac_autotune, per device, grid and field path; dirac_create
+// applies a remembered plan to a new simulation of the same kind.
+struct PlanKey {
+  int dev, dims, n0, n1, n2, coef, link, iso;
+  bool operator<(const PlanKey& o) const {
+    const int a[8] = {dev, dims, n0, n1, n2, coef, link, iso};
+    const int b[8] = {o.dev, o.dims, o.n0, o.n1, o.n2, o.coef, o.link, o.iso};
+    return std::lexicographical_compare(a, a + 8, b, b + 8);
+  }
+};
+static std::mutex g_plan_mu;
+static std::map<PlanKey, dirac_plan> g_plans;
+
+static PlanKey plan_key(const dirac_sim* s) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return PlanKey{dev, s->dims, s->N[0], s->N[1], s->N[2], s->coef_mode, s->link_mode, s->iso};
+}
+
+static void drop_graphs(dirac_sim* s) {
+  for (int k = 0; k < 2; ++k) {
+    if (s->graph[k]) cudaGraphExecDestroy(s->graph[k]);
+    s->graph[k] = nullptr;
+    s->graph_state[k] = nullptr;
+  }
+}
+
+static dirac_plan plan_of(const dirac_sim* s) {
+  dirac_plan p;
+  std::memset(&p, 0, sizeof(p));
+  if (!s->fused) return p;
+  p.chunk = s->chunk1;
+  p.two_step = s->dims == 2 ? s->tblock : 0;
+  p.chunk2 = s->dims == 2 ? s->chunk2 : 0;
+  p.us_per_step = s->plan_us;
+  return p;
+}
+
+static const char* plan_problem(const dirac_sim* s, const dirac_plan& p) {
+  if (!s->fused)
+    return (p.chunk || p.two_step || p.chunk2) ? "this simulation has no fused kernels to plan" : nullptr;
+  const int extent = s->dims == 3 ? s->N[2] : s->N[1];
+  if (p.chunk < 0 || p.chunk > extent) return "chunk must be in [0, the marching extent]";
+  if (p.chunk2 < 0 || p.chunk2 > extent) return "chunk2 must be in [0, the marching extent]";
+  if (p.two_step != 0 && p.two_step != 1) return "two_step must be 0 or 1";
+  if (s->dims == 3 && (p.two_step || p.chunk2)) return "two-step passes exist in (2+1)D only";
+  return nullptr;
+}
+
+static void apply_plan(dirac_sim* s, const dirac_plan& p) {
+  s->chunk1 = p.chunk;
+  s->chunk2 = p.chunk2;
+  if (s->dims == 2) s->tblock = p.two_step;
+  s->plan_us = p.us_per_step;
+}
+
 extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], const double dx[3],
                                      double dt, double m, const dirac_fields* fields,
                                      dirac_precision precision, unsigned flags, void* stream) {
@@ -405,6 +466,11 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
     return cleanup_fail(cuda_fail(s, e, "cudaMallocHost(sums)"));
   if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
     return cleanup_fail(cuda_fail(s, e, "cudaStreamSynchronize"));
+  if (s->fused) {
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    auto it = g_plans.find(plan_key(s));
+    if (it != g_plans.end()) apply_plan(s, it->second);
+  }
   *out = s;
   return DIRAC_OK;
 }
@@ -554,6 +620,7 @@ static dirac_status steps_fused(dirac_sim* s, long n, cudaStream_t st, bool want
                   std::getenv("DIRAC_NO_TEMPORAL_BLOCKING") == nullptr;
   while (tb && n >= 2) {
     FusedArgs<P> a = fused_args<P>(s, sim_time(s));
+    a.chunk = s->chunk2;
     if (want_e && n == 2) a.e_partials = s->e_partials;
     const int blocks = launch_fused2d_tb2(a, st);
     if (!blocks) break;
@@ -567,6 +634,7 @@ static dirac_status steps_fused(dirac_sim* s, long n, cudaStream_t st, bool want
   for (long i = 0; i < n; ++i) {
     link_table<P>(s, sim_time(s), st);
     FusedArgs<P> a = fused_args<P>(s, sim_time(s));
+    a.chunk = s->chunk1;
     if (want_e && i == n - 1) a.e_partials = s->e_partials;
     const int blocks = s->dims == 3 ? launch_fused<P, 3>(a, st) : launch_fused<P, 2>(a, st);
     if (a.e_partials) e_blocks = blocks;
@@ -679,7 +747,7 @@ static dirac_status batch_group(dirac_sim* const* g, int n, long nsteps) {
   h_first[0] = 0;
   for (int i = 0; i < n; ++i) {
     dirac_sim* s = g[i];
-    const int chunk = fused_chunk(s->dims, s->N);
+    const int chunk = s->chunk1 > 0 ? s->chunk1 : fused_chunk(s->dims, s->N);
     for (int p = 0; p < 2; ++p) {
       FusedArgs<F32> a = fused_args<F32>(s, sim_time(s));
       a.chunk = chunk;
@@ -859,5 +927,116 @@ extern "C" dirac_status dirac_set_time(dirac_sim* s, double t) {
   s->t0 = t;
   s->k = 0;
   s->e_valid_at = -1;
+  return DIRAC_OK;
+}
+
+extern "C" dirac_status dirac_get_plan(const dirac_sim* s, dirac_plan* out) {
+  if (!s || !out) return fail(const_cast<dirac_sim*>(s), DIRAC_ERR_INVALID, "NULL argument");
+  *out = plan_of(s);
+  return DIRAC_OK;
+}
+
+extern "C" dirac_status dirac_set_plan(dirac_sim* s, const dirac_plan* plan) {
+  if (!s || !plan) return fail(s, DIRAC_ERR_INVALID, "NULL argument");
+  if (const char* why = plan_problem(s, *plan)) return fail(s, DIRAC_ERR_INVALID, why);
+  if (!s->fused) return DIRAC_OK;
+  CK(s, cudaStreamSynchronize(s->stream));
+  drop_graphs(s);
+  dirac_plan p = *plan;
+  p.us_per_step = 0.0;
+  apply_plan(s, p);
+  return DIRAC_OK;
+}
+
+// Time `reps` launches of one candidate (after one untimed launch) on the
+// current state, out of place into the spare buffer; milliseconds per launch.
+static dirac_status time_candidate(dirac_sim* s, int two_step, int chunk, int reps, cudaEvent_t e0,
+                                   cudaEvent_t e1, float* ms) {
+  FusedArgs<F32> a = fused_args<F32>(s, sim_time(s));
+  a.chunk = chunk;
+  for (int r = 0; r <= reps; ++r) {
+    if (r == 1) CK(s, cudaEventRecord(e0, s->stream));
+    const int blocks = two_step ? launch_fused2d_tb2(a, s->stream)
+                                : (s->dims == 3 ? launch_fused<F32, 3>(a, s->stream)
+                                                : launch_fused<F32, 2>(a, s->stream));
+    if (!blocks) return fail(s, DIRAC_ERR_UNSUPPORTED, "no two-step kernel for these fields");
+    s->launches += 1;
+    CK(s, cudaGetLastError());
+  }
+  CK(s, cudaEventRecord(e1, s->stream));
+  CK(s, cudaEventSynchronize(e1));
+  float t = 0.0f;
+  CK(s, cudaEventElapsedTime(&t, e0, e1));
+  *ms = t / (float)reps;
+  return DIRAC_OK;
+}
+
+extern "C" dirac_status dirac_autotune(dirac_sim* s, dirac_plan* out) {
+  if (!s) return fail(s, DIRAC_ERR_INVALID, "NULL sim");
+  if (!s->fused) {
+    if (out) *out = plan_of(s);
+    return DIRAC_OK;
+  }
+  constexpr int kCandidates = 6;
+  int c1[kCandidates], c2[kCandidates];
+  const int n1 = fused_candidates(s->dims, s->N, 0, c1, kCandidates);
+  const bool tb_ok = s->dims == 2 && !time_dependent_fields(s) &&
+                     (s->coef_mode == COEF_UNIFORM || s->coef_mode == COEF_STEP ||
+                      s->coef_mode == COEF_SOFTCORE) &&
+                     (s->link_mode == LINK_NONE || s->link_mode == LINK_CONST) &&
+                     !(s->coef_mode == COEF_SOFTCORE && s->link_mode == LINK_CONST);
+  const int n2 = tb_ok ? fused_candidates(2, s->N, 1, c2, kCandidates) : 0;
+  link_table<F32>(s, sim_time(s), s->stream);  // plane-wave links of the current step, if any
+  cudaEvent_t e0, e1;
+  CK(s, cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(s, ce, "cudaEventCreate");
+  }
+  // repetitions: about a millisecond of launches per candidate and sweep
+  float t0 = 0.0f;
+  dirac_status st = time_candidate(s, 0, c1[0], 1, e0, e1, &t0);
+  int reps = 2;
+  if (st == DIRAC_OK && t0 > 0.0f) reps = (int)std::ceil(1.0f / t0);
+  reps = reps < 2 ? 2 : (reps > 50 ? 50 : reps);
+  float best1[kCandidates], best2[kCandidates];
+  for (int i = 0; i < kCandidates; ++i) best1[i] = best2[i] = 1e30f;
+  for (int sweep = 0; sweep < 2 && st == DIRAC_OK; ++sweep) {
+    for (int i = 0; i < n1 && st == DIRAC_OK; ++i) {
+      float ms = 0.0f;
+      st = time_candidate(s, 0, c1[i], reps, e0, e1, &ms);
+      if (ms < best1[i]) best1[i] = ms;
+    }
+    for (int i = 0; i < n2 && st == DIRAC_OK; ++i) {
+      float ms = 0.0f;
+      st = time_candidate(s, 1, c2[i], reps, e0, e1, &ms);
+      if (ms / 2.0f < best2[i]) best2[i] = ms / 2.0f;  // two steps per launch
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != DIRAC_OK) return st;
+  int i1 = 0, i2 = 0;
+  for (int i = 1; i < n1; ++i) if (best1[i] < best1[i1]) i1 = i;
+  for (int i = 1; i < n2; ++i) if (best2[i] < best2[i2]) i2 = i;
+  dirac_plan p;
+  std::memset(&p, 0, sizeof(p));
+  p.chunk = c1[i1];
+  p.us_per_step = 1e3 * best1[i1];
+  if (n2 > 0) {
+    p.chunk2 = c2[i2];
+    p.two_step = best2[i2] < best1[i1] ? 1 : 0;
+    if (p.two_step) p.us_per_step = 1e3 * best2[i2];
+  } else if (s->dims == 2) {
+    p.two_step = s->tblock;  // fields that never take two-step passes: keep the flag as it was
+  }
+  drop_graphs(s);
+  apply_plan(s, p);
+  {
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    g_plans[plan_key(s)] = p;
+  }
+  if (out) *out = p;
   return DIRAC_OK;
 }

@@ -63,7 +63,11 @@ struct BatchArgs {
   int workers;                   // set by the launcher
 };
 // levels per work item and number of items the fused kernels use for a grid
+// (a FusedArgs chunk of 0 makes the launchers take fused_chunk's rule)
 int fused_chunk(int dims, const int N[3]);
+// chunk lengths worth timing, best first by the planner's model, for the
+// one-step kernels or (two_step, (2+1)D) the two-step kernel; returns the count
+int fused_candidates(int dims, const int N[3], int two_step, int* out, int max);
 long long fused_items(int dims, const int N[3], int chunk);
 template <class P, int DIMS>
 void launch_fused_batch(const BatchArgs<P>& b, long long total_items, int coef_mode, int link_mode,

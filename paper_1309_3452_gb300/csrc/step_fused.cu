@@ -600,22 +600,43 @@ int sm_count() {
 // levels and `workers` persistent workers: maximise the busy fraction of the
 // rounds times the useful fraction chunk/(chunk+restart) of each item, where
 // `restart` is the cost of an item's extra first level in levels.
+// The `max` best chunk lengths by that model, best first, into out; returns
+// how many (at least one).
+int rank_chunks(long long tiles, int levels, long long workers, int min_chunk, double restart, int* out,
+                int max) {
+  int n = 0, prev = -1;
+  double eff_of[64];
+  if (max > 64) max = 64;
+  for (int c = 1; c <= levels; ++c) {
+    const int len = (levels + c - 1) / c;  // non-increasing in c
+    if (len < min_chunk && c > 1) break;
+    if (len == prev) continue;
+    prev = len;
+    const int chunks = (levels + len - 1) / len;
+    const long long items = tiles * chunks;
+    const long long rounds = (items + workers - 1) / workers;
+    // work of a round ~ len + restart levels; total time ~ rounds * (len + restart)
+    const double eff = (double)tiles * levels / ((double)rounds * workers * (len + restart));
+    // insert by efficiency (stable: on ties, fewer chunks first)
+    int pos = n;
+    while (pos > 0 && eff > eff_of[pos - 1] * 1.0001) --pos;
+    if (pos >= max) continue;
+    const int last = n < max ? n : max - 1;
+    for (int i = last; i > pos; --i) {
+      out[i] = out[i - 1];
+      eff_of[i] = eff_of[i - 1];
+    }
+    out[pos] = len;
+    eff_of[pos] = eff;
+    if (n < max) ++n;
+  }
+  if (n == 0) out[n++] = levels;
+  return n;
+}
+
 int plan_chunk(long long tiles, int levels, long long workers, int min_chunk, double restart) {
   int best = levels;
-  double best_eff = -1.0;
-  for (int c = 1; c <= levels; ++c) {
-    int len = (levels + c - 1) / c;
-    if (len < min_chunk && c > 1) break;
-    int chunks = (levels + len - 1) / len;
-    long long items = tiles * chunks;
-    long long rounds = (items + workers - 1) / workers;
-    // work of a round ~ len + restart levels; total time ~ rounds * (len + restart)
-    double eff = (double)tiles * levels / ((double)rounds * workers * (len + restart));
-    if (eff > best_eff * 1.0001) {
-      best_eff = eff;
-      best = len;
-    }
-  }
+  rank_chunks(tiles, levels, workers, min_chunk, restart, &best, 1);
   return best;
 }
 
@@ -647,7 +668,7 @@ template <int COEF, int LINK>
 int launch3d(FusedArgs<F32> a, cudaStream_t s) {
   auto k = fused3d_kernel<F32, COEF, LINK>;
   const int resident = workers3d<fused3d_kernel<F32, COEF, LINK>>();
-  a.chunk = fused_chunk(3, a.N);
+  if (a.chunk <= 0 || a.chunk > a.N[2]) a.chunk = fused_chunk(3, a.N);
   const long long items = items3d(a.N, a.chunk);
   a.workers = (int)(items < resident ? items : resident);
   k<<<(unsigned)a.workers, kThreads3d, kSmem3d, s>>>(a);
@@ -658,7 +679,7 @@ template <int COEF, int LINK>
 int launch2d(FusedArgs<F32> a, cudaStream_t s) {
   auto k = fused2d_kernel<F32, COEF, LINK>;
   const int warps = workers2d<fused2d_kernel<F32, COEF, LINK>>();
-  a.chunk = fused_chunk(2, a.N);
+  if (a.chunk <= 0 || a.chunk > a.N[1]) a.chunk = fused_chunk(2, a.N);
   const long long items = items2d(a.N, a.chunk);
   const long long w = items < warps ? items : warps;
   a.workers = (int)w;
@@ -710,7 +731,7 @@ int launch2d_tb2(FusedArgs<F32> a, cudaStream_t s) {
   auto k = fused2d_tb2_kernel<F32, COEF, LINK>;
   const int warps = workers2d<fused2d_tb2_kernel<F32, COEF, LINK>>();
   const long long strips = (a.N[0] + kCoreTb - 1) / kCoreTb;
-  a.chunk = plan_chunk(strips, a.N[1], warps, 32, 1.0);
+  if (a.chunk <= 0 || a.chunk > a.N[1]) a.chunk = plan_chunk(strips, a.N[1], warps, 32, 1.0);
   const long long items = strips * ((a.N[1] + a.chunk - 1) / a.chunk);
   const long long w = items < warps ? items : warps;
   a.workers = (int)w;
@@ -746,6 +767,22 @@ int fused_chunk(int dims, const int N[3]) {
   const int warps = workers2d<fused2d_kernel<F32, COEF_UNIFORM, LINK_NONE>>();
   const long long strips = (N[0] + kCore - 1) / kCore;
   return plan_chunk(strips, N[1], warps, 16, 1.0);
+}
+
+int fused_candidates(int dims, const int N[3], int two_step, int* out, int max) {
+  if (dims == 3) {
+    const int resident = workers3d<fused3d_kernel<F32, COEF_UNIFORM, LINK_NONE>>();
+    const long long tiles = (long long)((N[0] + CX - 1) / CX) * ((N[1] + CY - 1) / CY);
+    return rank_chunks(tiles, N[2], resident, 4, 0.5, out, max);
+  }
+  if (two_step) {
+    const int warps = workers2d<fused2d_tb2_kernel<F32, COEF_UNIFORM, LINK_NONE>>();
+    const long long strips = (N[0] + kCoreTb - 1) / kCoreTb;
+    return rank_chunks(strips, N[1], warps, 32, 1.0, out, max);
+  }
+  const int warps = workers2d<fused2d_kernel<F32, COEF_UNIFORM, LINK_NONE>>();
+  const long long strips = (N[0] + kCore - 1) / kCore;
+  return rank_chunks(strips, N[1], warps, 16, 1.0, out, max);
 }
 
 long long fused_items(int dims, const int N[3], int chunk) {

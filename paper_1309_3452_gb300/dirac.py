@@ -47,6 +47,14 @@ class Fields(C.Structure):
     ]
 
 
+class Plan(C.Structure):
+    _fields_ = [("chunk", C.c_int), ("two_step", C.c_int), ("chunk2", C.c_int), ("us_per_step", C.c_double)]
+
+    def as_dict(self):
+        return {"chunk": self.chunk, "two_step": self.two_step, "chunk2": self.chunk2,
+                "us_per_step": self.us_per_step}
+
+
 _vp = C.c_void_p
 _dp = C.POINTER(C.c_double)
 _lib.dirac_create.argtypes = [C.POINTER(_vp), C.c_int, C.POINTER(C.c_int), _dp, C.c_double,
@@ -68,12 +76,16 @@ _lib.dirac_last_error.restype = C.c_char_p
 _lib.dirac_destroy.argtypes = [_vp]
 _lib.dirac_fields_default.argtypes = [C.POINTER(Fields)]
 _lib.dirac_version.restype = C.c_int
+_lib.dirac_get_plan.argtypes = [_vp, C.POINTER(Plan)]
+_lib.dirac_set_plan.argtypes = [_vp, C.POINTER(Plan)]
+_lib.dirac_autotune.argtypes = [_vp, C.POINTER(Plan)]
 _lib.dirac_kernel_launches.argtypes = [_vp]
 _lib.dirac_kernel_launches.restype = C.c_longlong
 
 for _name in ("dirac_create", "dirac_set_spinor", "dirac_get_spinor", "dirac_set_spinor_device",
               "dirac_get_spinor_device", "dirac_step", "dirac_batch_step", "dirac_norm",
-              "dirac_partial_density", "dirac_get_time", "dirac_set_time"):
+              "dirac_partial_density", "dirac_get_time", "dirac_set_time", "dirac_get_plan",
+              "dirac_set_plan", "dirac_autotune"):
     getattr(_lib, _name).restype = C.c_int
 
 
@@ -193,6 +205,23 @@ class Sim:
     @property
     def launches(self):
         return int(_lib.dirac_kernel_launches(self._h))
+
+    @property
+    def plan(self):
+        p = Plan()
+        self._check(_lib.dirac_get_plan(self._h, C.byref(p)))
+        return p.as_dict()
+
+    def set_plan(self, chunk=0, two_step=0, chunk2=0):
+        p = Plan(int(chunk), int(two_step), int(chunk2), 0.0)
+        self._check(_lib.dirac_set_plan(self._h, C.byref(p)))
+
+    def autotune(self):
+        """Time the candidate launch plans on the current state and keep the
+        fastest (dirac_autotune); returns the plan."""
+        p = Plan()
+        self._check(_lib.dirac_autotune(self._h, C.byref(p)))
+        return p.as_dict()
 
     @property
     def time(self):
