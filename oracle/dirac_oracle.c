@@ -145,9 +145,28 @@ static void position(const oracle_problem* p, long X, long Y, long Z, double x[3
   if (p->dims == 2) x[2] = 0.0;
 }
 
-/* scalar potential V(x, t) at half-lattice point f */
-static double potential(const oracle_problem* p, const double* V_fine, long f, const double x[3],
-                        double t) {
+/* imaginary part of the scalar potential: a uniform part and absorbing
+   layers along the faces of the box (see dirac_oracle.h) */
+static double potential_imag(const oracle_problem* p, const double x[3]) {
+  double W = 0.0;
+  if (p->abs_W != 0.0) {
+    for (int a = 0; a < p->dims; ++a) {
+      if (!((p->abs_axes >> a) & 1)) continue;
+      double L = p->N[a] * p->dx[a];
+      double d = x[a] < L - x[a] ? x[a] : L - x[a];
+      if (d < p->abs_width) {
+        double u = 1.0 - d / p->abs_width;
+        W += u * u;
+      }
+    }
+  }
+  return p->V0_imag - p->abs_W * W;
+}
+
+/* scalar potential V(x, t) at half-lattice point f (complex: Sect. 3,
+   growth factors) */
+static cplx potential(const oracle_problem* p, const double* V_fine, long f, const double x[3],
+                      double t) {
   double V = p->V0;
   if (p->step_axis >= 0 && p->step_axis < p->dims && x[p->step_axis] > p->step_x0) V += p->step_V;
   if (p->sc_Z != 0.0) {
@@ -159,7 +178,7 @@ static double potential(const oracle_problem* p, const double* V_fine, long f, c
     V -= p->sc_Z / sqrt(r2 + p->sc_a * p->sc_a);
   }
   if (V_fine) V += V_fine[f] * (1.0 + p->Vmod_amp * cos(p->Vmod_omega * t));
-  return V;
+  return V + I * potential_imag(p, x);
 }
 
 static int has_vector_potential(const oracle_problem* p) {
@@ -230,7 +249,7 @@ static void half_step(const oracle_problem* p, const grid* g, cplx* psi, const d
       long f = fine_index(g, X, Y, Z);
       double x[3];
       position(p, X, Y, Z, x);
-      double th = p->dt * (beta * p->m + potential(p, V_fine, f, x, t)) / 2.0;
+      cplx th = p->dt * (beta * p->m + potential(p, V_fine, f, x, t)) / 2.0;
       cplx S = stencil(p, g, psi, X, Y, Z, t);
       psi[f] = ((1.0 - I * th) * psi[f] - S) / (1.0 + I * th);
     }

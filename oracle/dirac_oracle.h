@@ -58,6 +58,15 @@ typedef struct {
   /* cell offset of this grid inside a larger one; positions are
      x_a = (X + 2*origin_a) * dx_a / 2.  Used for light-cone windows. */
   int origin[3];
+  /* imaginary part of V (Sect. 3, growth factors: Im V < 0 damps):
+     Im V(x) = V0_imag - abs_W * sum_{a in abs_axes} w(d_a),
+     d_a = min(x_a, L_a - x_a) the distance to the box face along a
+     (L_a = N_a dx_a of this grid; windows with origin != 0 must not use
+     layers), w(d) = (1 - d/abs_width)^2 for d < abs_width, else 0;
+     abs_axes is a bit mask of axes. */
+  double V0_imag;
+  double abs_W, abs_width;
+  int abs_axes;
 } oracle_problem;
 
 /* Advance the state in place by nsteps full time steps.  `planes` is the

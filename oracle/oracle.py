@@ -54,6 +54,7 @@ class _Problem(C.Structure):
         ("Vmod_omega", C.c_double), ("q", C.c_double), ("A_const", C.c_double * 3),
         ("Apw_amp", C.c_double), ("Apw_k", C.c_double * 3), ("Apw_omega", C.c_double),
         ("Apw_phase", C.c_double), ("Apw_pol", C.c_int), ("origin", C.c_int * 3),
+        ("V0_imag", C.c_double), ("abs_W", C.c_double), ("abs_width", C.c_double), ("abs_axes", C.c_int),
     ]
 
 
@@ -93,6 +94,10 @@ def _problem(prob, origin=(0, 0, 0)):
     p.q = float(f.q)
     p.Apw_amp, p.Apw_omega, p.Apw_phase = float(f.Apw_amp), float(f.Apw_omega), float(f.Apw_phase)
     p.Apw_pol = int(f.Apw_pol)
+    p.V0_imag = float(f.V0_imag)
+    p.abs_W, p.abs_width, p.abs_axes = float(f.abs_W), float(f.abs_width), int(f.abs_axes)
+    if p.abs_W != 0.0 and any(origin):
+        raise ValueError("absorbing layers refer to the grid's own box: no window origin")
     return p, keep
 
 

@@ -46,8 +46,9 @@ class Fields:
     V(x,t) = V0 + step_V*H(x_axis - step_x0) - sc_Z/sqrt(|x-c|^2 + sc_a^2)
              + V_static(x)*(1 + Vmod_amp*cos(Vmod_omega*t)),
     vector potential A(x,t) = A_const + e_pol*Apw_amp*cos(k.x - Apw_omega*t + Apw_phase),
-    coupled with charge q (Sect. 4).  V_static is one real per site in
-    canonical layout (shape (P, Nz, Ny, Nx)) or None."""
+    coupled with charge q (Sect. 4), and an imaginary part of V for absorbing
+    boundary layers (Sect. 3, growth factors).  V_static is one real per site
+    in canonical layout (shape (P, Nz, Ny, Nx)) or None."""
 
     V0: float = 0.0
     step_axis: int = -1
@@ -66,6 +67,13 @@ class Fields:
     Apw_omega: float = 0.0
     Apw_phase: float = 0.0
     Apw_pol: int = 0
+    # imaginary part of V: V0_imag - abs_W * sum over the axes in the bit mask
+    # abs_axes of (1 - d/abs_width)^2 within abs_width of a box face (d = the
+    # distance to the nearer face); Im V < 0 absorbs
+    V0_imag: float = 0.0
+    abs_W: float = 0.0
+    abs_width: float = 0.0
+    abs_axes: int = 0
 
 
 @dataclass

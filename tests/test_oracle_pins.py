@@ -389,3 +389,121 @@ def test_partial_density_splits_naive_norm():
     xs = [W.site_positions(prob, pl)[0] for pl in range(4)]
     want = sum(float(np.sum(np.abs(psi[pl][xs[pl] > x0]) ** 2)) for pl in range(4))
     assert abs(right - want) < 1e-14
+
+
+# ---------------------------------------------------------------- complex potential, absorbing layers
+def growth_matrix_2d(kx, ky, m, V, dt, dx=1.0, dy=1.0):
+    """Amplification matrix G = -S^-1 T of the (2+1)D scheme for constant m
+    and complex V (Sect. 3, Eq. stabilityeq, hbar = c = 1).  The mass and
+    potential enter as (m +- V)/(2 i), the time average of the scheme: the
+    printed S and T drop the 1/2, while the printed det G = Q and N keep it."""
+    a = 2j / dx * math.sin(kx * dx / 2.0)
+    b = 2j / dy * math.sin(ky * dy / 2.0)
+    S = np.array([[1.0 / dt - (m + V) / 2j, 0.0], [a + 1j * b, 1.0 / dt + (m - V) / 2j]])
+    T = np.array([[-1.0 / dt - (m + V) / 2j, a - 1j * b], [0.0, -1.0 / dt + (m - V) / 2j]])
+    return -np.linalg.solve(S, T)
+
+
+def match_eigenvalues(got, want):
+    """Largest distance of a greedy one-to-one matching of two multisets."""
+    got = list(got)
+    worst = 0.0
+    for w in want:
+        i = int(np.argmin([abs(g - w) for g in got]))
+        worst = max(worst, abs(got.pop(i) - w))
+    return worst
+
+
+@pytest.mark.parametrize("V", [0.2 - 0.3j, -0.1 + 0.15j, -0.4j])
+def test_growth_factors_complex_potential_2d(V):
+    """Sect. 3 (growth factors): for a constant complex V the eigenvalues of
+    the oracle's one-step map are the eigenvalues of G(k) over the grid's k,
+    each twice (the staggered copy); det G equals the printed
+    Q = (4 + (m^2 - V^2) dt^2 - 4 i V dt) / N, N = 4 + (m^2 - V^2) dt^2 + 4 i V dt,
+    for every k; |lambda| < 1 where Im V < 0 (absorbing) and > 1 where Im V > 0."""
+    m = 0.3
+    prob = W.Problem(2, (4, 4, 1), (1.0, 1.0, 1.0), 0.9 * W.stability_limit(2), m,
+                     W.Fields(V0=V.real, V0_imag=V.imag))
+    dt = prob.dt
+    lam = np.linalg.eigvals(one_step_matrix(prob))
+    Nn = 4 + (m * m - V * V) * dt * dt + 4j * V * dt
+    Q = (4 + (m * m - V * V) * dt * dt - 4j * V * dt) / Nn
+    want = []
+    for nx, ny in np.ndindex(4, 4):
+        g = growth_matrix_2d(2 * math.pi * nx / 4, 2 * math.pi * ny / 4, m, V, dt)
+        assert abs(np.linalg.det(g) - Q) < 1e-13
+        want += list(np.linalg.eigvals(g)) * 2
+    assert len(want) == lam.size
+    assert match_eigenvalues(lam, want) < 1e-10
+    if V.imag < 0:
+        assert np.max(np.abs(lam)) < 1.0
+    else:
+        assert np.max(np.abs(lam)) > 1.0
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_uniform_state_complex_potential(dims):
+    """A spatially constant state has S = 0, so every upper value is
+    multiplied by (1 - i th_u)/(1 + i th_u) and every lower one by
+    (1 - i th_l)/(1 + i th_l) per step, th_u = dt (m + V)/2, th_l = dt (V - m)/2,
+    with V complex (Eqs. ss1-ss4)."""
+    V = 0.15 - 0.25j
+    m = 0.6
+    prob = prob2(N=(3, 4)) if dims == 2 else prob3(N=(2, 3, 2))
+    prob = W.Problem(prob.dims, prob.N, prob.dx, prob.dt, m, W.Fields(V0=V.real, V0_imag=V.imag))
+    rng = np.random.default_rng(3)
+    c = rng.standard_normal(prob.n_planes) + 1j * rng.standard_normal(prob.n_planes)
+    psi = np.broadcast_to(c[:, None, None, None], prob.shape).copy()
+    n = 7
+    out = O.step(prob, psi, n)
+    th_u, th_l = prob.dt * (m + V) / 2, prob.dt * (V - m) / 2
+    upper = 4 if dims == 3 else 2
+    for pl in range(prob.n_planes):
+        th = th_u if pl < upper else th_l
+        want = c[pl] * ((1 - 1j * th) / (1 + 1j * th)) ** n
+        assert np.max(np.abs(out[pl] - want)) < 1e-13 * abs(want) + 1e-15
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_absorbing_layer_functional_decreases(dims):
+    """Absorbing layers (Im V <= 0 near the box faces, Sect. 3): E never
+    grows from one step to the next and falls once the state reaches the
+    layers; abs_W = 0 reproduces the run without layers bit for bit."""
+    prob = prob2(N=(14, 12)) if dims == 2 else prob3(N=(8, 7, 9))
+    axes = 0b11 if dims == 2 else 0b101
+    V = W.random_potential(prob, 2, 0.5)
+    lay = prob.with_fields(V_static=V, abs_W=0.6, abs_width=2.5, abs_axes=axes)
+    psi = W.random_state(prob, 8)
+    E = [O.observables(lay, psi, 0.0)["E"]]
+    cur = psi
+    for s in range(12):
+        cur = O.step(lay, cur, 1, s * prob.dt)
+        E.append(O.observables(lay, cur, (s + 1) * prob.dt)["E"])
+    d = np.diff(E)
+    assert np.all(d <= 1e-13 * E[0])
+    assert E[-1] < 0.9 * E[0]
+    off = prob.with_fields(V_static=V, abs_W=0.0, abs_width=2.5, abs_axes=axes)
+    assert np.array_equal(O.step(off, psi, 5), O.step(prob.with_fields(V_static=V), psi, 5))
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_absorbing_layer_placement(dims):
+    """The layer acts only within abs_width of the box faces along the
+    selected axes: a state supported in the middle evolves bit for bit as
+    without layers while its light cone stays clear of them, and differs
+    once it has reached them."""
+    N = (30, 26) if dims == 2 else (22, 20, 18)
+    prob = prob2(N=N) if dims == 2 else prob3(N=N)
+    lay = prob.with_fields(abs_W=0.8, abs_width=4.0, abs_axes=(1 << dims) - 1)
+    psi = np.zeros(prob.shape, complex)
+    rng = np.random.default_rng(4)
+    mid = [n // 2 for n in prob.N[:dims]]
+    sl = [slice(None)]
+    sl += [slice(mid[2] - 1, mid[2] + 2)] if dims == 3 else [slice(0, 1)]
+    sl += [slice(mid[1] - 1, mid[1] + 2), slice(mid[0] - 1, mid[0] + 2)]
+    block = psi[tuple(sl)]
+    psi[tuple(sl)] = rng.standard_normal(block.shape) + 1j * rng.standard_normal(block.shape)
+    # the support reaches mid +- 2 cells; one step spreads it by one cell per axis
+    clear = min(prob.N[a] // 2 for a in range(dims)) - 2 - 5  # cells to the layer edge (width 4 + 1)
+    assert np.array_equal(O.step(lay, psi, clear), O.step(prob, psi, clear))
+    assert not np.array_equal(O.step(lay, psi, clear + 6), O.step(prob, psi, clear + 6))
