@@ -54,6 +54,12 @@ def workload(name):
         psi = ("device", 24.0, tuple(W.random_k0(1)), (256.0, 256.0, 256.0))
         desc = ("(3+1)D 512^3, m=1, soft core -1/sqrt(|x-c|^2+1) at the centre + A_x = 0.5 cos(2 pi z/64 - "
                 "omega t), packet sigma=24 seeded k0; 100 of the workload's 2000 time steps + E per step")
+    elif name == "3d256laser":  # the same fields on a 256^3 grid (profiling size)
+        prob, _, _ = W.workload_laser(N=256, steps=2000)
+        n = 50
+        psi = ("device", 24.0, tuple(W.random_k0(1)), (128.0, 128.0, 128.0))
+        desc = ("(3+1)D 256^3, m=1, soft core -1/sqrt(|x-c|^2+1) at the centre + A_x = 0.5 cos(2 pi z/64 - "
+                "omega t), packet sigma=24 seeded k0; 50 time steps + E per step")
     elif name == "2d4096":
         prob, psi, n = W.workload_klein(N=4096, steps=500)
         desc = ("(2+1)D 4096^2 Klein step (V0 = 2E+m at x0 = N/2+1/4), m=0.2, packet sigma=40, "
@@ -66,12 +72,24 @@ def workload(name):
     return prob, psi, n, desc
 
 
-def bytes_per_lup(dims, precision):
+def tabulated_potential(fields, precision):
+    """The FP32 kernels read a per-site coefficient table (b = 1/(1 + i theta)
+    as hi + lo complex floats, 16 B) for a time-independent potential beyond V0
+    and a Klein step."""
+    if precision != "fp32" or fields is None:
+        return False
+    if fields.V_static is not None:
+        return fields.Vmod_amp == 0.0
+    return fields.sc_Z != 0.0
+
+
+def bytes_per_lup(dims, precision, table=False):
     """Algorithmic HBM bytes per site update: every value read once and
     written once per full step (8 complex values per (3+1)D cell, 4 per
-    (2+1)D cell)."""
+    (2+1)D cell), plus one 16 B coefficient per value read when the
+    potential is tabulated."""
     vals = 8 if dims == 3 else 4
-    return 2 * vals * (8 if precision == "fp32" else 16)
+    return 2 * vals * (8 if precision == "fp32" else 16) + (16 * vals if table else 0)
 
 
 class Clocks:
@@ -279,7 +297,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="3d128", choices=["3d128", "3d512", "3d512laser", "2d4096", "2d64", "serve"])
+    ap.add_argument("--workload", default="3d128", choices=["3d128", "3d512", "3d512laser", "3d256laser", "2d4096", "2d64", "serve"])
     ap.add_argument("--requests", type=int, default=40, help="serve: requests in the stream")
     ap.add_argument("--quantum", type=int, default=100, help="serve: steps per batching quantum")
     ap.add_argument("--seed", type=int, default=0, help="serve: request stream seed")
@@ -370,7 +388,7 @@ def main():
 
     # dominant kernel: the time-step kernels; per launch = one full time step
     stencil_ms = (sum(step_ms) - sum(norm_ms)) / args.steps / n
-    bpl = bytes_per_lup(prob.dims, args.precision)
+    bpl = bytes_per_lup(prob.dims, args.precision, tabulated_potential(prob.fields, args.precision))
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))

@@ -96,6 +96,14 @@ typedef enum {
  * half-step at t + dt/2 (the time sheets of Eqs. ss1-ss4).
  * V_static: NULL, or a host array of one real per site (canonical layout);
  * it is copied during dirac_create.
+ * Imaginary part of V (Sect. 3, growth factors: Im V < 0 damps, so layers of
+ * negative Im V near the faces absorb outgoing waves):
+ *   Im V(x) = V0_imag - abs_W * sum_{a in abs_axes} w(d_a),
+ *   d_a = min(x_a, N_a dx_a - x_a), w(d) = (1 - d/abs_width)^2 for
+ *   d < abs_width, else 0; abs_axes is a bit mask of axes (bit a = axis a).
+ * abs_W != 0 needs abs_width > 0 and a non-empty mask of the grid's axes
+ * (else DIRAC_ERR_INVALID).  With any Im V the functional E is no longer
+ * conserved; with Im V <= 0 it does not grow.
  */
 typedef struct {
   double V0;
@@ -108,9 +116,13 @@ typedef struct {
   double A_const[3];
   double Apw_amp, Apw_k[3], Apw_omega, Apw_phase;
   int Apw_pol;
+  double V0_imag;
+  double abs_W, abs_width;
+  int abs_axes;
 } dirac_fields;
 
-/* Zero fields: everything 0 except q = 1, step_axis = -1, sc_a = 1. */
+/* Zero fields: everything 0 except q = 1, step_axis = -1, sc_a = 1 (no
+   imaginary part, no layers). */
 void dirac_fields_default(dirac_fields* f);
 
 /*

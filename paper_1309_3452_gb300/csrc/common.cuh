@@ -241,12 +241,14 @@ __device__ __forceinline__ float2 apply(const F32::Coef& c, float2 F, float2 S) 
 }
 
 // ------------------------------------------------------------------ fields
-// COEF_SOFTCORE: V0 + Klein step + soft core, evaluated per site in
-// double-float arithmetic (FP32 kernels).  LINK_PLANE: a plane-wave vector
-// potential whose wave vector lies along one axis other than its
-// polarisation; its link factors come from a per-half-step table indexed by
-// the half-lattice coordinate along that axis.  GENERAL: per-site FP64.
-enum CoefMode { COEF_UNIFORM = 0, COEF_STEP = 1, COEF_GENERAL = 2, COEF_SOFTCORE = 3 };
+// COEF_TABLE: a time-independent scalar potential (soft core, static array,
+// with V0 and a Klein step) whose coefficient b = 1/(1 + i theta), theta =
+// dt (beta m + V)/2, is tabulated per site at creation, in FP64 rounded to a
+// hi + lo pair of complex floats (FP32 kernels).  LINK_PLANE: a plane-wave vector potential whose wave vector lies
+// along one axis other than its polarisation; its link factors come from a
+// per-half-step table indexed by the half-lattice coordinate along that axis.
+// GENERAL: per-site FP64.
+enum CoefMode { COEF_UNIFORM = 0, COEF_STEP = 1, COEF_GENERAL = 2, COEF_TABLE = 3 };
 enum LinkMode { LINK_NONE = 0, LINK_CONST = 1, LINK_GENERAL = 2, LINK_PLANE = 3 };
 
 // Analytic field description, FP64, for the per-site (general) paths.
@@ -262,13 +264,39 @@ struct FieldDesc {
   double Vmod_amp, Vmod_omega;
   double q, A_const[3], Apw_amp, Apw_k[3], Apw_omega, Apw_phase;
   int Apw_pol;
+  // imaginary part of V: V0_imag - abs_W sum_{a in abs_axes} (1 - d_a/abs_width)^2
+  // within abs_width of a face of the box [0, L_a)
+  double V0_imag, abs_W, abs_width;
+  int abs_axes;
+  double L[3];
 };
 
-// Compute alpha and gamma in FP64 from theta.
-__device__ __forceinline__ void coef_from_theta(double th, double rx, double2& a, double2& g) {
-  double inv = 1.0 / (1.0 + th * th);
-  a = make_double2((1.0 - th * th) * inv, -2.0 * th * inv);
-  g = make_double2(rx * inv, -rx * th * inv);
+// Compute alpha = (1 - i th)/(1 + i th) and gamma = r_x/(1 + i th) in FP64
+// from th = ta + i tb (1 + i th = (1 - tb) + i ta).
+__device__ __forceinline__ void coef_from_theta(double ta, double tb, double rx, double2& a, double2& g) {
+  const double inv = 1.0 / ((1.0 - tb) * (1.0 - tb) + ta * ta);
+  a = make_double2((1.0 - tb * tb - ta * ta) * inv, -2.0 * ta * inv);
+  g = make_double2(rx * (1.0 - tb) * inv, -rx * ta * inv);
+}
+
+// imaginary part of the scalar potential at half-lattice point H (absorbing
+// layers; time-independent), FP64
+__device__ __forceinline__ double potential_imag_at(const FieldDesc& f, int dims, long long X, long long Y,
+                                                    long long Z) {
+  double W = 0.0;
+  if (f.abs_W != 0.0) {
+    const long long H[3] = {X, Y, Z};
+    for (int a = 0; a < dims; ++a) {
+      if (!((f.abs_axes >> a) & 1)) continue;
+      const double x = (double)H[a] * f.dx[a] * 0.5;
+      const double d = fmin(x, f.L[a] - x);
+      if (d < f.abs_width) {
+        const double u = 1.0 - d / f.abs_width;
+        W += u * u;
+      }
+    }
+  }
+  return f.V0_imag - f.abs_W * W;
 }
 
 // scalar potential at half-lattice point (X,Y,Z) at time t, FP64
@@ -338,32 +366,15 @@ __device__ __forceinline__ DF df_mulf(DF a, float b) {
   const float e = rfma(a.hi, b, -p);
   return df_fast_two_sum(p, rfma(a.lo, b, e));
 }
-// 1/sqrt(s) for s > 0: float estimate plus one Newton step on the residual
-// 1 - s y^2 formed in double-float
-__device__ __forceinline__ DF df_rsqrt(DF s) {
-  const float y = rsqrtf(s.hi);
-  const DF sy = df_mulf(s, y);                        // s y
-  const DF syy = df_mulf(sy, y);                      // s y^2
-  const float r = radd(rsub(1.0f, syy.hi), -syy.lo);  // 1 - s y^2 (small)
-  return df_fast_two_sum(y, rmul(rmul(0.5f, y), r));
-}
-// 1/q for q >= 1: float estimate plus one Newton step
+// 1/q for q >= 1: the hardware estimate (rcp.approx, within one ulp) plus one
+// Newton step y + y (1 - q y) on the residual formed in double-float
 __device__ __forceinline__ DF df_rcp(DF q) {
-  const float y = __frcp_rn(q.hi);
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(q.hi));
   const DF qy = df_mulf(q, y);
   const float r = radd(rsub(1.0f, qy.hi), -qy.lo);    // 1 - q y (small)
   return df_fast_two_sum(y, rmul(y, r));
 }
-
-// Per-simulation constants of the double-float soft-core path.
-struct SoftCore {
-  float h_hi[3], h_lo[3];  // dx_a / 2
-  float c_hi[3], c_lo[3];  // centre
-  float a2_hi, a2_lo;      // sc_a^2
-  float mz_hi, mz_lo;      // -sc_Z dt / 2
-  float rx_hi, rx_lo;      // r_x
-  int exact;               // positions, centre and r^2 are exact in FP32
-};
 
 // ------------------------------------------------------------------ site update
 // FP64 -> coefficient / link of the working precision
@@ -410,65 +421,42 @@ struct HalfFields {
   typename P::Link L[3];    // constant link factors exp(-i q A_a dx_a/2)
   double t;                 // field time of this half-step
   double beta;              // +1 upper (A,B,u), -1 lower (C,D,v)
-  // COEF_SOFTCORE: dt/2 (beta m + V0 [+ V_step]) before / beyond the step
-  float th0_hi[2], th0_lo[2];
-  SoftCore sc;
+  // COEF_TABLE: b of every site as {re hi, im hi, re lo, im lo}, one array
+  // per plane (cell index as in the state), and r_x as hi + lo
+  const float4* b_tab[8];
+  float rx_hi, rx_lo;
   // LINK_PLANE: table of exp(-i phi) for this half-step, indexed by the
   // half-lattice coordinate along ltab_axis; applies on axis lpol only
   const typename P::Link* ltab;
   int ltab_axis, lpol;
 };
 
-// The soft-core update in double-float (F32 only):
-//   theta = dt/2 (beta m + V0 [+ V_step]) - Z dt/2 / sqrt(|x - c|^2 + a^2)
-//   F+ = kappa (1 - i theta) [(1 - i theta) F - r_x S'],  kappa = 1/(1 + theta^2)
-// which is ((1 - i theta) F - S) / (1 + i theta) with every coefficient carried
-// to ~1e-13, so its rounding does not accumulate over steps.
+// The tabulated-potential update (F32 only), the paper's form of the Cayley
+// step (Eqs. ss1-ss4):  F+ = b (2F - S) - F,  b = 1/(1 + i theta),  S = r_x S'
+// which is ((1 - i theta) F - S)/(1 + i theta).  b and r_x are carried as
+// hi + lo pairs, so |2b - 1| = 1 holds to ~1e-14 and the rounding of the
+// coefficients does not accumulate over steps.
 template <class P>
-__device__ __forceinline__ typename P::cplx apply_softcore(const HalfFields<P>& h, typename P::cplx F,
-                                                           typename P::cplx S, const int (&H)[3]);
+__device__ __forceinline__ typename P::cplx apply_table(const HalfFields<P>& h, typename P::cplx F,
+                                                        typename P::cplx S, int plane, long long site);
 template <>
-__device__ __forceinline__ double2 apply_softcore<F64>(const HalfFields<F64>&, double2 F, double2,
-                                                       const int (&)[3]) {
+__device__ __forceinline__ double2 apply_table<F64>(const HalfFields<F64>&, double2 F, double2, int,
+                                                    long long) {
   return F;  // not used: FP64 kernels take the general path
 }
 template <>
-__device__ __forceinline__ float2 apply_softcore<F32>(const HalfFields<F32>& h, float2 F, float2 S,
-                                                      const int (&H)[3]) {
-  const SoftCore& c = h.sc;
-  DF r2;
-  if (c.exact) {
-    float acc = 0.0f;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float d = rsub(rmul((float)H[a], c.h_hi[a]), c.c_hi[a]);
-      acc = rfma(d, d, acc);
-    }
-    r2 = DF{acc, 0.0f};
-  } else {
-    r2 = DF{0.0f, 0.0f};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const DF x = df_mulf(DF{c.h_hi[a], c.h_lo[a]}, (float)H[a]);
-      const DF d = df_add(x, DF{-c.c_hi[a], -c.c_lo[a]});
-      r2 = df_add(r2, df_mul(d, d));
-    }
-  }
-  const DF y = df_rsqrt(df_add(r2, DF{c.a2_hi, c.a2_lo}));
-  const int hs = h.step_axis == 0 ? H[0] : (h.step_axis == 1 ? H[1] : H[2]);
-  const int side = (h.coef_mode == COEF_SOFTCORE && h.step_X != INT_MIN && hs >= h.step_X) ? 1 : 0;
-  const DF th = df_add(DF{h.th0_hi[side], h.th0_lo[side]}, df_mul(DF{c.mz_hi, c.mz_lo}, y));
-  const DF q = df_add(DF{1.0f, 0.0f}, df_mul(th, th));
-  const DF k = df_rcp(q);
-  // w = (1 - i th) F - r_x S'
-  float wr = rfma(th.hi, F.y, rfma(th.lo, F.y, F.x));
-  float wi = rfma(-th.hi, F.x, rfma(-th.lo, F.x, F.y));
-  wr = rfma(-c.rx_hi, S.x, rfma(-c.rx_lo, S.x, wr));
-  wi = rfma(-c.rx_hi, S.y, rfma(-c.rx_lo, S.y, wi));
-  // v = (1 - i th) w ; F+ = kappa v
-  const float vr = rfma(th.hi, wi, rfma(th.lo, wi, wr));
-  const float vi = rfma(-th.hi, wr, rfma(-th.lo, wr, wi));
-  return make_float2(rfma(k.hi, vr, rmul(k.lo, vr)), rfma(k.hi, vi, rmul(k.lo, vi)));
+__device__ __forceinline__ float2 apply_table<F32>(const HalfFields<F32>& h, float2 F, float2 S, int plane,
+                                                   long long site) {
+  const float4 b = __ldg(h.b_tab[plane] + site);
+  // w = 2F - r_x S'  (small product first)
+  const float2 w = pfma(make_float2(-h.rx_hi, -h.rx_hi), S,
+                        pfma(make_float2(-h.rx_lo, -h.rx_lo), S, padd(F, F)));
+  // b w, small (lo) products first
+  float re = rfma(b.z, w.x, -rmul(b.w, w.y));
+  float im = rfma(b.z, w.y, rmul(b.w, w.x));
+  re = rfma(b.x, w.x, rfma(-b.y, w.y, re));
+  im = rfma(b.x, w.y, rfma(b.y, w.x, im));
+  return psub(make_float2(re, im), F);
 }
 
 // Field-path selectors for site_update: a fixed CoefMode / LinkMode compiles
@@ -520,11 +508,12 @@ __device__ __forceinline__ typename P::cplx site_update(
     const int hs = h.step_axis == 0 ? H[0] : (h.step_axis == 1 ? H[1] : H[2]);
     return hs >= h.step_X ? apply(h.c_out, F, S) : apply(h.c_in, F, S);
   }
-  if (COEF == COEF_SOFTCORE) return apply_softcore(h, F, S, H);
+  if (coef == COEF_TABLE) return apply_table(h, F, S, plane, site);
   double V = potential_at(f, DIMS, H[0], H[1], H[2], site, pstride, plane, h.t);
   double th = f.dt * (h.beta * f.m + V) * 0.5;
+  double th_im = f.dt * potential_imag_at(f, DIMS, H[0], H[1], H[2]) * 0.5;
   double2 al, ga;
-  coef_from_theta(th, f.rx, al, ga);
+  coef_from_theta(th, th_im, f.rx, al, ga);
   return apply(coef_from(al, ga, (P*)nullptr), F, S);
 }
 

@@ -35,6 +35,7 @@ struct dirac_sim {
   double plan_us = 0;         // time per step the autotuner measured for the plan
   double2* staging = nullptr; // one canonical plane (FP32 conversions)
   double* Vstatic = nullptr;  // one real per site (plane-major, pstride)
+  float4* b_tab = nullptr;    // COEF_TABLE: b = 1/(1 + i theta) per site as hi + lo (plane-major, pstride)
   double* partials = nullptr;
   double* sums_dev = nullptr;
   double* sums_host = nullptr; // pinned
@@ -118,20 +119,23 @@ static int threshold_index(double x0, double dx) {
   return (int)H;
 }
 
-template <class P> static typename P::Coef make_coef(double th, double rx);
-template <> F64::Coef make_coef<F64>(double th, double rx) {
-  double inv = 1.0 / (1.0 + th * th);
+template <class P> static typename P::Coef make_coef(double th_re, double th_im, double rx);
+// alpha = (1 - i th)/(1 + i th), gamma = r_x/(1 + i th) for th = a + i b:
+// 1 + i th = (1 - b) + i a, so with D = (1 - b)^2 + a^2
+//   alpha = ((1 - b^2 - a^2) - 2 i a)/D,  gamma = r_x ((1 - b) - i a)/D
+template <> F64::Coef make_coef<F64>(double a, double b, double rx) {
+  const double inv = 1.0 / ((1.0 - b) * (1.0 - b) + a * a);
   F64::Coef c;
-  c.a = make_double2((1.0 - th * th) * inv, -2.0 * th * inv);
-  c.g = make_double2(rx * inv, -rx * th * inv);
+  c.a = make_double2((1.0 - b * b - a * a) * inv, -2.0 * a * inv);
+  c.g = make_double2(rx * (1.0 - b) * inv, -rx * a * inv);
   return c;
 }
 static void split(double v, float& hi, float& lo) {
   hi = (float)v;
   lo = (float)(v - (double)hi);
 }
-template <> F32::Coef make_coef<F32>(double th, double rx) {
-  F64::Coef d = make_coef<F64>(th, rx);
+template <> F32::Coef make_coef<F32>(double a, double b, double rx) {
+  F64::Coef d = make_coef<F64>(a, b, rx);
   F32::Coef c;
   split(d.a.x, c.a_hi.x, c.a_lo.x);
   split(d.a.y, c.a_hi.y, c.a_lo.y);
@@ -183,6 +187,11 @@ static FieldDesc field_desc(const dirac_sim* s) {
   d.Apw_omega = s->f.Apw_omega;
   d.Apw_phase = s->f.Apw_phase;
   d.Apw_pol = s->f.Apw_pol;
+  d.V0_imag = s->f.V0_imag;
+  d.abs_W = s->f.abs_W;
+  d.abs_width = s->f.abs_width;
+  d.abs_axes = s->f.abs_axes;
+  for (int a = 0; a < 3; ++a) d.L[a] = s->N[a] * s->dx[a];
   return d;
 }
 
@@ -192,24 +201,6 @@ static void plane_ptrs(dirac_sim* s, typename P::cplx* (&pl)[8]) {
   for (int k = 0; k < 8; ++k) pl[k] = k < s->np ? base + (long long)k * s->pstride : nullptr;
 }
 
-// Positions, centre and |x - c|^2 of the soft core are exact in FP32: equal
-// lattice constants whose half is a power of two, a centre on the half
-// lattice, and |x - c|^2 / (dx/2)^2 < 2^24 everywhere.
-static int softcore_exact(const dirac_sim* s) {
-  if (!s->iso) return 0;
-  const double h = s->dx[0] / 2.0;
-  int e = 0;
-  if (std::frexp(h, &e) != 0.5) return 0;
-  double sum = 0.0;
-  for (int a = 0; a < s->dims; ++a) {
-    const double n = s->f.sc_center[a] / h;
-    if (n != std::floor(n) || std::fabs(n) > 1e6) return 0;
-    const double far = std::fmax(std::fabs(n), std::fabs(2.0 * s->N[a] - n));
-    sum += far * far;
-  }
-  return sum < 16777216.0 ? 1 : 0;
-}
-
 template <class P>
 static HalfFields<P> half_fields(const dirac_sim* s, bool upper, double t) {
   HalfFields<P> h;
@@ -217,30 +208,18 @@ static HalfFields<P> half_fields(const dirac_sim* s, bool upper, double t) {
   double rx = s->dt / s->dx[0];
   double beta = upper ? 1.0 : -1.0;
   h.coef_mode = s->coef_mode;
-  h.c_in = make_coef<P>(s->dt * (beta * s->m + s->f.V0) / 2.0, rx);
-  h.c_out = make_coef<P>(s->dt * (beta * s->m + (s->f.V0 + s->f.step_V)) / 2.0, rx);
+  const double th_im = s->dt * s->f.V0_imag / 2.0;
+  h.c_in = make_coef<P>(s->dt * (beta * s->m + s->f.V0) / 2.0, th_im, rx);
+  h.c_out = make_coef<P>(s->dt * (beta * s->m + (s->f.V0 + s->f.step_V)) / 2.0, th_im, rx);
   h.step_axis = s->f.step_axis < 0 ? 0 : s->f.step_axis;
   h.step_X = s->step_X;
   h.link_mode = s->link_mode;
   for (int k = 0; k < 3; ++k) h.L[k] = make_link<P>(s->f.q * s->f.A_const[k] * s->dx[k] / 2.0);
   h.t = t;
   h.beta = beta;
-  // soft core (double-float path)
-  const double th_in = s->dt * (beta * s->m + s->f.V0) / 2.0;
-  const double th_out = s->f.step_axis >= 0 ? s->dt * (beta * s->m + (s->f.V0 + s->f.step_V)) / 2.0 : th_in;
-  split(th_in, h.th0_hi[0], h.th0_lo[0]);
-  split(th_out, h.th0_hi[1], h.th0_lo[1]);
-  SoftCore& c = h.sc;
-  for (int a = 0; a < 3; ++a) {
-    const double hh = a < s->dims ? s->dx[a] / 2.0 : 0.0;
-    const double cc = a < s->dims ? s->f.sc_center[a] : 0.0;
-    split(hh, c.h_hi[a], c.h_lo[a]);
-    split(cc, c.c_hi[a], c.c_lo[a]);
-  }
-  split(s->f.sc_a * s->f.sc_a, c.a2_hi, c.a2_lo);
-  split(-s->f.sc_Z * s->dt / 2.0, c.mz_hi, c.mz_lo);
-  split(s->dt / s->dx[0], c.rx_hi, c.rx_lo);
-  c.exact = softcore_exact(s);
+  // tabulated potential
+  for (int k = 0; k < 8; ++k) h.b_tab[k] = s->b_tab && k < s->np ? s->b_tab + (long long)k * s->pstride : nullptr;
+  split(rx, h.rx_hi, h.rx_lo);
   if (s->link_mode == LINK_PLANE) {
     h.ltab = static_cast<typename P::Link*>(s->ltab) + (upper ? 0 : s->ltab_n);
     h.ltab_axis = s->ltab_axis;
@@ -376,6 +355,12 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
   dirac_fields f;
   if (fields) f = *fields; else dirac_fields_default(&f);
   if (f.step_axis >= dims) return fail(nullptr, DIRAC_ERR_INVALID, "step_axis >= dims");
+  if (!std::isfinite(f.V0_imag) || !std::isfinite(f.abs_W))
+    return fail(nullptr, DIRAC_ERR_INVALID, "V0_imag and abs_W must be finite");
+  if (f.abs_W != 0.0 && (!(f.abs_width > 0.0) || !std::isfinite(f.abs_width) || f.abs_axes <= 0 ||
+                         f.abs_axes >= (1 << dims)))
+    return fail(nullptr, DIRAC_ERR_INVALID,
+                "absorbing layers need abs_width > 0 and abs_axes a non-empty mask of the dims axes");
   if (f.Apw_amp != 0.0 && (f.Apw_pol < 0 || f.Apw_pol >= dims))
     return fail(nullptr, DIRAC_ERR_INVALID, "Apw_pol must be a spatial axis");
 
@@ -398,8 +383,13 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
   s->np = dims == 3 ? 8 : 4;
   s->elem = precision == DIRAC_FP32 ? sizeof(float2) : sizeof(double2);
   s->iso = (dx[0] == dx[1]) && (dims == 2 || dx[0] == dx[2]);
-  if (fields && fields->V_static) s->coef_mode = COEF_GENERAL;
-  else if (f.sc_Z != 0.0) s->coef_mode = COEF_SOFTCORE;
+  // a time-independent potential beyond V0 and the step: tabulated for the FP32
+  // kernels, evaluated per site in FP64 otherwise
+  const bool vstatic = fields && fields->V_static;
+  const bool layers = f.abs_W != 0.0;
+  if ((vstatic && f.Vmod_amp == 0.0) || (!vstatic && (f.sc_Z != 0.0 || layers)))
+    s->coef_mode = precision == DIRAC_FP32 ? COEF_TABLE : COEF_GENERAL;
+  else if (vstatic || f.sc_Z != 0.0) s->coef_mode = COEF_GENERAL;
   else s->coef_mode = f.step_axis >= 0 ? COEF_STEP : COEF_UNIFORM;
   if (f.step_axis >= 0) s->step_X = threshold_index(f.step_x0, s->dx[f.step_axis]);
   bool any_A = f.A_const[0] != 0.0 || f.A_const[1] != 0.0 || f.A_const[2] != 0.0;
@@ -448,6 +438,13 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
       if (e != cudaSuccess) return cleanup_fail(cuda_fail(s, e, "cudaMemcpyAsync(V)"));
     }
   }
+  if (s->coef_mode == COEF_TABLE) {
+    if ((e = cudaMalloc(&s->b_tab, (size_t)s->np * s->pstride * sizeof(float4))) != cudaSuccess)
+      return cleanup_fail(cuda_fail(s, e, "cudaMalloc(coefficient table)"));
+    launch_coef_table(s->b_tab, field_desc(s), dims, s->N, s->pstride, s->stream);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cleanup_fail(cuda_fail(s, e, "coefficient table"));
+    s->launches += 1;
+  }
   if (s->link_mode == LINK_PLANE) {
     size_t tb = (size_t)2 * s->ltab_n * (precision == DIRAC_FP32 ? sizeof(F32::Link) : sizeof(F64::Link));
     if ((e = cudaMalloc(&s->ltab, tb)) != cudaSuccess) return cleanup_fail(cuda_fail(s, e, "cudaMalloc(link table)"));
@@ -466,6 +463,10 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
     return cleanup_fail(cuda_fail(s, e, "cudaMallocHost(sums)"));
   if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
     return cleanup_fail(cuda_fail(s, e, "cudaStreamSynchronize"));
+  if (s->coef_mode == COEF_TABLE && s->Vstatic) {  // folded into the table
+    cudaFree(s->Vstatic);
+    s->Vstatic = nullptr;
+  }
   if (s->fused) {
     std::lock_guard<std::mutex> lock(g_plan_mu);
     auto it = g_plans.find(plan_key(s));
@@ -484,6 +485,7 @@ extern "C" void dirac_destroy(dirac_sim* s) {
   cudaFree(s->state_alt);
   cudaFree(s->staging);
   cudaFree(s->Vstatic);
+  cudaFree(s->b_tab);
   cudaFree(s->ltab);
   cudaFree(s->e_partials);
   cudaFree(s->e_sums);
@@ -982,9 +984,9 @@ extern "C" dirac_status dirac_autotune(dirac_sim* s, dirac_plan* out) {
   const int n1 = fused_candidates(s->dims, s->N, 0, c1, kCandidates);
   const bool tb_ok = s->dims == 2 && !time_dependent_fields(s) &&
                      (s->coef_mode == COEF_UNIFORM || s->coef_mode == COEF_STEP ||
-                      s->coef_mode == COEF_SOFTCORE) &&
+                      s->coef_mode == COEF_TABLE) &&
                      (s->link_mode == LINK_NONE || s->link_mode == LINK_CONST) &&
-                     !(s->coef_mode == COEF_SOFTCORE && s->link_mode == LINK_CONST);
+                     !(s->coef_mode == COEF_TABLE && s->link_mode == LINK_CONST);
   const int n2 = tb_ok ? fused_candidates(2, s->N, 1, c2, kCandidates) : 0;
   link_table<F32>(s, sim_time(s), s->stream);  // plane-wave links of the current step, if any
   cudaEvent_t e0, e1;

@@ -105,6 +105,12 @@ template <class P>
 void launch_link_table(typename P::Link* tab, int n, const FieldDesc& f, int dims, int axis, int pol,
                        double t_up, double t_lo, cudaStream_t s);
 
+// coefficient table of a time-independent potential (COEF_TABLE): every
+// plane of the state layout (pstride), b = 1/(1 + i dt (beta m + V)/2) as
+// {re hi, im hi, re lo, im lo}
+void launch_coef_table(float4* tab, const FieldDesc& f, int dims, const int N[3], long long pstride,
+                       cudaStream_t s);
+
 // canonical complex128 plane <-> device plane of the simulation precision
 void launch_convert_in(const double2* src, float2* dst, long long n, cudaStream_t s);
 void launch_convert_out(const float2* src, double2* dst, long long n, cudaStream_t s);

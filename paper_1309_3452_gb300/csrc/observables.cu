@@ -146,6 +146,33 @@ __global__ void link_table_kernel(typename P::Link* tab, int n, const FieldDesc 
   tab[i] = link_from(link_phase(f, dims, HH, pol, +1, half ? t_lo : t_up), (P*)nullptr);
 }
 
+// b = 1/(1 + i theta), theta = dt (beta m + V)/2 with V complex, of every site
+// of one plane (blockIdx.y), V from the same FP64 potential functions as the
+// per-site general path, at time 0 (the table serves time-independent
+// potentials only); stored as {re hi, im hi, re lo, im lo}
+template <int DIMS>
+__global__ void coef_table_kernel(float4* __restrict__ tab, const FieldDesc f, int N0, int N1, int N2,
+                                  long long pstride) {
+  const int plane = blockIdx.y;
+  const long long ncell = (long long)N0 * N1 * N2;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    const long long x = c % N0, y = (c / N0) % N1, z = c / ((long long)N0 * N1);
+    const long long X = 2 * x + plane_off<DIMS>(plane, 0), Y = 2 * y + plane_off<DIMS>(plane, 1),
+                    Z = DIMS == 3 ? 2 * z + plane_off<DIMS>(plane, 2) : 0;
+    const double V = potential_at(f, DIMS, X, Y, Z, c, pstride, plane, 0.0);
+    const double beta = is_upper<DIMS>(plane) ? 1.0 : -1.0;
+    const double ta = f.dt * (beta * f.m + V) * 0.5;  // theta = ta + i tb
+    const double tb = f.dt * potential_imag_at(f, DIMS, X, Y, Z) * 0.5;
+    // b = 1/((1 - tb) + i ta)
+    const double k = 1.0 / ((1.0 - tb) * (1.0 - tb) + ta * ta);
+    const double re = (1.0 - tb) * k, im = -ta * k;
+    const float rh = __double2float_rn(re), ih = __double2float_rn(im);
+    tab[plane * pstride + c] =
+        make_float4(rh, ih, __double2float_rn(re - (double)rh), __double2float_rn(im - (double)ih));
+  }
+}
+
 __global__ void finish_sums_kernel(const double* partials, int nblocks, double* out) {
   // warp k sums column k: lane-strided, then a fixed shuffle tree
   const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;
@@ -201,6 +228,18 @@ template void launch_link_table<F64>(F64::Link*, int, const FieldDesc&, int, int
                                      cudaStream_t);
 template void launch_link_table<F32>(F32::Link*, int, const FieldDesc&, int, int, int, double, double,
                                      cudaStream_t);
+
+void launch_coef_table(float4* tab, const FieldDesc& f, int dims, const int N[3], long long pstride,
+                       cudaStream_t s) {
+  const long long ncell = (long long)N[0] * N[1] * (dims == 3 ? N[2] : 1);
+  long long bx = (ncell + 255) / 256;
+  if (bx > 152 * 16) bx = 152 * 16;
+  const dim3 grid((unsigned)bx, dims == 3 ? 8 : 4);
+  if (dims == 3)
+    coef_table_kernel<3><<<grid, 256, 0, s>>>(tab, f, N[0], N[1], N[2], pstride);
+  else
+    coef_table_kernel<2><<<grid, 256, 0, s>>>(tab, f, N[0], N[1], 1, pstride);
+}
 
 void launch_finish_sums2(const double* partials, int nblocks, double* out, cudaStream_t s) {
   finish_sums2_kernel<<<1, 64, 0, s>>>(partials, nblocks, out);

@@ -715,9 +715,9 @@ template <int DIMS>
 int dispatch(const FusedArgs<F32>& a, cudaStream_t s) {
   const int c = a.hu.coef_mode, l = a.hu.link_mode;
   if (c == COEF_GENERAL || l == LINK_GENERAL) return launch_dims<DIMS, kAnyMode, kAnyMode>(a, s);
-  if (c == COEF_SOFTCORE && l == LINK_NONE) return launch_dims<DIMS, COEF_SOFTCORE, LINK_NONE>(a, s);
-  if (c == COEF_SOFTCORE && l == LINK_PLANE) return launch_dims<DIMS, COEF_SOFTCORE, LINK_PLANE>(a, s);
-  if (c == COEF_SOFTCORE) return launch_dims<DIMS, kAnyMode, kAnyMode>(a, s);
+  if (c == COEF_TABLE && l == LINK_NONE) return launch_dims<DIMS, COEF_TABLE, LINK_NONE>(a, s);
+  if (c == COEF_TABLE && l == LINK_PLANE) return launch_dims<DIMS, COEF_TABLE, LINK_PLANE>(a, s);
+  if (c == COEF_TABLE) return launch_dims<DIMS, kAnyMode, kAnyMode>(a, s);
   if (c == COEF_UNIFORM && l == LINK_PLANE) return launch_dims<DIMS, COEF_UNIFORM, LINK_PLANE>(a, s);
   if (c == COEF_STEP && l == LINK_PLANE) return launch_dims<DIMS, COEF_STEP, LINK_PLANE>(a, s);
   if (c == COEF_UNIFORM && l == LINK_NONE) return launch_dims<DIMS, COEF_UNIFORM, LINK_NONE>(a, s);
@@ -754,7 +754,7 @@ int launch_fused2d_tb2(const FusedArgs<F32>& a, cudaStream_t s) {
   if (c == COEF_STEP && l == LINK_NONE) return launch2d_tb2<COEF_STEP, LINK_NONE>(a, s);
   if (c == COEF_UNIFORM && l == LINK_CONST) return launch2d_tb2<COEF_UNIFORM, LINK_CONST>(a, s);
   if (c == COEF_STEP && l == LINK_CONST) return launch2d_tb2<COEF_STEP, LINK_CONST>(a, s);
-  if (c == COEF_SOFTCORE && l == LINK_NONE) return launch2d_tb2<COEF_SOFTCORE, LINK_NONE>(a, s);
+  if (c == COEF_TABLE && l == LINK_NONE) return launch2d_tb2<COEF_TABLE, LINK_NONE>(a, s);
   return 0;
 }
 

@@ -43,7 +43,8 @@ class Fields(C.Structure):
         ("V_static", C.POINTER(C.c_double)), ("Vmod_amp", C.c_double), ("Vmod_omega", C.c_double),
         ("q", C.c_double), ("A_const", C.c_double * 3), ("Apw_amp", C.c_double),
         ("Apw_k", C.c_double * 3), ("Apw_omega", C.c_double), ("Apw_phase", C.c_double),
-        ("Apw_pol", C.c_int),
+        ("Apw_pol", C.c_int), ("V0_imag", C.c_double), ("abs_W", C.c_double), ("abs_width", C.c_double),
+        ("abs_axes", C.c_int),
     ]
 
 
@@ -113,6 +114,8 @@ def _fields_struct(f):
     s.q = float(f.q)
     s.Apw_amp, s.Apw_omega, s.Apw_phase = float(f.Apw_amp), float(f.Apw_omega), float(f.Apw_phase)
     s.Apw_pol = int(f.Apw_pol)
+    s.V0_imag = float(f.V0_imag)
+    s.abs_W, s.abs_width, s.abs_axes = float(f.abs_W), float(f.abs_width), int(f.abs_axes)
     return s, keep
 
 

@@ -57,6 +57,13 @@ def test_host_only_validation(lib):
     bad = (C.c_int * 3)(1, 8, 8)
     assert L.dirac_create(C.byref(h), 3, bad, dx, 0.5, 0.0, None, 0, 0, None) == D.ERR_INVALID
     assert L.dirac_create(C.byref(h), 2, N, dx, -0.1, 0.0, None, 0, 0, None) == D.ERR_INVALID
+    # absorbing layers: a width and a non-empty mask of the grid's axes
+    for width, axes, dims in ((0.0, 1, 3), (2.0, 0, 3), (2.0, 8, 3), (2.0, 4, 2)):
+        g = D.Fields()
+        L.dirac_fields_default(C.byref(g))
+        g.abs_W, g.abs_width, g.abs_axes = 0.5, width, axes
+        assert L.dirac_create(C.byref(h), dims, N, dx, 0.5, 0.0, C.byref(g), 0, 0, None) == D.ERR_INVALID
+    assert b"abs_axes" in L.dirac_last_error(None)
     assert not h.value
     # device bytes: 8 planes x 8^3 cells x complex128
     assert D.state_bytes(3, (8, 8, 8), D.FP64) == 8 * 512 * 16

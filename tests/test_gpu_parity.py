@@ -63,9 +63,11 @@ def field_cases(dims, N):
                            else (0, 2 * math.pi / L[1], 0), Apw_omega=0.3, Apw_pol=0),
         "A_wave_long": W.Fields(q=1.0, Apw_amp=0.4, Apw_k=(2 * math.pi / L[0], 0, 0),
                                 Apw_omega=0.0, Apw_pol=0, Apw_phase=0.3),
-        # soft core off the half lattice: the double-float |x - c|^2 branch
+        # soft core off the half lattice, with a Klein step
         "softcore_offgrid": W.Fields(sc_Z=0.8, sc_a=1.3, sc_center=(c[0] - 0.37, c[1] + 0.61, 2.13),
                                      V0=-0.1, step_axis=1, step_x0=N[1] / 2 + 0.25, step_V=0.3),
+        # absorbing layers on every face plus a uniform imaginary part (Sect. 3)
+        "absorb": W.Fields(V0=0.05, V0_imag=-0.02, abs_W=0.7, abs_width=3.0, abs_axes=(1 << dims) - 1),
         # the laser workload's fields: soft core plus a moving plane wave
         "laser": W.Fields(sc_Z=1.0, sc_a=1.0, sc_center=tuple(c), q=1.0, Apw_amp=0.5,
                           Apw_k=(0, 0, 2 * math.pi / L[dims - 1]) if dims == 3 else (0, 2 * math.pi / L[1], 0),
@@ -76,13 +78,16 @@ def field_cases(dims, N):
 
 @pytest.mark.parametrize("dims,N", [(2, (37, 29)), (3, (13, 11, 9))])
 @pytest.mark.parametrize("case", ["free", "V0", "klein", "klein_y", "softcore", "A_const", "A_wave",
-                                  "A_wave_long", "Vstatic_mod", "softcore_offgrid", "laser"])
+                                  "A_wave_long", "Vstatic", "Vstatic_mod", "softcore_offgrid", "laser",
+                                  "absorb"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_parity_fields(D, dims, N, case, precision):
     full = tuple(N) + ((1,) if dims == 2 else ())
     prob = W.Problem(dims, full, (1.0, 1.0, 1.0), 0.9 * W.stability_limit(dims), 0.45)
     if case == "Vstatic_mod":
         f = W.Fields(V_static=W.random_potential(prob, 4, 0.6), Vmod_amp=0.5, Vmod_omega=0.7)
+    elif case == "Vstatic":  # time-independent: tabulated theta in FP32
+        f = W.Fields(V_static=W.random_potential(prob, 4, 0.6), sc_Z=0.5, sc_a=1.5, sc_center=(3.0, 4.5, 2.0))
     else:
         f = field_cases(dims, N)[case]
     prob = W.Problem(prob.dims, prob.N, prob.dx, prob.dt, prob.m, f)
@@ -103,7 +108,7 @@ def test_parity_fields(D, dims, N, case, precision):
         assert abs(naive - ob1["naive"]) < 1e-12 * ob1["naive"]
     else:
         assert abs(E1 - ob1["E"]) < 1e-5 * abs(ob1["E"])
-        if case not in ("A_wave", "laser"):  # time-dependent A: E is not conserved
+        if case not in ("A_wave", "laser", "absorb"):  # time-dependent A, absorption: E not conserved
             assert abs(E1 - E0) < FP32_EDRIFT * abs(E0)
 
 
@@ -217,7 +222,7 @@ def test_unstable_is_rejected_and_diverges_when_forced(D):
 @pytest.mark.parametrize("dims,N", [(2, (37, 29)), (2, (64, 70)), (3, (13, 11, 9)), (3, (33, 17, 20)),
                                     (3, (2, 3, 2))])
 @pytest.mark.parametrize("case", ["free", "klein", "klein_y", "softcore", "A_const", "A_wave",
-                                  "Vstatic_mod", "softcore_offgrid", "laser"])
+                                  "Vstatic", "Vstatic_mod", "softcore_offgrid", "laser", "absorb"])
 def test_fused_kernel_bit_identical_to_reference_kernels(D, dims, N, case):
     """The fused time-step kernel (out of place, tiles with recomputed halos,
     z/y marching) uses the same per-value arithmetic as the one-kernel-per-
@@ -227,6 +232,8 @@ def test_fused_kernel_bit_identical_to_reference_kernels(D, dims, N, case):
     prob = W.Problem(dims, full, (1.0, 1.0, 1.0), 0.9 * W.stability_limit(dims), 0.45)
     if case == "Vstatic_mod":
         f = W.Fields(V_static=W.random_potential(prob, 4, 0.6), Vmod_amp=0.5, Vmod_omega=0.7)
+    elif case == "Vstatic":
+        f = W.Fields(V_static=W.random_potential(prob, 4, 0.6))
     else:
         f = field_cases(dims, N)[case]
     prob = W.Problem(prob.dims, prob.N, prob.dx, prob.dt, prob.m, f)
@@ -268,7 +275,8 @@ def test_graph_replay_bit_identical_to_plain_launches(D, dims, precision, monkey
 
 
 @pytest.mark.parametrize("N", [(70, 50), (29, 31), (5, 9), (129, 64)])
-@pytest.mark.parametrize("case", ["free", "klein", "klein_y", "A_const", "softcore", "softcore_offgrid"])
+@pytest.mark.parametrize("case", ["free", "klein", "klein_y", "A_const", "softcore", "softcore_offgrid",
+                                  "absorb"])
 def test_temporal_blocking_2d_bit_identical(D, N, case, monkeypatch):
     """(2+1)D: two time steps per pass (step 2 runs one row behind step 1 in
     registers) equal two single-step passes bit for bit; odd step counts
@@ -309,3 +317,31 @@ def test_fused_functional_matches_reduction(D, dims, N, case, nsteps, monkeypatc
         monkeypatch.delenv("DIRAC_NO_FUSED_NORM")
     assert abs(E_fused - E_red) <= 2e-7 * abs(E_red)
     assert abs(n_fused - n_red) <= 2e-7 * n_red
+
+
+@pytest.mark.parametrize("dims,N", [(2, (36, 30)), (3, (24, 20, 22))])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_absorbing_layers_functional_never_grows(D, dims, N, precision):
+    """Absorbing layers (Im V < 0 near the faces, Sect. 3): E computed after
+    every step never grows and falls well below its start once a packet has
+    run into a layer; the oracle agrees on the final state."""
+    full = tuple(N) + ((1,) if dims == 2 else ())
+    f = W.Fields(abs_W=0.8, abs_width=6.0, abs_axes=1)  # layers on the two x faces
+    prob = W.Problem(dims, full, (1.0, 1.0, 1.0), 0.9 * W.stability_limit(dims), 0.2, f)
+    c = [n / 2.0 for n in N]
+    psi = W.gaussian_packet(prob, 3.0, (1.2,) + (0.0,) * (dims - 1), tuple(c))
+    prec = D.FP64 if precision == "fp64" else D.FP32
+    E = []
+    with D.Sim(prob, prec) as s:
+        s.set_spinor(psi)
+        E.append(s.norm()[0])
+        for _ in range(40):
+            s.step(1)
+            E.append(s.norm()[0])
+        out = s.get_spinor()
+    d = np.diff(E)
+    slack = 1e-13 if precision == "fp64" else 2e-7
+    assert np.all(d <= slack * E[0])
+    assert E[-1] < 0.8 * E[0]
+    ref = O.step(prob, psi, 40)
+    assert rel(out, ref) < (FP64_TOL if precision == "fp64" else FP32_TOL)
