@@ -139,7 +139,9 @@ dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], const doubl
                           unsigned flags, void* cuda_stream);
 
 /* Copy a full state in the canonical host layout (complex128) into the
-   simulation (converted to the simulation's precision on the device). */
+   simulation (converted to the simulation's precision on the device).  The
+   functional of the new state is reduced on the device as the reference of
+   dirac_check (two more launches, no synchronisation). */
 dirac_status dirac_set_spinor(dirac_sim* sim, const double* host);
 
 /* Copy the current state out in the canonical host layout (complex128);
@@ -245,6 +247,50 @@ dirac_status dirac_set_plan(dirac_sim* sim, const dirac_plan* plan);
  * simulation without fused kernels keeps its zero plan (DIRAC_OK).
  */
 dirac_status dirac_autotune(dirac_sim* sim, dirac_plan* out);
+
+/*
+ * Stability diagnostics (Props. 2 and 4, Sect. 2.2 and Sect. 3).
+ *
+ * dirac_functional_bounds: constants lo, hi with
+ *     lo * sum|psi|^2 <= E <= hi * sum|psi|^2   for every state,
+ * E the conserved functional.  Without a vector potential, or with a
+ * constant one, lo = 1 - rho and hi = 1 + rho, rho = sqrt(sum_a (dt/dx_a)^2)
+ * (the cross term of E is, per lattice momentum k, a Hermitian 2x2 block
+ * pattern whose largest singular value is rho; the bounds are attained at the
+ * zone corner) - a sharpened form of the paper's estimate.  With any other
+ * vector potential the paper's estimate itself: lo = 1 - sum_a dt/dx_a,
+ * hi = 1 + sum_a dt/dx_a.  lo <= 0 means E bounds nothing (beyond the
+ * stability limit, or too coarse an estimate).  Host only: no device work.
+ * general_A: 0 = no or constant vector potential, 1 = any other.
+ */
+void dirac_functional_bounds(int dims, const double dx[3], double dt, int general_A, double* lo,
+                             double* hi);
+
+/* Result of dirac_check.  E_ref and naive_ref are taken from the state set
+   by the last dirac_set_spinor / dirac_set_spinor_device (NaN before any). */
+typedef struct {
+  double E, naive;          /* now (as dirac_norm) */
+  double E_ref, naive_ref;  /* at the last set_spinor */
+  double drift;             /* (E - E_ref) / |E_ref| */
+  double lower, upper;      /* bounds on naive implied by E: E/hi <= naive <= E/lo
+                               (0 and +inf where no bound applies) */
+  unsigned failed;          /* DIRAC_CHECK_* bits of the checks that failed */
+} dirac_check_report;
+#define DIRAC_CHECK_NONFINITE 0x1u /* E or the naive norm is not finite */
+#define DIRAC_CHECK_BOUND 0x2u     /* the naive norm is outside [lower, upper] */
+#define DIRAC_CHECK_DRIFT 0x4u     /* |drift| > tol for a conserving field set (real V, no
+                                      time-dependent A), or drift > tol with Im V <= 0 */
+
+/*
+ * Check the invariants the paper proves for the current state: E finite, E
+ * conserved (real V and static A) or not growing (Im V <= 0 everywhere), and
+ * sum|psi|^2 within the bounds that E implies (dirac_functional_bounds;
+ * relative slack 1e-10 for the rounding of the sums).  Synchronises.  Fills
+ * *out (may be NULL) and returns DIRAC_ERR_DIVERGED when a check failed,
+ * DIRAC_OK otherwise.  Costs one dirac_norm (no pass over the state right
+ * after a dirac_step of the FP32 fused path, whose last step accumulates E).
+ */
+dirac_status dirac_check(dirac_sim* sim, double tol, dirac_check_report* out);
 
 /* device bytes a simulation of this shape and precision allocates (without
    the optional static potential): the state, plus for DIRAC_FP32 a second

@@ -39,6 +39,8 @@ struct dirac_sim {
   double* partials = nullptr;
   double* sums_dev = nullptr;
   double* sums_host = nullptr; // pinned
+  double* ref_sums = nullptr;  // device: observables sums of the state set last (dirac_check)
+  int ref_valid = 0;
   int red_blocks = 0;
   double t0 = 0;              // time set by dirac_set_time (or 0)
   long long k = 0;            // steps taken since then: t = t0 + k dt
@@ -457,7 +459,8 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
   s->red_blocks = observables_blocks(s->N, dims);
   if ((e = cudaMalloc(&s->partials, (size_t)s->red_blocks * kObsSums * sizeof(double))) != cudaSuccess)
     return cleanup_fail(cuda_fail(s, e, "cudaMalloc(partials)"));
-  if ((e = cudaMalloc(&s->sums_dev, kObsSums * sizeof(double))) != cudaSuccess)
+  if ((e = cudaMalloc(&s->sums_dev, kObsSums * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&s->ref_sums, kObsSums * sizeof(double))) != cudaSuccess)
     return cleanup_fail(cuda_fail(s, e, "cudaMalloc(sums)"));
   if ((e = cudaMallocHost(&s->sums_host, kObsSums * sizeof(double))) != cudaSuccess)
     return cleanup_fail(cuda_fail(s, e, "cudaMallocHost(sums)"));
@@ -491,9 +494,12 @@ extern "C" void dirac_destroy(dirac_sim* s) {
   cudaFree(s->e_sums);
   cudaFree(s->partials);
   cudaFree(s->sums_dev);
+  cudaFree(s->ref_sums);
   if (s->sums_host) cudaFreeHost(s->sums_host);
   delete s;
 }
+
+static dirac_status take_reference(dirac_sim* s);
 
 extern "C" dirac_status dirac_set_spinor(dirac_sim* s, const double* host) {
   if (!s || !host) return fail(s, DIRAC_ERR_INVALID, "NULL argument");
@@ -512,7 +518,7 @@ extern "C" dirac_status dirac_set_spinor(dirac_sim* s, const double* host) {
       CK(s, cudaGetLastError());
     }
   }
-  return DIRAC_OK;
+  return take_reference(s);
 }
 
 extern "C" dirac_status dirac_get_spinor(dirac_sim* s, double* host) {
@@ -554,7 +560,7 @@ extern "C" dirac_status dirac_set_spinor_device(dirac_sim* s, const void* dev) {
       CK(s, cudaGetLastError());
     }
   }
-  return DIRAC_OK;
+  return take_reference(s);
 }
 
 extern "C" dirac_status dirac_get_spinor_device(dirac_sim* s, void* dev) {
@@ -855,7 +861,7 @@ static dirac_status batch_step_impl(dirac_sim* const* sims, int nsims, long nste
 }
 
 template <class P>
-static dirac_status observe(dirac_sim* s, int dens_axis, int dens_X) {
+static dirac_status observe_launch(dirac_sim* s, int dens_axis, int dens_X, double* out_dev) {
   ObsArgs<P> a;
   std::memset(&a, 0, sizeof(a));
   typename P::cplx* pl[8];
@@ -873,9 +879,15 @@ static dirac_status observe(dirac_sim* s, int dens_axis, int dens_X) {
   if (s->dims == 3) launch_observables<P, 3>(a, s->red_blocks, s->stream);
   else launch_observables<P, 2>(a, s->red_blocks, s->stream);
   CK(s, cudaGetLastError());
-  launch_finish_sums(s->partials, s->red_blocks, s->sums_dev, s->stream);
+  launch_finish_sums(s->partials, s->red_blocks, out_dev, s->stream);
   s->launches += 2;
   CK(s, cudaGetLastError());
+  return DIRAC_OK;
+}
+template <class P>
+static dirac_status observe(dirac_sim* s, int dens_axis, int dens_X) {
+  dirac_status st = observe_launch<P>(s, dens_axis, dens_X, s->sums_dev);
+  if (st != DIRAC_OK) return st;
   CK(s, cudaMemcpyAsync(s->sums_host, s->sums_dev, kObsSums * sizeof(double), cudaMemcpyDeviceToHost,
                         s->stream));
   CK(s, cudaStreamSynchronize(s->stream));
@@ -884,6 +896,15 @@ static dirac_status observe(dirac_sim* s, int dens_axis, int dens_X) {
 
 static dirac_status observe_any(dirac_sim* s, int dens_axis, int dens_X) {
   return s->prec == DIRAC_FP64 ? observe<F64>(s, dens_axis, dens_X) : observe<F32>(s, dens_axis, dens_X);
+}
+
+// reduce the functional of the state just set into ref_sums (stream-ordered,
+// no synchronisation): the reference of dirac_check
+static dirac_status take_reference(dirac_sim* s) {
+  dirac_status st = s->prec == DIRAC_FP64 ? observe_launch<F64>(s, -1, 0, s->ref_sums)
+                                          : observe_launch<F32>(s, -1, 0, s->ref_sums);
+  s->ref_valid = st == DIRAC_OK;
+  return st;
 }
 
 extern "C" dirac_status dirac_norm(dirac_sim* s, double* E, double* naive) {
@@ -1040,5 +1061,71 @@ extern "C" dirac_status dirac_autotune(dirac_sim* s, dirac_plan* out) {
     g_plans[plan_key(s)] = p;
   }
   if (out) *out = p;
+  return DIRAC_OK;
+}
+
+
+extern "C" void dirac_functional_bounds(int dims, const double dx[3], double dt, int general_A, double* lo,
+                                        double* hi) {
+  double sum = 0.0, sum2 = 0.0;
+  for (int a = 0; a < dims && dx; ++a) {
+    const double r = dt / dx[a];
+    sum += r;
+    sum2 += r * r;
+  }
+  const double rho = general_A ? sum : std::sqrt(sum2);
+  if (lo) *lo = 1.0 - rho;
+  if (hi) *hi = 1.0 + rho;
+}
+
+extern "C" dirac_status dirac_check(dirac_sim* s, double tol, dirac_check_report* out) {
+  if (!s) return fail(s, DIRAC_ERR_INVALID, "NULL sim");
+  if (!(tol >= 0.0)) return fail(s, DIRAC_ERR_INVALID, "tol must be >= 0");
+  dirac_check_report r;
+  std::memset(&r, 0, sizeof(r));
+  const double nan = std::nan("");
+  r.E_ref = r.naive_ref = r.drift = nan;
+  dirac_status st = dirac_norm(s, &r.E, &r.naive);
+  if (st != DIRAC_OK && st != DIRAC_ERR_DIVERGED) return st;
+  if (!std::isfinite(r.E) || !std::isfinite(r.naive)) r.failed |= DIRAC_CHECK_NONFINITE;
+  if (s->ref_valid) {
+    double ref[kObsSums];
+    CK(s, cudaMemcpyAsync(s->sums_host, s->ref_sums, kObsSums * sizeof(double), cudaMemcpyDeviceToHost,
+                          s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    std::memcpy(ref, s->sums_host, sizeof(ref));
+    r.naive_ref = ref[0];
+    r.E_ref = ref[0];
+    for (int a = 0; a < s->dims; ++a) r.E_ref += (s->dt / s->dx[a]) * ref[1 + a];
+    r.drift = (r.E - r.E_ref) / std::fabs(r.E_ref);
+  }
+  // bounds of the functional as a quadratic form
+  double lo = 0.0, hi = 0.0;
+  const int general_A = s->link_mode == LINK_GENERAL || s->link_mode == LINK_PLANE;
+  dirac_functional_bounds(s->dims, s->dx, s->dt, general_A, &lo, &hi);
+  r.lower = 0.0;
+  r.upper = INFINITY;
+  if (lo > 0.0 && std::isfinite(r.E)) {
+    r.lower = r.E / hi;
+    r.upper = r.E / lo;
+    const double slack = 1e-10 * r.naive;
+    if (r.naive < r.lower - slack || r.naive > r.upper + slack) r.failed |= DIRAC_CHECK_BOUND;
+  }
+  // conservation (real V, static A) or no growth (Im V <= 0 everywhere)
+  const bool moving_A = s->f.Apw_amp != 0.0 && s->f.Apw_omega != 0.0;
+  const bool imag = s->f.V0_imag != 0.0 || s->f.abs_W != 0.0;
+  const bool damping = s->f.V0_imag <= 0.0 && s->f.abs_W >= 0.0;
+  if (s->ref_valid && !moving_A && std::isfinite(r.drift)) {
+    if (!imag && std::fabs(r.drift) > tol) r.failed |= DIRAC_CHECK_DRIFT;
+    if (imag && damping && r.drift > tol) r.failed |= DIRAC_CHECK_DRIFT;
+  }
+  if (out) *out = r;
+  if (r.failed) {
+    std::string m = "stability check failed:";
+    if (r.failed & DIRAC_CHECK_NONFINITE) m += " non-finite values;";
+    if (r.failed & DIRAC_CHECK_BOUND) m += " sum |psi|^2 outside the bounds implied by E;";
+    if (r.failed & DIRAC_CHECK_DRIFT) m += " E drifted beyond tol;";
+    return fail(s, DIRAC_ERR_DIVERGED, m);
+  }
   return DIRAC_OK;
 }

@@ -56,6 +56,16 @@ class Plan(C.Structure):
                 "us_per_step": self.us_per_step}
 
 
+class CheckReport(C.Structure):
+    _fields_ = [("E", C.c_double), ("naive", C.c_double), ("E_ref", C.c_double), ("naive_ref", C.c_double),
+                ("drift", C.c_double), ("lower", C.c_double), ("upper", C.c_double), ("failed", C.c_uint)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+CHECK_NONFINITE, CHECK_BOUND, CHECK_DRIFT = 0x1, 0x2, 0x4
+
 _vp = C.c_void_p
 _dp = C.POINTER(C.c_double)
 _lib.dirac_create.argtypes = [C.POINTER(_vp), C.c_int, C.POINTER(C.c_int), _dp, C.c_double,
@@ -80,13 +90,16 @@ _lib.dirac_version.restype = C.c_int
 _lib.dirac_get_plan.argtypes = [_vp, C.POINTER(Plan)]
 _lib.dirac_set_plan.argtypes = [_vp, C.POINTER(Plan)]
 _lib.dirac_autotune.argtypes = [_vp, C.POINTER(Plan)]
+_lib.dirac_check.argtypes = [_vp, C.c_double, C.POINTER(CheckReport)]
+_lib.dirac_functional_bounds.argtypes = [C.c_int, _dp, C.c_double, C.c_int, _dp, _dp]
+_lib.dirac_functional_bounds.restype = None
 _lib.dirac_kernel_launches.argtypes = [_vp]
 _lib.dirac_kernel_launches.restype = C.c_longlong
 
 for _name in ("dirac_create", "dirac_set_spinor", "dirac_get_spinor", "dirac_set_spinor_device",
               "dirac_get_spinor_device", "dirac_step", "dirac_batch_step", "dirac_norm",
               "dirac_partial_density", "dirac_get_time", "dirac_set_time", "dirac_get_plan",
-              "dirac_set_plan", "dirac_autotune"):
+              "dirac_set_plan", "dirac_autotune", "dirac_check"):
     getattr(_lib, _name).restype = C.c_int
 
 
@@ -137,6 +150,14 @@ def batch_step(sims, nsteps):
     rc = _lib.dirac_batch_step(arr, len(sims), int(nsteps))
     if rc != OK:
         raise DiracError(rc, _lib.dirac_last_error(None).decode())
+
+
+def functional_bounds(dims, dx, dt, general_A=False):
+    """(lo, hi) with lo sum|psi|^2 <= E <= hi sum|psi|^2 (dirac_functional_bounds)."""
+    d = (C.c_double * 3)(*[float(v) for v in (list(dx) + [1.0, 1.0, 1.0])[:3]])
+    lo, hi = C.c_double(), C.c_double()
+    _lib.dirac_functional_bounds(int(dims), d, float(dt), int(bool(general_A)), C.byref(lo), C.byref(hi))
+    return lo.value, hi.value
 
 
 def state_bytes(dims, N, precision):
@@ -208,6 +229,15 @@ class Sim:
     @property
     def launches(self):
         return int(_lib.dirac_kernel_launches(self._h))
+
+    def check(self, tol=1e-6):
+        """dirac_check: (ok, report).  ok is False when a check failed
+        (DIRAC_ERR_DIVERGED); any other failure raises."""
+        r = CheckReport()
+        rc = _lib.dirac_check(self._h, float(tol), C.byref(r))
+        if rc not in (OK, ERR_DIVERGED):
+            self._check(rc)
+        return rc == OK, r.as_dict()
 
     @property
     def plan(self):
