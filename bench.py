@@ -249,9 +249,12 @@ def run_serve(args, rank, world):
     torch.cuda.set_device(local)
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.6 * free)
-    # calibration: a burst (all arrive at t = 0) of the stream's first requests
+    # calibration: a burst (all arrive at t = 0) of the stream's first requests,
+    # run once untimed first (the process's first kernel launches, allocations
+    # and module loads would otherwise lower the rate)
     cal = serve.make_requests(12, seed=args.seed, rate=1e9)
     srv = serve.Server(budget, quantum=args.quantum)
+    srv.run(cal)
     c = srv.run(cal)
     glups_sat = c["glups"]
     stream = serve.make_requests(args.requests, seed=args.seed, rate=1.0)
@@ -267,7 +270,7 @@ def run_serve(args, rank, world):
         sub.append(r2)
     fp64 = serve.plain_fp64_glups(sub)
     res = {"metric": METRIC, "value": out["glups"], "unit": "GLUPS", "n_gpus": world,
-           "steps": out["requests"], "warmup": 12, "ms_per_step": 1000.0 * out["makespan_s"] / out["requests"],
+           "steps": out["requests"], "warmup": 24, "ms_per_step": 1000.0 * out["makespan_s"] / out["requests"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic",
            "config": {"workload": "serving stream: seeded Poisson arrivals; each request (2+1)D side "
@@ -304,8 +307,11 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison line")
-    ap.add_argument("--plan", default="autotune", choices=["autotune", "rule"],
-                    help="launch plan: timed by dirac_autotune before the warm-up, or the built-in rule")
+    ap.add_argument("--plan", default="autotune",
+                    help="launch plan: 'autotune' (timed by dirac_autotune before the warm-up), 'rule' "
+                         "(the built-in rule), or a fixed 'CHUNK' / 'CHUNK:CHUNK2' (levels per work "
+                         "item of the one-step / (2+1)D two-step kernel), e.g. to profile the plan "
+                         "the autotuner picked")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -353,7 +359,14 @@ def main():
     if on_device:
         del dpsi
     # launch plan (chunk lengths, one or two steps per pass): measured on this state, untimed
-    plan = dict(sim.autotune() if args.plan == "autotune" else sim.plan, source=args.plan)
+    if args.plan == "autotune":
+        plan = dict(sim.autotune(), source="autotune")
+    elif args.plan == "rule":
+        plan = dict(sim.plan, source="rule")
+    else:
+        c = [int(v) for v in args.plan.split(":")]
+        sim.set_plan(chunk=c[0], two_step=int(prob.dims == 2 and len(c) > 1), chunk2=c[1] if len(c) > 1 else 0)
+        plan = dict(sim.plan, source="fixed")
 
     def one_step():
         sim.step(n)
