@@ -185,15 +185,22 @@ static int has_vector_potential(const oracle_problem* p) {
   return p->A_const[0] != 0.0 || p->A_const[1] != 0.0 || p->A_const[2] != 0.0 || p->Apw_amp != 0.0;
 }
 
-/* component a of the vector potential at point y, time t */
-static double vector_potential(const oracle_problem* p, int a, const double y[3], double t) {
-  double A = p->A_const[a];
+/* Line integral of component a of the vector potential along the link of
+   length h in direction a whose midpoint is y, at time t (Sect. 4: the
+   Peierls phase is q times the line integral of A).  The constant part
+   gives A_a h; the plane wave amp cos(k.x - w t + phase) gives, along a,
+   amp h cos(k.y - w t + phase) sin(k_a h/2) / (k_a h/2). */
+static double vector_potential_integral(const oracle_problem* p, int a, const double y[3], double h,
+                                        double t) {
+  double integral = p->A_const[a] * h;
   if (p->Apw_amp != 0.0 && p->Apw_pol == a) {
     double ph = -p->Apw_omega * t + p->Apw_phase;
     for (int b = 0; b < p->dims; ++b) ph += p->Apw_k[b] * y[b];
-    A += p->Apw_amp * cos(ph);
+    double u = 0.5 * p->Apw_k[a] * h;
+    double sinc = u == 0.0 ? 1.0 : sin(u) / u;
+    integral += p->Apw_amp * h * cos(ph) * sinc;
   }
-  return A;
+  return integral;
 }
 
 /* The difference part of one update at half-lattice point (X,Y,Z):
@@ -224,8 +231,8 @@ static cplx stencil(const oracle_problem* p, const grid* g, const cplx* psi, lon
       double yp[3] = {xs[0], xs[1], xs[2]}, ym[3] = {xs[0], xs[1], xs[2]};
       yp[a] += h / 2.0;
       ym[a] -= h / 2.0;
-      double phi_p = p->q * vector_potential(p, a, yp, t) * h;
-      double phi_m = p->q * vector_potential(p, a, ym, t) * h;
+      double phi_p = p->q * vector_potential_integral(p, a, yp, h, t);
+      double phi_m = p->q * vector_potential_integral(p, a, ym, h, t);
       up = up * cexp(-I * phi_p);
       dn = dn * cexp(I * phi_m);
     }

@@ -292,6 +292,32 @@ def test_gauge_covariance_constant_vector_potential(dims):
     assert np.max(np.abs(outA - gauge * out0)) < 1e-12
 
 
+@pytest.mark.parametrize("dims,axis", [(2, 0), (2, 1), (3, 2)])
+def test_gauge_covariance_longitudinal_plane_wave(dims, axis):
+    """Sect. 4: the Peierls phase of a link is q times the line integral of
+    A along it.  A static longitudinal wave A_a = amp cos(k x_a + ph) along
+    axis a is the pure gauge grad chi, chi = (amp/k) sin(k x_a + ph), so
+    psi_A(t) = exp(i q chi) psi_0(t) holds exactly at every value; evaluating
+    A at the link midpoint instead misses this by O((k dx)^2)."""
+    N = (8, 6, 10)
+    prob = W.Problem(dims, N if dims == 3 else (8, 6, 1), (1.0, 1.0, 1.0),
+                     0.9 * W.stability_limit(dims), 0.4)
+    prob = prob.with_fields(V_static=W.random_potential(prob, 6, 0.5))
+    q, amp, ph = 0.8, 0.9, 0.35
+    k = 2 * math.pi * 2 / (prob.N[axis] * prob.dx[axis])
+    kvec = [0.0, 0.0, 0.0]
+    kvec[axis] = k
+    psi0 = W.random_state(prob, 4)
+    gauge = np.zeros(prob.shape, complex)
+    for pl in range(prob.n_planes):
+        x = W.site_positions(prob, pl)[axis]
+        gauge[pl] = np.exp(1j * q * amp / k * np.sin(k * x + ph))
+    out0 = O.step(prob, psi0, 30)
+    f = dict(q=q, Apw_amp=amp, Apw_k=tuple(kvec), Apw_omega=0.0, Apw_phase=ph, Apw_pol=axis)
+    outA = O.step(prob.with_fields(**f), gauge * psi0, 30)
+    assert np.max(np.abs(outA - gauge * out0)) < 1e-12
+
+
 def test_uniform_time_dependent_vector_potential_2d():
     """Sect. 4 with a spatially uniform A(t): a lattice plane wave stays a
     plane wave whose momentum is shifted, P_a = (2/dx) sin((k_a - q A_a(t))
