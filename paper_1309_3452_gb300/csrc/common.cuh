@@ -319,11 +319,14 @@ __device__ __forceinline__ double potential_at(const FieldDesc& f, int dims, lon
   return V;
 }
 
-// link phase phi = q A_a(midpoint, t) dx_a/2 for the link from half-lattice
-// point H towards dir (+1/-1) along axis a; the midpoint is at H + dir/2.
+// link phase phi = q * (line integral of A_a along the link, Sect. 4) for the
+// link of length h = dx_a/2 from half-lattice point H towards dir (+1/-1)
+// along axis a, midpoint H + dir/2: A_const h, plus for the plane wave
+// amp h cos(k.mid - w t + phase) sin(k_a h/2)/(k_a h/2)
 __device__ __forceinline__ double link_phase(const FieldDesc& f, int dims, const long long H[3],
                                              int axis, int dir, double t) {
-  double A = f.A_const[axis];
+  const double h = f.dx[axis] * 0.5;
+  double I = f.A_const[axis] * h;
   if (f.Apw_amp != 0.0 && f.Apw_pol == axis) {
     double ph = -f.Apw_omega * t + f.Apw_phase;
     for (int b = 0; b < dims; ++b) {
@@ -331,9 +334,10 @@ __device__ __forceinline__ double link_phase(const FieldDesc& f, int dims, const
       if (b == axis) y += dir * f.dx[b] * 0.25;
       ph += f.Apw_k[b] * y;
     }
-    A += f.Apw_amp * cos(ph);
+    const double u = 0.5 * f.Apw_k[axis] * h;
+    I += f.Apw_amp * h * cos(ph) * (u == 0.0 ? 1.0 : sin(u) / u);
   }
-  return f.q * A * f.dx[axis] * 0.5;
+  return f.q * I;
 }
 
 // ------------------------------------------------------------------ double-float

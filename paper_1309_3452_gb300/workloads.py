@@ -282,6 +282,23 @@ def workload_klein(N: int = 4096, steps: int = 5000, m: float = 0.2, sigma: floa
     return prob, psi, steps
 
 
+def workload_klein_oblique(N: int = 4096, steps: int = 3000, sigma: float = 64.0, kabs: float = 0.25,
+                           angle_to_step_deg: float = 37.0, offset: float = 4.0):
+    """(2+1)D Klein refraction (Sect. 5, the oblique-incidence example): m = 0,
+    step height V = 2E (E = |k0|, the continuum packet energy) at x0 = N/2 + 1/4,
+    a packet whose momentum makes angle_to_step_deg with the step (the y-axis),
+    i.e. an incidence angle of 90 - angle_to_step_deg from the step's normal,
+    centred offset*sigma before the step along its direction of motion."""
+    inc = math.radians(90.0 - angle_to_step_deg)
+    k0 = (kabs * math.cos(inc), kabs * math.sin(inc))
+    x0 = N / 2.0 + 0.25
+    f = Fields(step_axis=0, step_x0=x0, step_V=2.0 * kabs)
+    prob = Problem(2, (N, N, 1), (1.0, 1.0, 1.0), 0.9 * stability_limit(2), 0.0, f)
+    c = (x0 - offset * sigma * math.cos(inc), N / 2.0 - offset * sigma * math.sin(inc))
+    psi = gaussian_packet(prob, sigma, k0, c)
+    return prob, psi, steps
+
+
 def laser_fields(N: int) -> Fields:
     """Soft-core potential -1/sqrt(|x-c|^2 + 1) at the box centre plus a plane
     wave A_x = 0.5 cos(2 pi z / 64 - omega t), omega = 2 pi / 64."""

@@ -345,3 +345,53 @@ def test_absorbing_layers_functional_never_grows(D, dims, N, precision):
     assert E[-1] < 0.8 * E[0]
     ref = O.step(prob, psi, 40)
     assert rel(out, ref) < (FP64_TOL if precision == "fp64" else FP32_TOL)
+
+
+@pytest.mark.parametrize("dims,axis", [(2, 0), (3, 2)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_gauge_covariance_longitudinal_wave(D, dims, axis, precision):
+    """Sect. 4: Peierls phases are line integrals of A, so a static
+    longitudinal wave (a pure gauge) only multiplies the state by
+    exp(i q chi), chi = (amp/k) sin(k x_a + ph), on the GPU too."""
+    N = (24, 20, 18)
+    prob = W.Problem(dims, N if dims == 3 else (24, 20, 1), (1.0, 1.0, 1.0), 0.9 * W.stability_limit(dims), 0.4)
+    q, amp, ph = 0.8, 0.9, 0.35
+    k = 2 * math.pi * 2 / (prob.N[axis] * prob.dx[axis])
+    kvec = [0.0, 0.0, 0.0]
+    kvec[axis] = k
+    psi0 = W.random_state(prob, 4)
+    gauge = np.zeros(prob.shape, complex)
+    for pl in range(prob.n_planes):
+        x = W.site_positions(prob, pl)[axis]
+        gauge[pl] = np.exp(1j * q * amp / k * np.sin(k * x + ph))
+    prec = D.FP64 if precision == "fp64" else D.FP32
+    out0, *_ = run_gpu(D, prob, psi0, 40, prec)
+    fA = prob.with_fields(q=q, Apw_amp=amp, Apw_k=tuple(kvec), Apw_omega=0.0, Apw_phase=ph, Apw_pol=axis)
+    outA, *_ = run_gpu(D, fA, gauge * psi0, 40, prec)
+    assert rel(outA, gauge * out0) < (1e-12 if precision == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_klein_negative_refraction(D, precision):
+    """Sect. 5, oblique incidence (m = 0, V = 2E): the GPU state equals the
+    oracle's, and the transmitted packet is refracted to negative angles with
+    phase and group velocity opposed."""
+    from tests import klein_refraction as K
+    prob, psi, _ = W.workload_klein_oblique(N=384, sigma=16.0, kabs=0.5, offset=4.0)
+    x0 = prob.fields.step_x0
+    prec = D.FP64 if precision == "fp64" else D.FP32
+    with D.Sim(prob, prec) as s:
+        s.set_spinor(psi)
+        s.step(250)
+        p1 = s.get_spinor()
+        s.step(100)
+        p2 = s.get_spinor()
+        T = s.partial_density(0, x0)
+    ref = O.step(prob, psi, 350)
+    assert rel(p2, ref) < (FP64_TOL if precision == "fp64" else FP32_TOL)
+    v, part = K.velocity(prob, p1, p2, 100, x0)
+    ang_t = math.degrees(math.atan2(v["T"][1], v["T"][0]))
+    assert -60.0 < ang_t < -40.0
+    kt = part["T"][2]
+    assert kt @ v["T"] / (np.linalg.norm(kt) * np.linalg.norm(v["T"])) < -0.9
+    assert abs(T - part["T"][0]) < 1e-6

@@ -533,3 +533,29 @@ def test_absorbing_layer_placement(dims):
     clear = min(prob.N[a] // 2 for a in range(dims)) - 2 - 5  # cells to the layer edge (width 4 + 1)
     assert np.array_equal(O.step(lay, psi, clear), O.step(prob, psi, clear))
     assert not np.array_equal(O.step(lay, psi, clear + 6), O.step(prob, psi, clear + 6))
+
+
+# ---------------------------------------------------------------- Klein refraction (Sect. 5)
+def test_klein_step_negative_refraction():
+    """Sect. 5, oblique incidence on a Klein step with m = 0 and V = 2E: the
+    transmitted packet is refracted to the other side of the normal (negative
+    angle, specular for a single plane wave since |k| is the same on both
+    sides), the reflected one leaves at the specular angle, and on the far
+    side phase and group velocity point in opposite directions while on the
+    near side they agree."""
+    from tests import klein_refraction as K
+    prob, psi, _ = W.workload_klein_oblique(N=384, sigma=16.0, kabs=0.5, offset=4.0)
+    x0 = prob.fields.step_x0
+    inc = math.radians(90.0 - 37.0)
+    p1 = O.step(prob, psi, 250)
+    p2 = O.step(prob, p1, 100, 250 * prob.dt)
+    v, part = K.velocity(prob, p1, p2, 100, x0)
+    ang_t = math.degrees(math.atan2(v["T"][1], v["T"][0]))
+    ang_r = math.degrees(math.atan2(v["R"][1], v["R"][0]))
+    assert -60.0 < ang_t < -40.0                      # negative refraction (53 deg incidence)
+    assert abs(ang_r - (180.0 - math.degrees(inc))) < 3.0  # specular reflection
+    assert part["T"][0] > 0.2 and part["R"][0] > 0.5
+    kt, kr = part["T"][2], part["R"][2]
+    cos_t = kt @ v["T"] / (np.linalg.norm(kt) * np.linalg.norm(v["T"]))
+    cos_r = kr @ v["R"] / (np.linalg.norm(kr) * np.linalg.norm(v["R"]))
+    assert cos_t < -0.9 and cos_r > 0.9
