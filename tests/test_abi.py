@@ -64,6 +64,10 @@ def test_host_only_validation(lib):
         g.abs_W, g.abs_width, g.abs_axes = 0.5, width, axes
         assert L.dirac_create(C.byref(h), dims, N, dx, 0.5, 0.0, C.byref(g), 0, 0, None) == D.ERR_INVALID
     assert b"abs_axes" in L.dirac_last_error(None)
+    # grids beyond the 32-bit row indexing of the kernels are refused before any device work
+    big = (C.c_int * 3)(65536, 32768, 1)
+    assert L.dirac_create(C.byref(h), 2, big, dx, 0.5, 0.0, None, 1, 0, None) == D.ERR_UNSUPPORTED
+    assert b"2^31" in L.dirac_last_error(None)
     assert not h.value
     # device bytes: 8 planes x 8^3 cells x complex128
     assert D.state_bytes(3, (8, 8, 8), D.FP64) == 8 * 512 * 16

@@ -4,8 +4,8 @@ benchmark times (FP32 fused kernels; FP64 split kernels for the FP64 line).
 * (3+1)D 128^3, 1000 steps: sampled values and E against stored oracle
   results (tests/golden/workload_3d128_1000.json, written by
   tests/golden/make_golden.py from the oracle only).
-* (2+1)D 4096^2 Klein step and (3+1)D 512^3 soft core + plane-wave vector
-  potential: light-cone windows.  After n steps a value depends only on the
+* (2+1)D 4096^2 Klein step, the oblique Klein refraction workload and (3+1)D
+  512^3 soft core + plane-wave vector potential: light-cone windows.  After n steps a value depends only on the
   values within n cells (one half-lattice site per half-step), so the oracle
   run on a periodic window of half-width n + 2 around a cell, placed at the
   same position (origin), reproduces that cell exactly; windows are kept
@@ -130,3 +130,23 @@ def test_workload_laser512_windows(env):
         want = ref[:, w:w + 1, w:w + 1, w:w + 1]
         scale = max(float(np.max(np.abs(ref))), 1e-30)
         assert float(np.max(np.abs(got - want))) / scale < 2e-6, cell
+
+
+def test_workload_klein_oblique4096_windows_and_conservation(env):
+    torch, D = env
+    prob, psi, _ = W.workload_klein_oblique(N=4096)
+    n = 10
+    x0 = prob.fields.step_x0
+    with D.Sim(prob, D.FP32) as s:
+        s.set_spinor(psi)
+        E0, _ = s.norm()
+        s.step(n)
+        out = s.get_spinor()
+        # around the packet (centred 4 sigma before the step), on both sides of the step, far away
+        c = (int(x0 - 4 * 64 * math.cos(math.radians(53))), int(2048 - 4 * 64 * math.sin(math.radians(53))))
+        cells = [c, (c[0] + 9, c[1] - 17), (2048, 2000), (2049, 2100), (3500, 600), (100, 4000)]
+        check_windows(prob, psi, out, cells, n, 2e-6)
+        s.step(490)
+        ok, r = s.check(1e-6)
+    assert ok, r
+    assert abs(r["E"] - E0) < 1e-6 * abs(E0)
