@@ -292,9 +292,13 @@ typedef struct {
  */
 dirac_status dirac_check(dirac_sim* sim, double tol, dirac_check_report* out);
 
-/* device bytes a simulation of this shape and precision allocates (without
-   the optional static potential): the state, plus for DIRAC_FP32 a second
-   state buffer and one complex128 conversion plane */
+/* device bytes a simulation of this shape and precision allocates for a
+   potential made of V0 and a Klein step only: the state, plus for
+   DIRAC_FP32 a second state buffer and one complex128 conversion plane.
+   Other potentials add one double per value (DIRAC_FP64, or a time-
+   dependent static array) or the coefficient table, 16 bytes per value
+   (DIRAC_FP32, time-independent), and every simulation a few KiB of
+   reduction scratch. */
 size_t dirac_state_bytes(int dims, const int N[3], dirac_precision precision);
 
 /* human-readable description of the last failure on sim (or of the last
