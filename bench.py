@@ -77,26 +77,6 @@ def workload(name):
     return prob, psi, n, desc
 
 
-def tabulated_potential(fields, precision):
-    """The FP32 kernels read a per-site coefficient table (b = 1/(1 + i theta)
-    as hi + lo complex floats, 16 B) for a time-independent potential beyond V0
-    and a Klein step."""
-    if precision != "fp32" or fields is None:
-        return False
-    if fields.V_static is not None:
-        return fields.Vmod_amp == 0.0
-    return fields.sc_Z != 0.0
-
-
-def bytes_per_lup(dims, precision, table=False):
-    """Algorithmic HBM bytes per site update: every value read once and
-    written once per full step (8 complex values per (3+1)D cell, 4 per
-    (2+1)D cell), plus one 16 B coefficient per value read when the
-    potential is tabulated."""
-    vals = 8 if dims == 3 else 4
-    return 2 * vals * (8 if precision == "fp32" else 16) + (16 * vals if table else 0)
-
-
 class Clocks:
     """Samples nvidia-smi during the timed region."""
 
@@ -406,7 +386,7 @@ def main():
 
     # dominant kernel: the time-step kernels; per launch = one full time step
     stencil_ms = (sum(step_ms) - sum(norm_ms)) / args.steps / n
-    bpl = bytes_per_lup(prob.dims, args.precision, tabulated_potential(prob.fields, args.precision))
+    bpl = sim.algorithmic_bytes  # the library's own count for the path it runs (state + per-site tables)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))

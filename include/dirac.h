@@ -292,6 +292,13 @@ typedef struct {
  */
 dirac_status dirac_check(dirac_sim* sim, double tol, dirac_check_report* out);
 
+/* Algorithmic HBM bytes of one site update (one cell advanced one full time
+   step) on this simulation's path: every value read and written once, plus
+   a per-site coefficient (16 bytes) or static potential (8 bytes) read per
+   value where the potential needs one.  The roofline numerator of a time
+   step.  0 for NULL. */
+double dirac_algorithmic_bytes(const dirac_sim* sim);
+
 /* device bytes a simulation of this shape and precision allocates for a
    potential made of V0 and a Klein step only: the state, plus for
    DIRAC_FP32 a second state buffer and one complex128 conversion plane.

@@ -1129,3 +1129,12 @@ extern "C" dirac_status dirac_check(dirac_sim* s, double tol, dirac_check_report
   }
   return DIRAC_OK;
 }
+
+
+extern "C" double dirac_algorithmic_bytes(const dirac_sim* s) {
+  if (!s) return 0.0;
+  double b = 2.0 * s->np * (double)s->elem;                    // every value read and written once
+  if (s->coef_mode == COEF_TABLE) b += 16.0 * s->np;           // one coefficient per value read
+  if (s->coef_mode == COEF_GENERAL && s->Vstatic) b += 8.0 * s->np;  // one real per value read
+  return b;
+}

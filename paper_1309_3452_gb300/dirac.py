@@ -93,6 +93,8 @@ _lib.dirac_autotune.argtypes = [_vp, C.POINTER(Plan)]
 _lib.dirac_check.argtypes = [_vp, C.c_double, C.POINTER(CheckReport)]
 _lib.dirac_functional_bounds.argtypes = [C.c_int, _dp, C.c_double, C.c_int, _dp, _dp]
 _lib.dirac_functional_bounds.restype = None
+_lib.dirac_algorithmic_bytes.argtypes = [_vp]
+_lib.dirac_algorithmic_bytes.restype = C.c_double
 _lib.dirac_kernel_launches.argtypes = [_vp]
 _lib.dirac_kernel_launches.restype = C.c_longlong
 
@@ -238,6 +240,11 @@ class Sim:
         if rc not in (OK, ERR_DIVERGED):
             self._check(rc)
         return rc == OK, r.as_dict()
+
+    @property
+    def algorithmic_bytes(self):
+        """HBM bytes per site update on this simulation's path (dirac_algorithmic_bytes)."""
+        return float(_lib.dirac_algorithmic_bytes(self._h))
 
     @property
     def plan(self):
