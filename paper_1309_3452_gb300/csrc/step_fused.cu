@@ -113,7 +113,7 @@ __host__ __device__ __forceinline__ long long items3d(const int (&N)[3], int chu
 // `a` may live in the constant bank (kernel parameter) or in shared memory.
 template <class P, int COEF, int LINK>
 __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long item, const Thread3d& th,
-                                             unsigned char* smem_raw, float& e_n, float& e_c) {
+                                             unsigned char* smem_raw, double* e_acc) {
   using C = typename P::cplx;
   // every tile is double-buffered by level parity: slot [k & 1] holds level k
   C (*sC)[2][kSlots] = reinterpret_cast<C (*)[2][kSlots]>(smem_raw);  // old C(k)
@@ -217,33 +217,37 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
           const C nA0 = sA[pk][0][t], nA1 = sA[pk][1][t];
           C nC0, nC1, nD0, nD1, S;
           const bool acc = want_e && core;  // this cell's new values count towards E
+          float lc = 0.0f;
           {
             C nb[6] = {nB0k, sB[pk][0][sxm], nB1k, sB[pk][1][sym], nA0n, nA0};
             const int H[3] = {hx, hy, 2 * zk + 1};
             nC0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 4, oC0, nb, H, ok, a.pstride, &S);
-            if (acc) e_c = fmaf(nC0.x, S.x, fmaf(nC0.y, S.y, e_c));
+            if (acc) lc = fmaf(nC0.x, S.x, fmaf(nC0.y, S.y, lc));
           }
           {
             C nb[6] = {sB[pk][1][sxp], nB1k, sB[pk][0][syp], nB0k, nA1n, nA1};
             const int H[3] = {hx + 1, hy + 1, 2 * zk + 1};
             nC1 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 5, oC1, nb, H, ok, a.pstride, &S);
-            if (acc) e_c = fmaf(nC1.x, S.x, fmaf(nC1.y, S.y, e_c));
+            if (acc) lc = fmaf(nC1.x, S.x, fmaf(nC1.y, S.y, lc));
           }
           {
             C nb[6] = {sA[pk][0][sxp], nA0, nA1, sA[pk][1][sym], nB0k, sB[pm][0][t]};
             const int H[3] = {hx + 1, hy, 2 * zk};
             nD0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 6, sD[pk][0][t], nb, H, ok,
                                                 a.pstride, &S);
-            if (acc) e_c = fmaf(nD0.x, S.x, fmaf(nD0.y, S.y, e_c));
+            if (acc) lc = fmaf(nD0.x, S.x, fmaf(nD0.y, S.y, lc));
           }
           {
             C nb[6] = {nA1, sA[pk][1][sxm], sA[pk][0][syp], nA0, nB1k, sB[pm][1][t]};
             const int H[3] = {hx, hy + 1, 2 * zk};
             nD1 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 7, sD[pk][1][t], nb, H, ok,
                                                 a.pstride, &S);
-            if (acc) e_c = fmaf(nD1.x, S.x, fmaf(nD1.y, S.y, e_c));
+            if (acc) lc = fmaf(nD1.x, S.x, fmaf(nD1.y, S.y, lc));
           }
-          if (acc) e_n += ((n2(nB0k) + n2(nB1k)) + (n2(nC0) + n2(nC1))) + (n2(nD0) + n2(nD1));
+          if (acc) {  // this level's few terms in FP32, the running sums in FP64 (shared memory)
+            e_acc[1] += lc;
+            e_acc[0] += ((n2(nB0k) + n2(nB1k)) + (n2(nC0) + n2(nC1))) + (n2(nD0) + n2(nD1));
+          }
           if (core) {
             a.out[2][ok] = nB0k;
             a.out[3][ok] = nB1k;
@@ -254,7 +258,7 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
           }
         }
         if (k + 1 < z1 && core) {
-          if (want_e) e_n += n2(nA0n) + n2(nA1n);
+          if (want_e) e_acc[0] += n2(nA0n) + n2(nA1n);
           a.out[0][on] = nA0n;
           a.out[1][on] = nA1n;
         }
@@ -267,7 +271,7 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
 
 // FP64 block reduction of the two conserved-functional accumulators into
 // out[blockIdx.x][2] (all threads of the block call it)
-__device__ __forceinline__ void block_store_e(float e_n, float e_c, double* out) {
+__device__ __forceinline__ void block_store_e(double e_n, double e_c, double* out) {
   __shared__ double red[32][2];
   double n = e_n, c = e_c;
 #pragma unroll
@@ -302,10 +306,13 @@ __global__ void __launch_bounds__(kThreads3d, 2) fused3d_kernel(const FusedArgs<
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Thread3d th = thread3d();
   const long long items = items3d(a.N, a.chunk);
-  float e_n = 0.0f, e_c = 0.0f;
+  // running sums of the functional, one FP64 pair per thread, kept in shared
+  // memory so that they take no registers in the z-march
+  __shared__ double e_acc[kThreads3d][2];
+  e_acc[threadIdx.x][0] = e_acc[threadIdx.x][1] = 0.0;
   for (long long item = blockIdx.x; item < items; item += a.workers)
-    fused3d_item<P, COEF, LINK>(a, item, th, smem_raw, e_n, e_c);
-  if (a.e_partials) block_store_e(e_n, e_c, a.e_partials);
+    fused3d_item<P, COEF, LINK>(a, item, th, smem_raw, e_acc[threadIdx.x]);
+  if (a.e_partials) block_store_e(e_acc[threadIdx.x][0], e_acc[threadIdx.x][1], a.e_partials);
 }
 
 // simulation of global item g: the last s with first[s] <= g
@@ -346,8 +353,8 @@ __global__ void __launch_bounds__(kThreads3d, 2) fused3d_batch_kernel(const Batc
       __syncthreads();
       cur = s;
     }
-    float e_n = 0.0f, e_c = 0.0f;  // (batched launches never accumulate the functional)
-    fused3d_item<P, COEF, LINK>(sa, g - b.first_item[s], th, smem_raw, e_n, e_c);
+    // (batched launches never accumulate the functional: e_partials is null)
+    fused3d_item<P, COEF, LINK>(sa, g - b.first_item[s], th, smem_raw, nullptr);
   }
 }
 
@@ -396,8 +403,8 @@ __device__ __forceinline__ void row2d(const FusedArgs<P>& a, bool iso, int hx, i
 // One work item (one 32-cell strip over one chunk of rows) of one simulation,
 // processed by one warp.
 template <class P, int COEF, int LINK>
-__device__ __forceinline__ void fused2d_item(const FusedArgs<P>& a, long long item, int lane, float& e_n,
-                                             float& e_c) {
+__device__ __forceinline__ void fused2d_item(const FusedArgs<P>& a, long long item, int lane, double& e_n,
+                                             double& e_c) {
   using C = typename P::cplx;
   const int Nx = a.N[0], Ny = a.N[1];
   const int strips = (Nx + kCore - 1) / kCore;
@@ -442,7 +449,7 @@ __device__ __forceinline__ void fused2d_item(const FusedArgs<P>& a, long long it
         if (a.e_partials) {
           e_n += (fmaf(nU1k.x, nU1k.x, nU1k.y * nU1k.y) + fmaf(nV0.x, nV0.x, nV0.y * nV0.y)) +
                  fmaf(nV1.x, nV1.x, nV1.y * nV1.y);
-          e_c = fmaf(nV1.x, S1.x, fmaf(nV1.y, S1.y, fmaf(nV0.x, S0.x, fmaf(nV0.y, S0.y, e_c))));
+          e_c += fmaf(nV1.x, S1.x, fmaf(nV1.y, S1.y, fmaf(nV0.x, S0.x, nV0.y * S0.y)));
         }
       }
       if (k + 1 < y1) {
@@ -470,7 +477,7 @@ constexpr int kCoreTb = 28;
 
 template <class P, int COEF, int LINK>
 __device__ __forceinline__ void fused2d_tb2_item(const FusedArgs<P>& a, long long item, int lane,
-                                                 float& e_n, float& e_c) {
+                                                 double& e_n, double& e_c) {
   using C = typename P::cplx;
   const int Nx = a.N[0], Ny = a.N[1];
   const int strips = (Nx + kCoreTb - 1) / kCoreTb;
@@ -523,7 +530,7 @@ __device__ __forceinline__ void fused2d_tb2_item(const FusedArgs<P>& a, long lon
           if (a.e_partials) {
             e_n += (fmaf(tU1k.x, tU1k.x, tU1k.y * tU1k.y) + fmaf(tV0.x, tV0.x, tV0.y * tV0.y)) +
                    fmaf(tV1.x, tV1.x, tV1.y * tV1.y);
-            e_c = fmaf(tV1.x, S1.x, fmaf(tV1.y, S1.y, fmaf(tV0.x, S0.x, fmaf(tV0.y, S0.y, e_c))));
+            e_c += fmaf(tV1.x, S1.x, fmaf(tV1.y, S1.y, fmaf(tV0.x, S0.x, tV0.y * S0.y)));
           }
         }
         if (k < y1) {
@@ -552,7 +559,7 @@ __global__ void __launch_bounds__(32 * kFused2dWarps) fused2d_kernel(const Fused
   const int lane = threadIdx.x & 31;
   const long long worker = (long long)blockIdx.x * kFused2dWarps + (threadIdx.x >> 5);
   const long long items = items2d(a.N, a.chunk);
-  float e_n = 0.0f, e_c = 0.0f;
+  double e_n = 0.0, e_c = 0.0;
   for (long long item = worker; item < items; item += a.workers)  // uniform per warp
     fused2d_item<P, COEF, LINK>(a, item, lane, e_n, e_c);
   if (a.e_partials) block_store_e(e_n, e_c, a.e_partials);
@@ -563,7 +570,7 @@ __global__ void __launch_bounds__(32 * kFused2dWarps) fused2d_tb2_kernel(const F
   const int lane = threadIdx.x & 31;
   const long long worker = (long long)blockIdx.x * kFused2dWarps + (threadIdx.x >> 5);
   const long long items = (long long)((a.N[0] + kCoreTb - 1) / kCoreTb) * ((a.N[1] + a.chunk - 1) / a.chunk);
-  float e_n = 0.0f, e_c = 0.0f;
+  double e_n = 0.0, e_c = 0.0;
   for (long long item = worker; item < items; item += a.workers)  // uniform per warp
     fused2d_tb2_item<P, COEF, LINK>(a, item, lane, e_n, e_c);
   if (a.e_partials) block_store_e(e_n, e_c, a.e_partials);
@@ -584,7 +591,7 @@ __global__ void __launch_bounds__(32 * kFused2dWarps) fused2d_batch_kernel(const
       __syncwarp();
       cur = s;
     }
-    float e_n = 0.0f, e_c = 0.0f;  // (batched launches never accumulate the functional)
+    double e_n = 0.0, e_c = 0.0;  // (batched launches never accumulate the functional)
     fused2d_item<P, COEF, LINK>(sa[w], g - b.first_item[s], lane, e_n, e_c);
   }
 }
