@@ -34,17 +34,19 @@
  * without the trailing [2].
  *
  * Ownership: the library allocates and owns all device memory of a
- * simulation; host buffers belong to the caller, are only read or written
- * during the call, and are never retained.
+ * simulation; host buffers belong to the caller and are never retained (a
+ * page-locked buffer given to dirac_set_spinor is read when the stream gets
+ * there, see that call).
  *
  * Errors: every call returns a dirac_status; no exception or abort crosses
  * the ABI.  On failure dirac_last_error() describes the cause.  A CUDA error
  * leaves the simulation in an unspecified state (destroy it).
  *
  * Streams: all device work of a simulation runs on the stream given at
- * creation (NULL = the legacy default stream).  dirac_step only enqueues
- * work; dirac_norm, dirac_partial_density, dirac_get_spinor synchronise the
- * stream before returning.
+ * creation (NULL = the legacy default stream).  dirac_step, dirac_batch_step
+ * and dirac_set_spinor(_device) only enqueue work; dirac_norm,
+ * dirac_partial_density, dirac_get_spinor, dirac_check, dirac_autotune and
+ * dirac_set_plan synchronise the stream before returning.
  * ---------------------------------------------------------------------------
  */
 #ifndef DIRAC_H
@@ -64,8 +66,10 @@ typedef enum {
   DIRAC_ERR_UNSTABLE = 2,    /* r_x^2 + r_y^2 (+ r_z^2) > 1 (Sect. 2.2 / Sect. 3 bound) */
   DIRAC_ERR_OOM = 3,         /* device allocation failed */
   DIRAC_ERR_CUDA = 4,        /* a CUDA call or kernel launch failed */
-  DIRAC_ERR_DIVERGED = 5,    /* the conserved functional became non-finite or grew */
-  DIRAC_ERR_TIMEOUT = 6,     /* a bounded device wait gave up */
+  DIRAC_ERR_DIVERGED = 5,    /* the functional became non-finite (dirac_norm) or a
+                                stability check failed (dirac_check) */
+  DIRAC_ERR_TIMEOUT = 6,     /* reserved for bounded device waits (no kernel of this
+                                build waits on another, so none is returned) */
   DIRAC_ERR_UNSUPPORTED = 7  /* valid request this build does not implement */
 } dirac_status;
 
@@ -140,8 +144,11 @@ dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], const doubl
 
 /* Copy a full state in the canonical host layout (complex128) into the
    simulation (converted to the simulation's precision on the device).  The
-   functional of the new state is reduced on the device as the reference of
-   dirac_check (two more launches, no synchronisation). */
+   copies are enqueued on the simulation's stream: a pageable host buffer may
+   be reused as soon as the call returns, a page-locked one only once the
+   stream has passed this point (any synchronising call).  The functional of
+   the new state is reduced on the device as the reference of dirac_check
+   (two more launches, no synchronisation). */
 dirac_status dirac_set_spinor(dirac_sim* sim, const double* host);
 
 /* Copy the current state out in the canonical host layout (complex128);
