@@ -743,32 +743,41 @@ static bool batchable(const dirac_sim* s) {
 static dirac_status batch_group(dirac_sim* const* g, int n, long nsteps) {
   dirac_sim* s0 = g[0];
   cudaStream_t st = s0->stream;
-  const size_t args_bytes = (size_t)2 * n * sizeof(FusedArgs<F32>);
-  const size_t first_bytes = (size_t)(n + 1) * sizeof(long long);
-  FusedArgs<F32>* h_args = new (std::nothrow) FusedArgs<F32>[2 * n];
-  long long* h_first = new (std::nothrow) long long[n + 1];
+  // (2+1)D groups take two steps per pass for pairs of steps, as stepping alone
+  bool tb = s0->dims == 2 && nsteps >= 2 && std::getenv("DIRAC_NO_TEMPORAL_BLOCKING") == nullptr;
+  for (int i = 0; i < n && tb; ++i) tb = g[i]->tblock != 0;
+  // arguments [mode][buffer parity][sim]: mode 0 one step per pass, 1 two steps
+  const size_t args_bytes = (size_t)4 * n * sizeof(FusedArgs<F32>);
+  const size_t first_bytes = (size_t)2 * (n + 1) * sizeof(long long);  // one-step, two-step items
+  FusedArgs<F32>* h_args = new (std::nothrow) FusedArgs<F32>[4 * n];
+  long long* h_first = new (std::nothrow) long long[2 * (n + 1)];
   if (!h_args || !h_first) {
     delete[] h_args;
     delete[] h_first;
     return fail(s0, DIRAC_ERR_OOM, "host allocation failed");
   }
   h_first[0] = 0;
+  h_first[n + 1] = 0;
   for (int i = 0; i < n; ++i) {
     dirac_sim* s = g[i];
     const int chunk = s->chunk1 > 0 ? s->chunk1 : fused_chunk(s->dims, s->N);
-    for (int p = 0; p < 2; ++p) {
-      FusedArgs<F32> a = fused_args<F32>(s, sim_time(s));
-      a.chunk = chunk;
-      if (p == 1) {
-        for (int k = 0; k < 8; ++k) {  // the other buffer is the input after an odd step
-          typename F32::cplx* tmp = a.out[k];
-          a.out[k] = const_cast<typename F32::cplx*>(a.in[k]);
-          a.in[k] = tmp;
+    const int chunk2 = s->chunk2 > 0 ? s->chunk2 : (tb ? fused_chunk_tb2(s->N) : 0);
+    for (int mode = 0; mode < 2; ++mode) {
+      for (int p = 0; p < 2; ++p) {
+        FusedArgs<F32> a = fused_args<F32>(s, sim_time(s));
+        a.chunk = mode ? chunk2 : chunk;
+        if (p == 1) {
+          for (int k = 0; k < 8; ++k) {  // the other buffer is the input after an odd launch
+            typename F32::cplx* tmp = a.out[k];
+            a.out[k] = const_cast<typename F32::cplx*>(a.in[k]);
+            a.in[k] = tmp;
+          }
         }
+        h_args[(mode * 2 + p) * n + i] = a;
       }
-      h_args[p * n + i] = a;
     }
     h_first[i + 1] = h_first[i] + fused_items(s->dims, s->N, chunk);
+    h_first[n + 1 + i + 1] = h_first[n + 1 + i] + (tb ? fused_items_tb2(s->N, chunk2) : 0);
   }
   void* d = nullptr;
   cudaError_t e = cudaMallocAsync(&d, args_bytes + first_bytes, st);
@@ -776,7 +785,7 @@ static dirac_status batch_group(dirac_sim* const* g, int n, long nsteps) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(static_cast<char*>(d) + args_bytes, h_first, first_bytes, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host tables can be freed
-  const long long total = h_first[n];
+  const long long total = h_first[n], total2 = h_first[2 * n + 1];
   delete[] h_args;
   delete[] h_first;
   if (e != cudaSuccess) {
@@ -785,15 +794,24 @@ static dirac_status batch_group(dirac_sim* const* g, int n, long nsteps) {
   }
   const FusedArgs<F32>* d_args = static_cast<const FusedArgs<F32>*>(d);
   BatchArgs<F32> b;
-  b.first_item = reinterpret_cast<const long long*>(static_cast<char*>(d) + args_bytes);
+  const long long* first = reinterpret_cast<const long long*>(static_cast<char*>(d) + args_bytes);
   b.nsims = n;
   b.workers = 0;
-  for (long i = 0; i < nsteps; ++i) {
-    b.sims = d_args + (i & 1) * n;
-    if (s0->dims == 3)
-      launch_fused_batch<F32, 3>(b, total, s0->coef_mode, s0->link_mode, st);
-    else
-      launch_fused_batch<F32, 2>(b, total, s0->coef_mode, s0->link_mode, st);
+  // every launch swaps the buffers: pairs of steps first, then a single step
+  const long pairs = tb ? nsteps / 2 : 0;
+  const long launches = pairs + (nsteps - 2 * pairs);
+  for (long i = 0; i < launches; ++i) {
+    b.sims = d_args + ((i < pairs ? 2 : 0) + (i & 1)) * n;
+    if (i < pairs) {
+      b.first_item = first + n + 1;
+      launch_fused2d_tb2_batch(b, total2, s0->coef_mode, s0->link_mode, st);
+    } else {
+      b.first_item = first;
+      if (s0->dims == 3)
+        launch_fused_batch<F32, 3>(b, total, s0->coef_mode, s0->link_mode, st);
+      else
+        launch_fused_batch<F32, 2>(b, total, s0->coef_mode, s0->link_mode, st);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) {
       cudaFreeAsync(d, st);
@@ -803,11 +821,11 @@ static dirac_status batch_group(dirac_sim* const* g, int n, long nsteps) {
   cudaFreeAsync(d, st);
   for (int i = 0; i < n; ++i) {
     dirac_sim* s = g[i];
-    if (nsteps & 1) std::swap(s->state, s->state_alt);
+    if (launches & 1) std::swap(s->state, s->state_alt);
     s->k += nsteps;
     s->stepped = 1;
   }
-  g[0]->launches += nsteps;  // one launch per step serves the whole group
+  g[0]->launches += launches;  // one launch per pass serves the whole group
   return DIRAC_OK;
 }
 

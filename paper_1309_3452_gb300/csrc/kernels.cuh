@@ -72,6 +72,12 @@ long long fused_items(int dims, const int N[3], int chunk);
 template <class P, int DIMS>
 void launch_fused_batch(const BatchArgs<P>& b, long long total_items, int coef_mode, int link_mode,
                         cudaStream_t s);
+// (2+1)D two steps per pass: rows per item by the rule, items of a grid, and
+// the batched launch (uniform / Klein-step coefficients, no / constant links)
+int fused_chunk_tb2(const int N[3]);
+long long fused_items_tb2(const int N[3], int chunk);
+void launch_fused2d_tb2_batch(const BatchArgs<F32>& b, long long total_items, int coef_mode, int link_mode,
+                              cudaStream_t s);
 
 // Observables of the stored state: per-block FP64 partial sums of
 // [sum|psi|^2, Bx, By, Bz, sum_{beyond} |psi|^2] with

@@ -596,6 +596,28 @@ __global__ void __launch_bounds__(32 * kFused2dWarps) fused2d_batch_kernel(const
   }
 }
 
+// Two time steps per pass for several (2+1)D simulations (time-independent
+// fields): as fused2d_batch_kernel with the two-step item of each simulation.
+template <class P, int COEF, int LINK>
+__global__ void __launch_bounds__(32 * kFused2dWarps) fused2d_tb2_batch_kernel(const BatchArgs<P> b) {
+  __shared__ FusedArgs<P> sa[kFused2dWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long worker = (long long)blockIdx.x * kFused2dWarps + w;
+  const long long total = b.first_item[b.nsims];
+  int cur = -1;
+  for (long long g = worker; g < total; g += b.workers) {
+    const int s = find_sim(b.first_item, b.nsims, g);
+    if (s != cur) {
+      __syncwarp();
+      copy_args(&sa[w], b.sims + s, lane, 32);
+      __syncwarp();
+      cur = s;
+    }
+    double e_n = 0.0, e_c = 0.0;  // (batched launches never accumulate the functional)
+    fused2d_tb2_item<P, COEF, LINK>(sa[w], g - b.first_item[s], lane, e_n, e_c);
+  }
+}
+
 int sm_count() {
   int dev = 0, n = 0;
   cudaGetDevice(&dev);
@@ -712,6 +734,15 @@ void launch2d_batch(BatchArgs<F32> b, long long total, cudaStream_t s) {
   k<<<(unsigned)((w + kFused2dWarps - 1) / kFused2dWarps), 32 * kFused2dWarps, 0, s>>>(b);
 }
 
+template <int COEF, int LINK>
+void launch2d_tb2_batch(BatchArgs<F32> b, long long total, cudaStream_t s) {
+  auto k = fused2d_tb2_batch_kernel<F32, COEF, LINK>;
+  const int warps = workers2d<fused2d_tb2_batch_kernel<F32, COEF, LINK>>();
+  const long long w = total < warps ? total : warps;
+  b.workers = (int)w;
+  k<<<(unsigned)((w + kFused2dWarps - 1) / kFused2dWarps), 32 * kFused2dWarps, 0, s>>>(b);
+}
+
 template <int DIMS, int COEF, int LINK>
 int launch_dims(const FusedArgs<F32>& a, cudaStream_t s) {
   if (DIMS == 3) return launch3d<COEF, LINK>(a, s);
@@ -763,6 +794,23 @@ int launch_fused2d_tb2(const FusedArgs<F32>& a, cudaStream_t s) {
   if (c == COEF_STEP && l == LINK_CONST) return launch2d_tb2<COEF_STEP, LINK_CONST>(a, s);
   if (c == COEF_TABLE && l == LINK_NONE) return launch2d_tb2<COEF_TABLE, LINK_NONE>(a, s);
   return 0;
+}
+
+int fused_chunk_tb2(const int N[3]) {
+  const int warps = workers2d<fused2d_tb2_kernel<F32, COEF_UNIFORM, LINK_NONE>>();
+  const long long strips = (N[0] + kCoreTb - 1) / kCoreTb;
+  return plan_chunk(strips, N[1], warps, 32, 1.0);
+}
+
+long long fused_items_tb2(const int N[3], int chunk) {
+  return (long long)((N[0] + kCoreTb - 1) / kCoreTb) * ((N[1] + chunk - 1) / chunk);
+}
+
+void launch_fused2d_tb2_batch(const BatchArgs<F32>& b, long long total, int coef, int link, cudaStream_t s) {
+  if (coef == COEF_UNIFORM && link == LINK_NONE) return launch2d_tb2_batch<COEF_UNIFORM, LINK_NONE>(b, total, s);
+  if (coef == COEF_STEP && link == LINK_NONE) return launch2d_tb2_batch<COEF_STEP, LINK_NONE>(b, total, s);
+  if (coef == COEF_UNIFORM && link == LINK_CONST) return launch2d_tb2_batch<COEF_UNIFORM, LINK_CONST>(b, total, s);
+  return launch2d_tb2_batch<COEF_STEP, LINK_CONST>(b, total, s);
 }
 
 int fused_chunk(int dims, const int N[3]) {
