@@ -479,9 +479,12 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
   return DIRAC_OK;
 }
 
+static void drop_batch_graphs(const dirac_sim* s);
+
 extern "C" void dirac_destroy(dirac_sim* s) {
   if (!s) return;
   cudaStreamSynchronize(s->stream);
+  drop_batch_graphs(s);
   for (int k = 0; k < 2; ++k)
     if (s->graph[k]) cudaGraphExecDestroy(s->graph[k]);
   cudaFree(s->state);
@@ -739,6 +742,76 @@ static bool batchable(const dirac_sim* s) {
          (s->link_mode == LINK_NONE || s->link_mode == LINK_CONST);
 }
 
+// CUDA graphs of batched step loops, reused while the same group (same
+// simulations, buffer parities, plans, step count) is stepped again, as the
+// serving loop does quantum after quantum; each keeps its device argument
+// tables.  Entries that name a destroyed simulation are dropped by
+// dirac_destroy; at most kBatchGraphs are kept (least recently used go).
+struct BatchGraph {
+  std::vector<dirac_sim*> sims;
+  std::vector<void*> states;
+  std::vector<int> chunks;
+  long nsteps = 0;
+  int tb = 0;
+  void* tables = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t stream = nullptr;  // the group's stream, where the graph runs
+  unsigned long long used = 0;
+};
+static std::mutex g_bg_mu;
+static std::vector<BatchGraph> g_bgraphs;
+static unsigned long long g_bg_clock = 0;
+static const size_t kBatchGraphs = 8;
+static const long kBatchGraphMaxLaunches = 256;
+
+static void release_batch_graph(BatchGraph& e) {
+  if (e.exec) cudaGraphExecDestroy(e.exec);
+  if (e.tables) cudaFree(e.tables);
+  e.exec = nullptr;
+  e.tables = nullptr;
+}
+
+// called by dirac_destroy (the stream is synchronised, no graph of s runs)
+static void drop_batch_graphs(const dirac_sim* s) {
+  std::lock_guard<std::mutex> lock(g_bg_mu);
+  for (size_t i = 0; i < g_bgraphs.size();) {
+    bool has = false;
+    for (dirac_sim* t : g_bgraphs[i].sims) has = has || t == s;
+    if (has) {
+      release_batch_graph(g_bgraphs[i]);
+      g_bgraphs.erase(g_bgraphs.begin() + (long)i);
+    } else {
+      ++i;
+    }
+  }
+}
+
+// the launches of one batched call: pairs of steps (two-step kernel) first,
+// then single steps; every launch swaps the buffers
+static cudaError_t enqueue_batch(const FusedArgs<F32>* d_args, const long long* first, int n, long pairs,
+                                 long launches, long long total, long long total2, int dims, int coef,
+                                 int link, cudaStream_t st) {
+  BatchArgs<F32> b;
+  b.nsims = n;
+  b.workers = 0;
+  for (long i = 0; i < launches; ++i) {
+    b.sims = d_args + ((i < pairs ? 2 : 0) + (i & 1)) * n;
+    if (i < pairs) {
+      b.first_item = first + n + 1;
+      launch_fused2d_tb2_batch(b, total2, coef, link, st);
+    } else {
+      b.first_item = first;
+      if (dims == 3)
+        launch_fused_batch<F32, 3>(b, total, coef, link, st);
+      else
+        launch_fused_batch<F32, 2>(b, total, coef, link, st);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // one group: same dims and field path, all batchable
 static dirac_status batch_group(dirac_sim* const* g, int n, long nsteps) {
   dirac_sim* s0 = g[0];
@@ -746,26 +819,52 @@ static dirac_status batch_group(dirac_sim* const* g, int n, long nsteps) {
   // (2+1)D groups take two steps per pass for pairs of steps, as stepping alone
   bool tb = s0->dims == 2 && nsteps >= 2 && std::getenv("DIRAC_NO_TEMPORAL_BLOCKING") == nullptr;
   for (int i = 0; i < n && tb; ++i) tb = g[i]->tblock != 0;
-  // arguments [mode][buffer parity][sim]: mode 0 one step per pass, 1 two steps
-  const size_t args_bytes = (size_t)4 * n * sizeof(FusedArgs<F32>);
-  const size_t first_bytes = (size_t)2 * (n + 1) * sizeof(long long);  // one-step, two-step items
-  FusedArgs<F32>* h_args = new (std::nothrow) FusedArgs<F32>[4 * n];
-  long long* h_first = new (std::nothrow) long long[2 * (n + 1)];
-  if (!h_args || !h_first) {
-    delete[] h_args;
-    delete[] h_first;
-    return fail(s0, DIRAC_ERR_OOM, "host allocation failed");
-  }
-  h_first[0] = 0;
-  h_first[n + 1] = 0;
+  const long pairs = tb ? nsteps / 2 : 0;
+  const long launches = pairs + (nsteps - 2 * pairs);
+  std::vector<int> chunks(2 * n);
   for (int i = 0; i < n; ++i) {
     dirac_sim* s = g[i];
-    const int chunk = s->chunk1 > 0 ? s->chunk1 : fused_chunk(s->dims, s->N);
-    const int chunk2 = s->chunk2 > 0 ? s->chunk2 : (tb ? fused_chunk_tb2(s->N) : 0);
+    chunks[2 * i] = s->chunk1 > 0 ? s->chunk1 : fused_chunk(s->dims, s->N);
+    chunks[2 * i + 1] = s->chunk2 > 0 ? s->chunk2 : (tb ? fused_chunk_tb2(s->N) : 0);
+  }
+  const bool use_graph = launches <= kBatchGraphMaxLaunches && std::getenv("DIRAC_NO_GRAPHS") == nullptr;
+
+  auto finish = [&]() {
+    for (int i = 0; i < n; ++i) {
+      dirac_sim* s = g[i];
+      if (launches & 1) std::swap(s->state, s->state_alt);
+      s->k += nsteps;
+      s->stepped = 1;
+    }
+    g[0]->launches += launches;  // one launch per pass serves the whole group
+    return DIRAC_OK;
+  };
+
+  if (use_graph) {  // a recorded loop of this very call?
+    std::lock_guard<std::mutex> lock(g_bg_mu);
+    for (BatchGraph& e : g_bgraphs) {
+      if (e.nsteps != nsteps || e.tb != (int)tb || e.sims.size() != (size_t)n || e.chunks != chunks) continue;
+      bool same = true;
+      for (int i = 0; i < n && same; ++i) same = e.sims[i] == g[i] && e.states[i] == g[i]->state;
+      if (!same) continue;
+      CK(s0, cudaGraphLaunch(e.exec, st));
+      e.used = ++g_bg_clock;
+      return finish();
+    }
+  }
+
+  // argument tables [mode][buffer parity][sim] (mode 0 one step per pass, 1
+  // two steps) and item prefix sums [mode][n + 1]
+  const size_t args_bytes = (size_t)4 * n * sizeof(FusedArgs<F32>);
+  const size_t first_bytes = (size_t)2 * (n + 1) * sizeof(long long);
+  std::vector<FusedArgs<F32>> h_args(4 * (size_t)n);
+  std::vector<long long> h_first(2 * (size_t)(n + 1), 0);
+  for (int i = 0; i < n; ++i) {
+    dirac_sim* s = g[i];
     for (int mode = 0; mode < 2; ++mode) {
       for (int p = 0; p < 2; ++p) {
         FusedArgs<F32> a = fused_args<F32>(s, sim_time(s));
-        a.chunk = mode ? chunk2 : chunk;
+        a.chunk = chunks[2 * i + mode];
         if (p == 1) {
           for (int k = 0; k < 8; ++k) {  // the other buffer is the input after an odd launch
             typename F32::cplx* tmp = a.out[k];
@@ -773,60 +872,79 @@ static dirac_status batch_group(dirac_sim* const* g, int n, long nsteps) {
             a.in[k] = tmp;
           }
         }
-        h_args[(mode * 2 + p) * n + i] = a;
+        h_args[(mode * 2 + p) * (size_t)n + i] = a;
       }
     }
-    h_first[i + 1] = h_first[i] + fused_items(s->dims, s->N, chunk);
-    h_first[n + 1 + i + 1] = h_first[n + 1 + i] + (tb ? fused_items_tb2(s->N, chunk2) : 0);
+    h_first[i + 1] = h_first[i] + fused_items(s->dims, s->N, chunks[2 * i]);
+    h_first[n + 1 + i + 1] = h_first[n + 1 + i] + (tb ? fused_items_tb2(s->N, chunks[2 * i + 1]) : 0);
   }
+  const long long total = h_first[n], total2 = h_first[2 * (size_t)n + 1];
   void* d = nullptr;
-  cudaError_t e = cudaMallocAsync(&d, args_bytes + first_bytes, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d, h_args, args_bytes, cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaMalloc(&d, args_bytes + first_bytes);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d, h_args.data(), args_bytes, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(static_cast<char*>(d) + args_bytes, h_first, first_bytes, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host tables can be freed
-  const long long total = h_first[n], total2 = h_first[2 * n + 1];
-  delete[] h_args;
-  delete[] h_first;
+    e = cudaMemcpyAsync(static_cast<char*>(d) + args_bytes, h_first.data(), first_bytes, cudaMemcpyHostToDevice,
+                        st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host tables go out of scope; graphs run later
   if (e != cudaSuccess) {
-    if (d) cudaFreeAsync(d, st);
+    if (d) cudaFree(d);
     return cuda_fail(s0, e, "batch tables");
   }
   const FusedArgs<F32>* d_args = static_cast<const FusedArgs<F32>*>(d);
-  BatchArgs<F32> b;
-  const long long* first = reinterpret_cast<const long long*>(static_cast<char*>(d) + args_bytes);
-  b.nsims = n;
-  b.workers = 0;
-  // every launch swaps the buffers: pairs of steps first, then a single step
-  const long pairs = tb ? nsteps / 2 : 0;
-  const long launches = pairs + (nsteps - 2 * pairs);
-  for (long i = 0; i < launches; ++i) {
-    b.sims = d_args + ((i < pairs ? 2 : 0) + (i & 1)) * n;
-    if (i < pairs) {
-      b.first_item = first + n + 1;
-      launch_fused2d_tb2_batch(b, total2, s0->coef_mode, s0->link_mode, st);
-    } else {
-      b.first_item = first;
-      if (s0->dims == 3)
-        launch_fused_batch<F32, 3>(b, total, s0->coef_mode, s0->link_mode, st);
-      else
-        launch_fused_batch<F32, 2>(b, total, s0->coef_mode, s0->link_mode, st);
+  const long long* d_first = reinterpret_cast<const long long*>(static_cast<char*>(d) + args_bytes);
+
+  if (use_graph) {  // record the loop on a private stream, keep it with its tables
+    cudaStream_t cap;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool ok = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) {
+      ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+      cudaError_t le = ok ? enqueue_batch(d_args, d_first, n, pairs, launches, total, total2, s0->dims,
+                                          s0->coef_mode, s0->link_mode, cap)
+                          : cudaSuccess;
+      if (ok) ok = cudaStreamEndCapture(cap, &graph) == cudaSuccess && le == cudaSuccess && graph;
+      if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+      if (graph) cudaGraphDestroy(graph);
+      cudaStreamDestroy(cap);
     }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) {
-      cudaFreeAsync(d, st);
-      return cuda_fail(s0, e, "batched fused launch");
+    cudaGetLastError();  // a failed capture falls back to direct launches
+    if (ok && exec) {
+      e = cudaGraphLaunch(exec, st);
+      if (e != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        cudaFree(d);
+        return cuda_fail(s0, e, "batched graph launch");
+      }
+      BatchGraph ent;
+      ent.sims.assign(g, g + n);
+      for (int i = 0; i < n; ++i) ent.states.push_back(g[i]->state);
+      ent.chunks = chunks;
+      ent.nsteps = nsteps;
+      ent.tb = (int)tb;
+      ent.tables = d;
+      ent.exec = exec;
+      ent.stream = st;
+      std::lock_guard<std::mutex> lock(g_bg_mu);
+      ent.used = ++g_bg_clock;
+      if (g_bgraphs.size() >= kBatchGraphs) {  // evict the least recently used
+        size_t lru = 0;
+        for (size_t i = 1; i < g_bgraphs.size(); ++i)
+          if (g_bgraphs[i].used < g_bgraphs[lru].used) lru = i;
+        cudaStreamSynchronize(g_bgraphs[lru].stream);  // it may still run there
+        release_batch_graph(g_bgraphs[lru]);
+        g_bgraphs.erase(g_bgraphs.begin() + (long)lru);
+      }
+      g_bgraphs.push_back(ent);
+      return finish();
     }
   }
-  cudaFreeAsync(d, st);
-  for (int i = 0; i < n; ++i) {
-    dirac_sim* s = g[i];
-    if (launches & 1) std::swap(s->state, s->state_alt);
-    s->k += nsteps;
-    s->stepped = 1;
-  }
-  g[0]->launches += launches;  // one launch per pass serves the whole group
-  return DIRAC_OK;
+  e = enqueue_batch(d_args, d_first, n, pairs, launches, total, total2, s0->dims, s0->coef_mode,
+                    s0->link_mode, st);
+  cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(s0, e, "batched fused launch");
+  return finish();
 }
 
 static dirac_status batch_step_impl(dirac_sim* const* sims, int nsims, long nsteps);

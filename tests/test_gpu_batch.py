@@ -99,3 +99,52 @@ def test_serving_loop_small_stream(D):
     assert out["p99_s"] >= out["p50_s"] > 0.0
     for r in out["results"]:
         assert r.finished >= r.admitted >= r.arrival - 1e-9
+
+
+def test_batch_graph_replay_and_membership_changes(D, monkeypatch):
+    """Batched step loops are recorded as CUDA graphs and replayed while the
+    group repeats (the serving loop's quanta); replays, odd and even step
+    counts, a member leaving (destroyed) and one joining must all give the
+    states of stepping alone, bit for bit, as with graphs switched off."""
+    probs = [p for p, prec in mix() if prec == 0][:6]
+    states = [W.random_state(p, 200 + i) for i, p in enumerate(probs)]
+    plan = [(list(range(6)), 10), (list(range(6)), 10), (list(range(6)), 7), (list(range(6)), 10),
+            ([0, 2, 3, 4, 5], 10), ([0, 2, 3, 4, 5], 10), ([0, 2, 3, 4, 5, 1], 6)]
+
+    def run(graphs):
+        if not graphs:
+            monkeypatch.setenv("DIRAC_NO_GRAPHS", "1")
+        sims = []
+        for p, psi in zip(probs, states):
+            s = D.Sim(p, D.FP32)
+            s.set_spinor(psi)
+            sims.append(s)
+        out = {}
+        try:
+            for members, n in plan:
+                if members == [0, 2, 3, 4, 5] and sims[1] is not None and 1 not in out:
+                    out[1] = sims[1].get_spinor()  # member 1 leaves: destroyed, then re-created
+                    sims[1].close()
+                    sims[1] = None
+                if 1 in members and sims[1] is None:
+                    sims[1] = D.Sim(probs[1], D.FP32)
+                    sims[1].set_spinor(out[1])
+                D.batch_step([sims[i] for i in members], n)
+            res = [s.get_spinor() for s in sims]
+        finally:
+            for s in sims:
+                if s is not None:
+                    s.close()
+            monkeypatch.delenv("DIRAC_NO_GRAPHS", raising=False)
+        return res
+
+    with_graphs, without = run(True), run(False)
+    for a, b in zip(with_graphs, without):
+        assert np.array_equal(a, b)
+    # and against stepping each simulation alone for the same number of steps
+    total = [sum(n for members, n in plan if i in members) for i in range(6)]
+    for i, (p, psi) in enumerate(zip(probs, states)):
+        with D.Sim(p, D.FP32) as s:
+            s.set_spinor(psi)
+            s.step(total[i])
+            assert np.array_equal(s.get_spinor(), with_graphs[i])
