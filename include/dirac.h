@@ -171,14 +171,19 @@ dirac_status dirac_step(dirac_sim* sim, long nsteps);
  * simulations with time-independent fields (no modulated static potential,
  * no moving plane wave; a static soft core or static array is not batched
  * either) that share dims and field path run as ONE persistent launch of the
- * fused kernel per time step: the work items of all of them (tile x level
+ * fused kernel per time step ((2+1)D: per two time steps, with a single-step
+ * pass for an odd remainder): the work items of all of them (tile x level
  * chunk) are dealt to the resident blocks together, so small grids fill the
  * GPU jointly.  Other simulations are stepped one after another as by
  * dirac_step.  The result of every simulation is identical, bit for bit, to
  * stepping it alone.  All simulations must have been created with the same
  * stream (else DIRAC_ERR_INVALID).  The call enqueues the work; its small
- * argument tables are copied synchronously before it returns.  On failure
- * dirac_last_error(NULL) describes the cause.
+ * argument tables are copied synchronously before it returns.  Loops of up
+ * to 256 launches are recorded as a CUDA graph, kept with their argument
+ * tables (at most eight, least recently used evicted) and replayed when the
+ * same simulations, in the same buffer state, with the same plans and step
+ * count come back; dirac_destroy forgets the loops that name a simulation.
+ * On failure dirac_last_error(NULL) describes the cause.
  */
 dirac_status dirac_batch_step(dirac_sim* const* sims, int nsims, long nsteps);
 
