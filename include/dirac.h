@@ -69,8 +69,8 @@ typedef enum {
   DIRAC_ERR_DIVERGED = 5,    /* the functional became non-finite (dirac_norm) or a
                                 stability check failed (dirac_check) */
   DIRAC_ERR_TIMEOUT = 6,     /* reserved for bounded device waits (no kernel of this
-                                build waits on another, so none is returned) */
-  DIRAC_ERR_UNSUPPORTED = 7  /* valid request this build does not implement */
+                                library waits on another, so none is returned) */
+  DIRAC_ERR_UNSUPPORTED = 7  /* valid request this library does not implement */
 } dirac_status;
 
 typedef enum {

@@ -3,7 +3,7 @@
 Usage: python -m paper_1309_3452_gb300.build [--force]
 Each .cu file compiles to an object in parallel, then one shared library is
 linked next to this file.  The CUDA runtime is linked statically, so loading
-the library needs no GPU (the driver is only touched at the first CUDA call).
+the library needs no GPU (the CUDA driver is only touched at the first CUDA call).
 """
 from __future__ import annotations
 
