@@ -320,8 +320,8 @@ double dirac_algorithmic_bytes(const dirac_sim* sim);
    reduction scratch. */
 size_t dirac_state_bytes(int dims, const int N[3], dirac_precision precision);
 
-/* human-readable description of the last failure on sim (or of the last
-   failed dirac_create when sim is NULL) */
+/* human-readable description of the last failure on sim (or, when sim is
+   NULL, of the calling thread's last failed dirac_create / dirac_batch_step) */
 const char* dirac_last_error(const dirac_sim* sim);
 
 /* free all device memory of sim (NULL is ignored); synchronises its stream */

@@ -65,7 +65,7 @@ struct dirac_sim {
 
 static const long kGraphSteps = 64;
 
-static std::string g_create_error;
+static thread_local std::string g_create_error;  // per host thread: concurrent creations do not mix messages
 
 static dirac_status fail(dirac_sim* s, dirac_status st, const std::string& msg) {
   if (s) s->err = msg; else g_create_error = msg;
