@@ -413,3 +413,35 @@ def test_algorithmic_bytes_per_path(D):
     for prob, prec, want in cases:
         with D.Sim(prob, prec) as s:
             assert s.algorithmic_bytes == want, (prob.fields, prec)
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_degenerate_inputs(D, dims, precision):
+    """Empty and degenerate work: zero steps change nothing, an empty batch is
+    a no-op, the zero state stays zero with E = 0 and passes the stability
+    check, and the smallest grid (two cells per axis) matches the oracle."""
+    prec = D.FP64 if precision == "fp64" else D.FP32
+    tol = FP64_TOL if precision == "fp64" else FP32_TOL
+    N = (2, 2, 1) if dims == 2 else (2, 2, 2)
+    prob = W.Problem(dims, N, (1.0, 1.0, 1.0), 0.9 * W.stability_limit(dims), 0.6,
+                     W.Fields(step_axis=0, step_x0=1.25, step_V=0.4))
+    psi = W.random_state(prob, 31)
+    with D.Sim(prob, prec) as s:
+        s.set_spinor(psi)
+        t0, launches = s.time, s.launches
+        s.step(0)
+        D.batch_step([s], 0)
+        D.batch_step([], 5)
+        assert s.time == t0 and s.launches == launches
+        back = s.get_spinor()
+        assert rel(back, psi) < (1e-15 if precision == "fp64" else 1e-7)
+        s.step(25)
+        assert rel(s.get_spinor(), O.step(prob, psi, 25)) < tol
+    with D.Sim(W.Problem(dims, (9, 7, 5) if dims == 3 else (9, 7, 1), (1.0, 1.0, 1.0), 0.5, 0.3), prec) as z:
+        z.set_spinor(np.zeros(z.prob.shape, complex))
+        z.step(12)
+        E, naive = z.norm()
+        ok, r = z.check(1e-6)
+        assert E == 0.0 and naive == 0.0 and ok and r["failed"] == 0
+        assert not np.any(z.get_spinor())
