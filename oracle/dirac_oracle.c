@@ -41,6 +41,7 @@ typedef struct {
   int dims;
   long M[3];  /* half-lattice extent per axis: 2 N_a (1 for an absent z axis) */
   long n;     /* number of half-lattice points */
+  double* link[3];  /* A_links on the half lattice: link[a][f] belongs to the link f -> f + e_a */
 } grid;
 
 static grid make_grid(const oracle_problem* p) {
@@ -50,6 +51,7 @@ static grid make_grid(const oracle_problem* p) {
   g.M[1] = 2L * p->N[1];
   g.M[2] = (p->dims == 3) ? 2L * p->N[2] : 1;
   g.n = g.M[0] * g.M[1] * g.M[2];
+  g.link[0] = g.link[1] = g.link[2] = NULL;
   return g;
 }
 
@@ -138,6 +140,17 @@ static double* real_planes_to_fine(const oracle_problem* p, const grid* g, const
   return fine;
 }
 
+/* A_links (one real per value and axis, canonical layout) -> g->link */
+static void links_to_fine(const oracle_problem* p, grid* g) {
+  if (!p->A_links) return;
+  long per_axis = (long)n_planes(p) * cells(p);
+  for (int a = 0; a < p->dims; ++a) g->link[a] = real_planes_to_fine(p, g, p->A_links + a * per_axis);
+}
+
+static void free_links(grid* g) {
+  for (int a = 0; a < 3; ++a) free(g->link[a]);
+}
+
 /* physical position of a half-lattice point */
 static void position(const oracle_problem* p, long X, long Y, long Z, double x[3]) {
   long F[3] = {X, Y, Z};
@@ -182,7 +195,8 @@ static cplx potential(const oracle_problem* p, const double* V_fine, long f, con
 }
 
 static int has_vector_potential(const oracle_problem* p) {
-  return p->A_const[0] != 0.0 || p->A_const[1] != 0.0 || p->A_const[2] != 0.0 || p->Apw_amp != 0.0;
+  return p->A_const[0] != 0.0 || p->A_const[1] != 0.0 || p->A_const[2] != 0.0 || p->Apw_amp != 0.0 ||
+         p->A_links != NULL;
 }
 
 /* Line integral of component a of the vector potential along the link of
@@ -233,6 +247,11 @@ static cplx stencil(const oracle_problem* p, const grid* g, const cplx* psi, lon
       ym[a] -= h / 2.0;
       double phi_p = p->q * vector_potential_integral(p, a, yp, h, t);
       double phi_m = p->q * vector_potential_integral(p, a, ym, h, t);
+      if (g->link[a]) {  /* own link upwards, the lower neighbour's link to this point */
+        double mod = 1.0 + p->Alink_amp * cos(p->Alink_omega * t);
+        phi_p += p->q * mod * g->link[a][fine_index(g, C[0], C[1], C[2])];
+        phi_m += p->q * mod * g->link[a][fine_index(g, Cm[0], Cm[1], Cm[2])];
+      }
       up = up * cexp(-I * phi_p);
       dn = dn * cexp(I * phi_m);
     }
@@ -267,6 +286,7 @@ void oracle_step(const oracle_problem* p, double* planes, double t0, long nsteps
   grid g = make_grid(p);
   cplx* psi = (cplx*)malloc((size_t)g.n * sizeof(cplx));
   double* V_fine = real_planes_to_fine(p, &g, p->V_site);
+  links_to_fine(p, &g);
   planes_to_fine(p, &g, planes, psi);
   double t = t0;
   for (long s = 0; s < nsteps; ++s) {
@@ -276,6 +296,7 @@ void oracle_step(const oracle_problem* p, double* planes, double t0, long nsteps
   }
   fine_to_planes(p, &g, psi, planes);
   free(V_fine);
+  free_links(&g);
   free(psi);
 }
 
@@ -298,6 +319,7 @@ void oracle_step(const oracle_problem* p, double* planes, double t0, long nsteps
 void oracle_observables(const oracle_problem* p, const double* planes, double t, double out[3]) {
   grid g = make_grid(p);
   cplx* psi = (cplx*)malloc((size_t)g.n * sizeof(cplx));
+  links_to_fine(p, &g);
   planes_to_fine(p, &g, planes, psi);
   double naive = 0.0, cross_lower = 0.0, cross_upper = 0.0;
 #pragma omp parallel for schedule(static) reduction(+ : naive, cross_lower, cross_upper)
@@ -319,6 +341,7 @@ void oracle_observables(const oracle_problem* p, const double* planes, double t,
   out[0] = naive + cross_lower;
   out[1] = naive - cross_upper;
   out[2] = naive;
+  free_links(&g);
   free(psi);
 }
 

@@ -67,6 +67,14 @@ typedef struct {
   double V0_imag;
   double abs_W, abs_width;
   int abs_axes;
+  /* an arbitrary vector potential given by its line integrals (Sect. 4):
+     A_links[a * P * cells + plane * cells + cell] is the integral of A_a
+     along the link from that value's point to its neighbour at +dx_a/2
+     (P planes, canonical layout, a < dims), at time t scaled by
+     1 + Alink_amp cos(Alink_omega t); added to the analytic A above; NULL:
+     none */
+  const double* A_links;
+  double Alink_amp, Alink_omega;
 } oracle_problem;
 
 /* Advance the state in place by nsteps full time steps.  `planes` is the

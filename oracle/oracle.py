@@ -55,6 +55,7 @@ class _Problem(C.Structure):
         ("Apw_amp", C.c_double), ("Apw_k", C.c_double * 3), ("Apw_omega", C.c_double),
         ("Apw_phase", C.c_double), ("Apw_pol", C.c_int), ("origin", C.c_int * 3),
         ("V0_imag", C.c_double), ("abs_W", C.c_double), ("abs_width", C.c_double), ("abs_axes", C.c_int),
+        ("A_links", C.POINTER(C.c_double)), ("Alink_amp", C.c_double), ("Alink_omega", C.c_double),
     ]
 
 
@@ -98,6 +99,11 @@ def _problem(prob, origin=(0, 0, 0)):
     p.abs_W, p.abs_width, p.abs_axes = float(f.abs_W), float(f.abs_width), int(f.abs_axes)
     if p.abs_W != 0.0 and any(origin):
         raise ValueError("absorbing layers refer to the grid's own box: no window origin")
+    if f.A_links is not None:
+        links = np.ascontiguousarray(f.A_links, dtype=np.float64).reshape((prob.dims,) + tuple(prob.shape))
+        p.A_links = links.ctypes.data_as(C.POINTER(C.c_double))
+        keep = (keep, links)
+    p.Alink_amp, p.Alink_omega = float(f.Alink_amp), float(f.Alink_omega)
     return p, keep
 
 

@@ -74,6 +74,13 @@ class Fields:
     abs_W: float = 0.0
     abs_width: float = 0.0
     abs_axes: int = 0
+    # an arbitrary vector potential by its line integrals (Sect. 4): shape
+    # (dims, P, Nz, Ny, Nx), entry [a, plane, cell] = integral of A_a along the
+    # link from that value's point to its neighbour at +dx_a/2, scaled at time
+    # t by 1 + Alink_amp cos(Alink_omega t); None: none
+    A_links: Optional[np.ndarray] = None
+    Alink_amp: float = 0.0
+    Alink_omega: float = 0.0
 
 
 @dataclass

@@ -559,3 +559,104 @@ def test_klein_step_negative_refraction():
     cos_t = kt @ v["T"] / (np.linalg.norm(kt) * np.linalg.norm(v["T"]))
     cos_r = kr @ v["R"] / (np.linalg.norm(kr) * np.linalg.norm(v["R"]))
     assert cos_t < -0.9 and cos_r > 0.9
+
+
+# ---------------------------------------------------------------- arbitrary vector potentials (Sect. 4)
+def fine_positions(prob, pl):
+    """Half-lattice integer coordinates (X, Y, Z) of every value of a plane."""
+    xyz = W.site_positions(prob, pl)
+    out = []
+    for a in range(3):
+        if a < prob.dims:
+            out.append(np.rint(2 * np.broadcast_to(xyz[a], prob.shape[1:]) / prob.dx[a]).astype(int))
+        else:
+            out.append(np.zeros(prob.shape[1:], int))
+    return out
+
+
+def links_from_fine(prob, fine_fn):
+    """A_links array (dims, P, Nz, Ny, Nx) from a function of the two
+    half-lattice end points of each link (start, end)."""
+    M = [2 * prob.N[a] if a < prob.dims else 1 for a in range(3)]
+    L = np.zeros((prob.dims,) + tuple(prob.shape))
+    for pl in range(prob.n_planes):
+        X = fine_positions(prob, pl)
+        for a in range(prob.dims):
+            E = [c.copy() for c in X]
+            E[a] = (E[a] + 1) % M[a]
+            L[a, pl] = fine_fn(a, X, E)
+    return L
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_gauge_covariance_arbitrary_lattice_gauge(dims):
+    """Sect. 4: phases given as line integrals on every link.  For the pure
+    gauge of an arbitrary (random) lattice function chi, link (F -> F + e_a)
+    carrying chi(F + e_a) - chi(F), the evolution is exactly covariant:
+    psi_A(t) = exp(i q chi) psi_0(t), which checks every link's start and end."""
+    prob = prob2(N=(6, 5)) if dims == 2 else prob3(N=(4, 3, 5))
+    prob = prob.with_fields(V_static=W.random_potential(prob, 8, 0.4))
+    q = 0.9
+    M = [2 * prob.N[a] if a < dims else 1 for a in range(3)]
+    chi = np.random.default_rng(12).uniform(-3.0, 3.0, size=(M[2], M[1], M[0]))
+    at = lambda P: chi[P[2], P[1], P[0]]
+    links = links_from_fine(prob, lambda a, S, E: at(E) - at(S))
+    gauge = np.zeros(prob.shape, complex)
+    for pl in range(prob.n_planes):
+        gauge[pl] = np.exp(1j * q * at(fine_positions(prob, pl)))
+    psi0 = W.random_state(prob, 13)
+    out0 = O.step(prob, psi0, 25)
+    outA = O.step(prob.with_fields(q=q, A_links=links), gauge * psi0, 25)
+    assert np.max(np.abs(outA - gauge * out0)) < 1e-12
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_link_integrals_equal_the_analytic_plane_wave(dims):
+    """The array path and the analytic path are the same Peierls substitution:
+    line integrals of a plane wave (with a constant part and a time
+    modulation) tabulated per link reproduce the analytic fields."""
+    prob = prob2(N=(8, 6)) if dims == 2 else prob3(N=(4, 6, 5))
+    k = [2 * math.pi / (prob.N[a] * prob.dx[a]) * n for a, n in zip(range(dims), (1, 2, 1))] + [0.0] * (3 - dims)
+    A0, amp, om, pol = 0.3, 0.8, 0.45, 1
+    h = prob.dx[pol] / 2
+
+    def integral(a, S, E):  # a constant A0 along pol: every link carries A0 h
+        return np.full(S[0].shape, A0 * h if a == pol else 0.0)
+
+    links = links_from_fine(prob, integral)
+    f_arr = dict(q=1.0, A_links=links, Alink_amp=amp, Alink_omega=om)
+    # A_pol(t) = A0 (1 + amp cos(om t)): a constant plus a k = 0 wave of amplitude A0 amp
+    f_ana = dict(q=1.0, A_const=tuple(A0 if b == pol else 0.0 for b in range(3)), Apw_amp=A0 * amp,
+                 Apw_k=(0.0, 0.0, 0.0), Apw_omega=om, Apw_phase=0.0, Apw_pol=pol)
+    psi0 = W.random_state(prob, 14)
+    a = O.step(prob.with_fields(**f_arr), psi0, 30, 0.2)
+    b = O.step(prob.with_fields(**f_ana), psi0, 30, 0.2)
+    assert np.max(np.abs(a - b)) < 1e-12
+    # a static wave along k (analytic line integrals per link) against the analytic path
+    def wave(a_, S, E):
+        if a_ != pol:
+            return np.zeros(S[0].shape)
+        mid = [(S[b] + 0.5 * (b == a_)) * prob.dx[b] / 2 for b in range(3)]
+        ph = sum(k[b] * mid[b] for b in range(dims)) + 0.3
+        u = 0.5 * k[a_] * h
+        return amp * h * np.cos(ph) * (np.sin(u) / u if u != 0 else 1.0)
+    links = links_from_fine(prob, wave)
+    a = O.step(prob.with_fields(q=1.0, A_links=links), psi0, 30)
+    b = O.step(prob.with_fields(q=1.0, Apw_amp=amp, Apw_k=tuple(k), Apw_omega=0.0, Apw_phase=0.3, Apw_pol=pol),
+               psi0, 30)
+    assert np.max(np.abs(a - b)) < 1e-12
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_conservation_arbitrary_static_links(dims):
+    """Lemma of Sect. 2 / Sect. 3 with an arbitrary static vector potential
+    (random link integrals, not a pure gauge) and a random V: E is conserved
+    exactly."""
+    prob = prob2(N=(6, 5)) if dims == 2 else prob3(N=(4, 3, 5))
+    prob = prob.with_fields(V_static=W.random_potential(prob, 9, 0.5))
+    links = np.random.default_rng(15).uniform(-1.0, 1.0, size=(dims,) + tuple(prob.shape))
+    prob = prob.with_fields(q=0.7, A_links=links)
+    psi0 = W.random_state(prob, 16)
+    d, e0, e1, psi = rel_drift(prob, psi0, 40)
+    assert abs(d) < 1e-13
+    assert abs(e1["naive"] - e0["naive"]) > 1e-6 * e0["naive"]  # a real field: the naive norm moves
