@@ -235,6 +235,50 @@ def random_potential(prob: Problem, seed: int, amplitude: float) -> np.ndarray:
     return amplitude * (2.0 * rng.random(prob.shape) - 1.0)
 
 
+def half_lattice_points(prob: Problem, plane: int):
+    """Integer half-lattice coordinates (X, Y, Z) (units of dx/2) of every
+    value of a plane, each an int array of shape (Nz, Ny, Nx); Z = 0 in
+    (2+1)D."""
+    _, offs, _, _ = plane_tables(prob.dims)
+    o = offs[plane]
+    nz = prob.N[2] if prob.dims == 3 else 1
+    jz, jy, jx = np.meshgrid(np.arange(nz), np.arange(prob.N[1]), np.arange(prob.N[0]), indexing="ij")
+    Z = 2 * jz + o[2] if prob.dims == 3 else np.zeros_like(jx)
+    return 2 * jx + o[0], 2 * jy + o[1], Z
+
+
+def link_integrals(prob: Problem, fn) -> np.ndarray:
+    """An A_links array (dims, P, Nz, Ny, Nx) from fn(a, S, E) -> array: the
+    value for the link along axis a from the half-lattice points S to E = S +
+    e_a (coordinate tuples as from half_lattice_points; E wraps at the far
+    face)."""
+    M = [2 * prob.N[a] if a < prob.dims else 1 for a in range(3)]
+    out = np.zeros((prob.dims,) + tuple(prob.shape))
+    for pl in range(prob.n_planes):
+        S = half_lattice_points(prob, pl)
+        for a in range(prob.dims):
+            E = list(S)
+            E[a] = (S[a] + 1) % M[a]
+            out[a, pl] = fn(a, S, tuple(E))
+    return out
+
+
+def random_links(prob: Problem, seed: int, amplitude: float) -> np.ndarray:
+    """Link integrals of an arbitrary (not pure gauge) static vector
+    potential, uniform in [-a, a] per link."""
+    rng = np.random.default_rng(seed)
+    return amplitude * (2.0 * rng.random((prob.dims,) + tuple(prob.shape)) - 1.0)
+
+
+def random_lattice_gauge(prob: Problem, seed: int, amplitude: float) -> np.ndarray:
+    """A random real function chi on the half lattice, shape (2Nz or 1, 2Ny,
+    2Nx), uniform in [-a, a]; its lattice gradient chi(E) - chi(S) is a pure
+    gauge."""
+    M = [2 * prob.N[a] if a < prob.dims else 1 for a in range(3)]
+    rng = np.random.default_rng(seed)
+    return amplitude * (2.0 * rng.random((M[2], M[1], M[0])) - 1.0)
+
+
 def delta_state(prob: Problem, plane: int, cell: Sequence[int]) -> np.ndarray:
     """A single unit value at one site."""
     out = np.zeros(prob.shape, np.complex128)

@@ -42,6 +42,11 @@ MUTATIONS = [
      "phi_m += p->q * mod * g->link[a][fine_index(g, C[0], C[1], C[2])];"),
     ("sign of the cross term of the functional", "out[0] = naive + cross_lower;",
      "out[0] = naive - cross_lower;"),
+    ("modulated potential taken half a step late",
+     "if (V_fine) V += V_fine[f] * (1.0 + p->Vmod_amp * cos(p->Vmod_omega * t));",
+     "if (V_fine) V += V_fine[f] * (1.0 + p->Vmod_amp * cos(p->Vmod_omega * (t + p->dt / 2)));"),
+    ("link integrals not modulated in time", "double mod = 1.0 + p->Alink_amp * cos(p->Alink_omega * t);",
+     "double mod = 1.0 + p->Alink_amp;"),
 ]
 
 

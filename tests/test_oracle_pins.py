@@ -360,6 +360,42 @@ def test_uniform_time_dependent_vector_potential_2d():
     assert np.max(np.abs(out - ref)) < 1e-12
 
 
+def test_uniform_time_dependent_scalar_potential_2d():
+    """Eqs. ss1-ss4 with a spatially uniform V(t) (a constant static array
+    modulated by 1 + a cos(w t)): a lattice plane wave stays a plane wave
+    and each half-step is a 2x2 Cayley map of its two amplitudes, with
+    theta = dt (m + V(t))/2 on the upper half-step and dt (V(t + dt/2) - m)/2
+    on the lower one (each at its own sheet's midpoint time).  The oracle must
+    agree with this per-mode recursion."""
+    N = (8, 6)
+    dt = 0.9 * W.stability_limit(2)
+    V1, amp, om, m = 0.35, 0.7, 0.5, 0.3
+    prob = W.Problem(2, (N[0], N[1], 1), (1.0, 1.0, 1.0), dt, m)
+    prob = prob.with_fields(V0=-0.1, V_static=np.full(prob.shape, V1), Vmod_amp=amp, Vmod_omega=om)
+    k = (2 * math.pi * 3 / N[0], 2 * math.pi * -1 / N[1])
+    u, v = 0.2 - 0.5j, 0.8 + 0.1j
+    psi0 = np.zeros(prob.shape, complex)
+    for pl in range(4):
+        xyz = W.site_positions(prob, pl)
+        psi0[pl] = (u if pl < 2 else v) * np.exp(1j * (k[0] * xyz[0] + k[1] * xyz[1]))
+    Px, Py = 2 * math.sin(k[0] / 2), 2 * math.sin(k[1] / 2)
+    V = lambda t: -0.1 + V1 * (1 + amp * math.cos(om * t))
+    n, t0 = 40, 0.35
+    t = t0
+    for _ in range(n):
+        th = dt * (m + V(t)) / 2
+        u = ((1 - 1j * th) * u - dt * 1j * (Px - 1j * Py) * v) / (1 + 1j * th)
+        th = dt * (V(t + dt / 2) - m) / 2
+        v = ((1 - 1j * th) * v - dt * 1j * (Px + 1j * Py) * u) / (1 + 1j * th)
+        t += dt
+    out = O.step(prob, psi0, n, t0)
+    ref = np.zeros(prob.shape, complex)
+    for pl in range(4):
+        xyz = W.site_positions(prob, pl)
+        ref[pl] = (u if pl < 2 else v) * np.exp(1j * (k[0] * xyz[0] + k[1] * xyz[1]))
+    assert np.max(np.abs(out - ref)) < 1e-12
+
+
 # ---------------------------------------------------------------- T10
 def test_proposition_2_bound():
     """Prop. 2: for r_x + r_y + r_z < 1 the naive norm stays below
@@ -562,32 +598,6 @@ def test_klein_step_negative_refraction():
 
 
 # ---------------------------------------------------------------- arbitrary vector potentials (Sect. 4)
-def fine_positions(prob, pl):
-    """Half-lattice integer coordinates (X, Y, Z) of every value of a plane."""
-    xyz = W.site_positions(prob, pl)
-    out = []
-    for a in range(3):
-        if a < prob.dims:
-            out.append(np.rint(2 * np.broadcast_to(xyz[a], prob.shape[1:]) / prob.dx[a]).astype(int))
-        else:
-            out.append(np.zeros(prob.shape[1:], int))
-    return out
-
-
-def links_from_fine(prob, fine_fn):
-    """A_links array (dims, P, Nz, Ny, Nx) from a function of the two
-    half-lattice end points of each link (start, end)."""
-    M = [2 * prob.N[a] if a < prob.dims else 1 for a in range(3)]
-    L = np.zeros((prob.dims,) + tuple(prob.shape))
-    for pl in range(prob.n_planes):
-        X = fine_positions(prob, pl)
-        for a in range(prob.dims):
-            E = [c.copy() for c in X]
-            E[a] = (E[a] + 1) % M[a]
-            L[a, pl] = fine_fn(a, X, E)
-    return L
-
-
 @pytest.mark.parametrize("dims", [2, 3])
 def test_gauge_covariance_arbitrary_lattice_gauge(dims):
     """Sect. 4: phases given as line integrals on every link.  For the pure
@@ -597,13 +607,12 @@ def test_gauge_covariance_arbitrary_lattice_gauge(dims):
     prob = prob2(N=(6, 5)) if dims == 2 else prob3(N=(4, 3, 5))
     prob = prob.with_fields(V_static=W.random_potential(prob, 8, 0.4))
     q = 0.9
-    M = [2 * prob.N[a] if a < dims else 1 for a in range(3)]
-    chi = np.random.default_rng(12).uniform(-3.0, 3.0, size=(M[2], M[1], M[0]))
+    chi = W.random_lattice_gauge(prob, 12, 3.0)
     at = lambda P: chi[P[2], P[1], P[0]]
-    links = links_from_fine(prob, lambda a, S, E: at(E) - at(S))
+    links = W.link_integrals(prob, lambda a, S, E: at(E) - at(S))
     gauge = np.zeros(prob.shape, complex)
     for pl in range(prob.n_planes):
-        gauge[pl] = np.exp(1j * q * at(fine_positions(prob, pl)))
+        gauge[pl] = np.exp(1j * q * at(W.half_lattice_points(prob, pl)))
     psi0 = W.random_state(prob, 13)
     out0 = O.step(prob, psi0, 25)
     outA = O.step(prob.with_fields(q=q, A_links=links), gauge * psi0, 25)
@@ -623,7 +632,7 @@ def test_link_integrals_equal_the_analytic_plane_wave(dims):
     def integral(a, S, E):  # a constant A0 along pol: every link carries A0 h
         return np.full(S[0].shape, A0 * h if a == pol else 0.0)
 
-    links = links_from_fine(prob, integral)
+    links = W.link_integrals(prob, integral)
     f_arr = dict(q=1.0, A_links=links, Alink_amp=amp, Alink_omega=om)
     # A_pol(t) = A0 (1 + amp cos(om t)): a constant plus a k = 0 wave of amplitude A0 amp
     f_ana = dict(q=1.0, A_const=tuple(A0 if b == pol else 0.0 for b in range(3)), Apw_amp=A0 * amp,
@@ -640,7 +649,7 @@ def test_link_integrals_equal_the_analytic_plane_wave(dims):
         ph = sum(k[b] * mid[b] for b in range(dims)) + 0.3
         u = 0.5 * k[a_] * h
         return amp * h * np.cos(ph) * (np.sin(u) / u if u != 0 else 1.0)
-    links = links_from_fine(prob, wave)
+    links = W.link_integrals(prob, wave)
     a = O.step(prob.with_fields(q=1.0, A_links=links), psi0, 30)
     b = O.step(prob.with_fields(q=1.0, Apw_amp=amp, Apw_k=tuple(k), Apw_omega=0.0, Apw_phase=0.3, Apw_pol=pol),
                psi0, 30)
@@ -654,8 +663,7 @@ def test_conservation_arbitrary_static_links(dims):
     exactly."""
     prob = prob2(N=(6, 5)) if dims == 2 else prob3(N=(4, 3, 5))
     prob = prob.with_fields(V_static=W.random_potential(prob, 9, 0.5))
-    links = np.random.default_rng(15).uniform(-1.0, 1.0, size=(dims,) + tuple(prob.shape))
-    prob = prob.with_fields(q=0.7, A_links=links)
+    prob = prob.with_fields(q=0.7, A_links=W.random_links(prob, 15, 1.0))
     psi0 = W.random_state(prob, 16)
     d, e0, e1, psi = rel_drift(prob, psi0, 40)
     assert abs(d) < 1e-13
