@@ -95,9 +95,19 @@ typedef enum {
  *          + V_static(x) * (1 + Vmod_amp * cos(Vmod_omega * t))
  * Vector potential, coupled with charge q through link factors:
  *   A(x,t) = A_const + e_{Apw_pol} * Apw_amp * cos(Apw_k . x - Apw_omega t + Apw_phase)
+ * plus, optionally, an arbitrary A given by its line integrals (Sect. 4: the
+ * Peierls phase of a link is q times the integral of A along it):
+ *   A_links[(a * P + plane) * cells + cell], a < dims, P planes, canonical
+ *   layout = integral of A_a along the link from that value's point x to
+ *   x + (dx_a/2) e_a (the value's neighbour on the partner plane; at the far
+ *   face the link wraps to the periodic image), multiplied at time t by
+ *   1 + Alink_amp * cos(Alink_omega * t).
  * A must be periodic on the box for the link factors at the wrap to be
- * consistent.  The upper half-step uses the fields at time t, the lower
- * half-step at t + dt/2 (the time sheets of Eqs. ss1-ss4).
+ * consistent.  A_links: NULL or a host array of dims * P * cells reals, copied
+ * during dirac_create; with it the link factors are evaluated per site in FP64
+ * (the general field path) and dirac_norm_noalloc is unavailable.  The upper
+ * half-step uses the fields at time t, the lower half-step at t + dt/2 (the
+ * time sheets of Eqs. ss1-ss4).
  * V_static: NULL, or a host array of one real per site (canonical layout);
  * it is copied during dirac_create.
  * Imaginary part of V (Sect. 3, growth factors: Im V < 0 damps, so layers of
@@ -123,10 +133,12 @@ typedef struct {
   double V0_imag;
   double abs_W, abs_width;
   int abs_axes;
+  const double* A_links;
+  double Alink_amp, Alink_omega;
 } dirac_fields;
 
 /* Zero fields: everything 0 except q = 1, step_axis = -1, sc_a = 1 (no
-   imaginary part, no layers). */
+   imaginary part, no layers, no link integrals). */
 void dirac_fields_default(dirac_fields* f);
 
 /*
@@ -307,8 +319,9 @@ dirac_status dirac_check(dirac_sim* sim, double tol, dirac_check_report* out);
 /* Algorithmic HBM bytes of one site update (one cell advanced one full time
    step) on this simulation's path: every value read and written once, plus
    a per-site coefficient (16 bytes) or static potential (8 bytes) read per
-   value where the potential needs one.  The roofline numerator of a time
-   step.  0 for NULL. */
+   value where the potential needs one, and with A_links two link integrals
+   (16 bytes) per axis and value.  The roofline numerator of a time step.  0
+   for NULL. */
 double dirac_algorithmic_bytes(const dirac_sim* sim);
 
 /* device bytes a simulation of this shape and precision allocates for a
@@ -316,8 +329,8 @@ double dirac_algorithmic_bytes(const dirac_sim* sim);
    DIRAC_FP32 a second state buffer and one complex128 conversion plane.
    Other potentials add one double per value (DIRAC_FP64, or a time-
    dependent static array) or the coefficient table, 16 bytes per value
-   (DIRAC_FP32, time-independent), and every simulation a few KiB of
-   reduction scratch. */
+   (DIRAC_FP32, time-independent), A_links 16 bytes per axis and value, and
+   every simulation a few KiB of reduction scratch. */
 size_t dirac_state_bytes(int dims, const int N[3], dirac_precision precision);
 
 /* human-readable description of the last failure on sim (or, when sim is
@@ -350,7 +363,8 @@ void dirac_destroy(dirac_sim* sim);
  *   device memory (8193 x 5 doubles, about 320 KiB, held by every GPU that
  *   loads the library until the process exits).  Grids whose reduction needs
  *   more than 8192 blocks, i.e. ceil(N[0]/32) * ceil(N[1]/8) > 8192, are
- *   rejected with DIRAC_ERR_UNSUPPORTED before any device work.  Every call
+ *   rejected with DIRAC_ERR_UNSUPPORTED before any device work, and so are
+ *   fields with A_links (their device copy would be an allocation).  Every call
  *   shares that array and overwrites all of it that it reads, so nothing
  *   needs clearing between calls; calls that overlap on the GPU (other
  *   streams, or another host thread) race on it and must be serialised by

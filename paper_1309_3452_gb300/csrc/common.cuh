@@ -269,6 +269,13 @@ struct FieldDesc {
   double V0_imag, abs_W, abs_width;
   int abs_axes;
   double L[3];
+  // an arbitrary vector potential by its link integrals (Sect. 4): q times
+  // the integral of A_a along the up link (dir +1, slot 2a) and the down link
+  // (dir -1, slot 2a+1) of every value, at [slot * Alink_n + plane * Alink_ps
+  // + site]; scaled at time t by 1 + Alink_amp cos(Alink_omega t); NULL: none
+  const double* Alink;
+  long long Alink_n, Alink_ps;
+  double Alink_amp, Alink_omega;
 };
 
 // Compute alpha = (1 - i th)/(1 + i th) and gamma = r_x/(1 + i th) in FP64
@@ -338,6 +345,19 @@ __device__ __forceinline__ double link_phase(const FieldDesc& f, int dims, const
     I += f.Apw_amp * h * cos(ph) * (u == 0.0 ? 1.0 : sin(u) / u);
   }
   return f.q * I;
+}
+
+// the phase of a value's link: the analytic part above plus, if given, the
+// tabulated link integral of that value (plane, site)
+__device__ __forceinline__ double link_phase_site(const FieldDesc& f, int dims, const long long H[3], int axis,
+                                                  int dir, double t, int plane, long long site) {
+  double phi = link_phase(f, dims, H, axis, dir, t);
+  if (f.Alink) {
+    const double mod = 1.0 + f.Alink_amp * cos(f.Alink_omega * t);
+    const long long slot = 2 * axis + (dir > 0 ? 0 : 1);
+    phi += mod * f.Alink[slot * f.Alink_n + (long long)plane * f.Alink_ps + site];
+  }
+  return phi;
 }
 
 // ------------------------------------------------------------------ double-float
@@ -498,9 +518,9 @@ __device__ __forceinline__ typename P::cplx site_update(
       }
     } else if (LINK == kAnyMode && (link == LINK_GENERAL || link == LINK_PLANE)) {
       long long HH[3] = {H[0], H[1], H[2]};
-      up = link_mul(link_from(link_phase(f, DIMS, HH, ax, +1, h.t), (P*)nullptr), up);
+      up = link_mul(link_from(link_phase_site(f, DIMS, HH, ax, +1, h.t, plane, site), (P*)nullptr), up);
       // exp(+i phi-) = conj(exp(-i phi-))
-      dn = link_mulc(link_from(link_phase(f, DIMS, HH, ax, -1, h.t), (P*)nullptr), dn);
+      dn = link_mulc(link_from(link_phase_site(f, DIMS, HH, ax, -1, h.t, plane, site), (P*)nullptr), dn);
     }
     d[ax] = csub(up, dn);
   }

@@ -36,6 +36,7 @@ struct dirac_sim {
   double2* staging = nullptr; // one canonical plane (FP32 conversions)
   double* Vstatic = nullptr;  // one real per site (plane-major, pstride)
   float4* b_tab = nullptr;    // COEF_TABLE: b = 1/(1 + i theta) per site as hi + lo (plane-major, pstride)
+  double* Alink = nullptr;    // link integrals x q: 2 dims slots (up, down link per axis) of np * pstride
   double* partials = nullptr;
   double* sums_dev = nullptr;
   double* sums_host = nullptr; // pinned
@@ -194,6 +195,11 @@ static FieldDesc field_desc(const dirac_sim* s) {
   d.abs_width = s->f.abs_width;
   d.abs_axes = s->f.abs_axes;
   for (int a = 0; a < 3; ++a) d.L[a] = s->N[a] * s->dx[a];
+  d.Alink = s->Alink;
+  d.Alink_n = (long long)s->np * s->pstride;
+  d.Alink_ps = s->pstride;
+  d.Alink_amp = s->f.Alink_amp;
+  d.Alink_omega = s->f.Alink_omega;
   return d;
 }
 
@@ -365,6 +371,8 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
                 "absorbing layers need abs_width > 0 and abs_axes a non-empty mask of the dims axes");
   if (f.Apw_amp != 0.0 && (f.Apw_pol < 0 || f.Apw_pol >= dims))
     return fail(nullptr, DIRAC_ERR_INVALID, "Apw_pol must be a spatial axis");
+  if (f.A_links && (!std::isfinite(f.Alink_amp) || !std::isfinite(f.Alink_omega) || !std::isfinite(f.q)))
+    return fail(nullptr, DIRAC_ERR_INVALID, "Alink_amp, Alink_omega and q must be finite");
 
   dirac_sim* s = new (std::nothrow) dirac_sim();
   if (!s) return fail(nullptr, DIRAC_ERR_OOM, "host allocation failed");
@@ -379,6 +387,7 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
   s->flags = flags;
   s->f = f;
   s->f.V_static = nullptr;
+  s->f.A_links = nullptr;
   s->stream = static_cast<cudaStream_t>(stream);
   s->ncell = cells_of(dims, s->N);
   s->pstride = round_up(s->ncell, 64);
@@ -395,8 +404,10 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
   else s->coef_mode = f.step_axis >= 0 ? COEF_STEP : COEF_UNIFORM;
   if (f.step_axis >= 0) s->step_X = threshold_index(f.step_x0, s->dx[f.step_axis]);
   bool any_A = f.A_const[0] != 0.0 || f.A_const[1] != 0.0 || f.A_const[2] != 0.0;
-  s->link_mode = f.Apw_amp != 0.0 ? LINK_GENERAL : (any_A ? LINK_CONST : LINK_NONE);
-  if (f.Apw_amp != 0.0) {
+  // link integrals of an arbitrary A: per-site FP64 phases (the general path)
+  const bool alinks = f.A_links != nullptr;
+  s->link_mode = (f.Apw_amp != 0.0 || alinks) ? LINK_GENERAL : (any_A ? LINK_CONST : LINK_NONE);
+  if (f.Apw_amp != 0.0 && !alinks) {
     // a plane wave along one axis other than its polarisation (and no constant
     // A across it) is tabulated per time step along that axis
     int along = -1, count = 0;
@@ -439,6 +450,26 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
                           (size_t)s->ncell * sizeof(double), cudaMemcpyHostToDevice, s->stream);
       if (e != cudaSuccess) return cleanup_fail(cuda_fail(s, e, "cudaMemcpyAsync(V)"));
     }
+  }
+  if (alinks) {
+    const size_t per_axis = (size_t)s->np * s->ncell;
+    const size_t tb = (size_t)2 * dims * s->np * s->pstride * sizeof(double);
+    if ((e = cudaMalloc(&s->Alink, tb)) != cudaSuccess)
+      return cleanup_fail(cuda_fail(s, e, "cudaMalloc(link integrals)"));
+    if ((e = cudaMemsetAsync(s->Alink, 0, tb, s->stream)) != cudaSuccess)
+      return cleanup_fail(cuda_fail(s, e, "cudaMemsetAsync(link integrals)"));
+    double* raw = nullptr;  // the caller's array, freed once the table is built
+    if ((e = cudaMalloc(&raw, dims * per_axis * sizeof(double))) != cudaSuccess)
+      return cleanup_fail(cuda_fail(s, e, "cudaMalloc(link integrals, upload)"));
+    e = cudaMemcpyAsync(raw, f.A_links, dims * per_axis * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) {
+      launch_link_integral_table(s->Alink, raw, dims, s->N, s->pstride, f.q, s->stream);
+      e = cudaGetLastError();
+      s->launches += 1;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaFree(raw);
+    if (e != cudaSuccess) return cleanup_fail(cuda_fail(s, e, "link integral table"));
   }
   if (s->coef_mode == COEF_TABLE) {
     if ((e = cudaMalloc(&s->b_tab, (size_t)s->np * s->pstride * sizeof(float4))) != cudaSuccess)
@@ -492,6 +523,7 @@ extern "C" void dirac_destroy(dirac_sim* s) {
   cudaFree(s->staging);
   cudaFree(s->Vstatic);
   cudaFree(s->b_tab);
+  cudaFree(s->Alink);
   cudaFree(s->ltab);
   cudaFree(s->e_partials);
   cudaFree(s->e_sums);
@@ -586,8 +618,12 @@ extern "C" dirac_status dirac_get_spinor_device(dirac_sim* s, void* dev) {
 }
 
 // n time steps with one launch sequence each, on stream st
+static bool moving_vector_potential(const dirac_sim* s) {
+  return (s->f.Apw_amp != 0.0 && s->f.Apw_omega != 0.0) ||
+         (s->Alink && s->f.Alink_amp != 0.0 && s->f.Alink_omega != 0.0);
+}
 static bool time_dependent_fields(const dirac_sim* s) {
-  return (s->Vstatic && s->f.Vmod_amp != 0.0) || (s->f.Apw_amp != 0.0 && s->f.Apw_omega != 0.0);
+  return (s->Vstatic && s->f.Vmod_amp != 0.0) || moving_vector_potential(s);
 }
 
 // LINK_PLANE: tabulate this step's link factors (both half-steps)
@@ -1248,7 +1284,7 @@ extern "C" dirac_status dirac_check(dirac_sim* s, double tol, dirac_check_report
     if (r.naive < r.lower - slack || r.naive > r.upper + slack) r.failed |= DIRAC_CHECK_BOUND;
   }
   // conservation (real V, static A) or no growth (Im V <= 0 everywhere)
-  const bool moving_A = s->f.Apw_amp != 0.0 && s->f.Apw_omega != 0.0;
+  const bool moving_A = moving_vector_potential(s);
   const bool imag = s->f.V0_imag != 0.0 || s->f.abs_W != 0.0;
   const bool damping = s->f.V0_imag <= 0.0 && s->f.abs_W >= 0.0;
   if (s->ref_valid && !moving_A && std::isfinite(r.drift)) {
@@ -1272,5 +1308,6 @@ extern "C" double dirac_algorithmic_bytes(const dirac_sim* s) {
   double b = 2.0 * s->np * (double)s->elem;                    // every value read and written once
   if (s->coef_mode == COEF_TABLE) b += 16.0 * s->np;           // one coefficient per value read
   if (s->coef_mode == COEF_GENERAL && s->Vstatic) b += 8.0 * s->np;  // one real per value read
+  if (s->Alink) b += 16.0 * s->dims * s->np;                   // its up and down link integral per axis
   return b;
 }

@@ -117,6 +117,13 @@ void launch_link_table(typename P::Link* tab, int n, const FieldDesc& f, int dim
 void launch_coef_table(float4* tab, const FieldDesc& f, int dims, const int N[3], long long pstride,
                        cudaStream_t s);
 
+// link integrals of an arbitrary vector potential (Sect. 4): raw = the
+// caller's integrals [axis][plane][cell] (canonical layout, cells dense), out
+// = q times them per value in the state layout, slot 2a = the value's up link
+// and 2a+1 = its down link: out[slot * P * pstride + plane * pstride + cell]
+void launch_link_integral_table(double* out, const double* raw, int dims, const int N[3], long long pstride,
+                                double q, cudaStream_t s);
+
 // canonical complex128 plane <-> device plane of the simulation precision
 void launch_convert_in(const double2* src, float2* dst, long long n, cudaStream_t s);
 void launch_convert_out(const float2* src, double2* dst, long long n, cudaStream_t s);

@@ -107,6 +107,8 @@ extern "C" dirac_status dirac_norm_noalloc(int dims, const int N[3], const doubl
   for (int k = 0; k < (dims == 3 ? 8 : 4); ++k)
     if (!planes[k]) return DIRAC_ERR_INVALID;
   if ((long long)N[0] * N[1] >= (1LL << 31)) return DIRAC_ERR_UNSUPPORTED;
+  // link integrals would need a device copy of A_links (an allocation)
+  if (fields && fields->A_links) return DIRAC_ERR_UNSUPPORTED;
   // the reduction grid of this size must fit the fixed scratch array
   const int blocks = observables_blocks(N, dims);
   if (blocks > kNoAllocMaxBlocks) return DIRAC_ERR_UNSUPPORTED;

@@ -88,8 +88,8 @@ __global__ void __launch_bounds__(256) observables_kernel(const ObsArgs<P> a) {
           C dn = nb[cell + (long long)(jm - j[ax]) * stride[ax]];
           R re, im;
           if (a.link_mode == LINK_GENERAL || a.link_mode == LINK_PLANE) {
-            double2 u = mul_expm(widen(up), link_phase(a.f, DIMS, H, ax, +1, a.t_links));
-            double2 v = mul_expm(widen(dn), -link_phase(a.f, DIMS, H, ax, -1, a.t_links));
+            double2 u = mul_expm(widen(up), link_phase_site(a.f, DIMS, H, ax, +1, a.t_links, plane, cell));
+            double2 v = mul_expm(widen(dn), -link_phase_site(a.f, DIMS, H, ax, -1, a.t_links, plane, cell));
             re = (R)(u.x - v.x);
             im = (R)(u.y - v.y);
           } else {
@@ -173,6 +173,32 @@ __global__ void coef_table_kernel(float4* __restrict__ tab, const FieldDesc f, i
   }
 }
 
+// q times the link integrals of every value in the state layout: the value's
+// own link towards +dx_a/2 (slot 2a) and the link from its neighbour at
+// -dx_a/2 to it (slot 2a+1), which that neighbour (partner plane, cell shifted
+// with the periodic wrap) carries as its own up link
+template <int DIMS>
+__global__ void link_integral_table_kernel(double* __restrict__ out, const double* __restrict__ raw, int N0,
+                                           int N1, int N2, long long pstride, double q) {
+  const int plane = blockIdx.y, axis = blockIdx.z;
+  const long long ncell = (long long)N0 * N1 * N2;
+  const long long n = (long long)nplanes<DIMS>() * pstride;
+  const double* raw_a = raw + (long long)axis * nplanes<DIMS>() * ncell;
+  const int pp = partner<DIMS>(plane, axis);
+  const int shift = nb_shift<DIMS>(plane, axis, -1);
+  const int Nn[3] = {N0, N1, N2};
+  const long long stride[3] = {1, N0, (long long)N0 * N1};
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    const long long j[3] = {c % N0, (c / N0) % N1, c / ((long long)N0 * N1)};
+    long long jm = j[axis] + shift;
+    if (jm < 0) jm += Nn[axis];
+    const long long cm = c + (jm - j[axis]) * stride[axis];
+    out[(2LL * axis) * n + plane * pstride + c] = q * raw_a[(long long)plane * ncell + c];
+    out[(2LL * axis + 1) * n + plane * pstride + c] = q * raw_a[(long long)pp * ncell + cm];
+  }
+}
+
 __global__ void finish_sums_kernel(const double* partials, int nblocks, double* out) {
   // warp k sums column k: lane-strided, then a fixed shuffle tree
   const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;
@@ -239,6 +265,18 @@ void launch_coef_table(float4* tab, const FieldDesc& f, int dims, const int N[3]
     coef_table_kernel<3><<<grid, 256, 0, s>>>(tab, f, N[0], N[1], N[2], pstride);
   else
     coef_table_kernel<2><<<grid, 256, 0, s>>>(tab, f, N[0], N[1], 1, pstride);
+}
+
+void launch_link_integral_table(double* out, const double* raw, int dims, const int N[3], long long pstride,
+                                double q, cudaStream_t s) {
+  const long long ncell = (long long)N[0] * N[1] * (dims == 3 ? N[2] : 1);
+  long long bx = (ncell + 255) / 256;
+  if (bx > 152 * 16) bx = 152 * 16;
+  const dim3 grid((unsigned)bx, dims == 3 ? 8 : 4, dims);
+  if (dims == 3)
+    link_integral_table_kernel<3><<<grid, 256, 0, s>>>(out, raw, N[0], N[1], N[2], pstride, q);
+  else
+    link_integral_table_kernel<2><<<grid, 256, 0, s>>>(out, raw, N[0], N[1], 1, pstride, q);
 }
 
 void launch_finish_sums2(const double* partials, int nblocks, double* out, cudaStream_t s) {

@@ -44,7 +44,8 @@ class Fields(C.Structure):
         ("q", C.c_double), ("A_const", C.c_double * 3), ("Apw_amp", C.c_double),
         ("Apw_k", C.c_double * 3), ("Apw_omega", C.c_double), ("Apw_phase", C.c_double),
         ("Apw_pol", C.c_int), ("V0_imag", C.c_double), ("abs_W", C.c_double), ("abs_width", C.c_double),
-        ("abs_axes", C.c_int),
+        ("abs_axes", C.c_int), ("A_links", C.POINTER(C.c_double)), ("Alink_amp", C.c_double),
+        ("Alink_omega", C.c_double),
     ]
 
 
@@ -113,7 +114,7 @@ def _fields_struct(f):
     s = Fields()
     _lib.dirac_fields_default(C.byref(s))
     if f is None:
-        return s, None
+        return s, {}
     s.V0 = f.V0
     s.step_axis, s.step_x0, s.step_V = int(f.step_axis), float(f.step_x0), float(f.step_V)
     s.sc_Z, s.sc_a = float(f.sc_Z), float(f.sc_a)
@@ -121,10 +122,15 @@ def _fields_struct(f):
         s.sc_center[a] = float(f.sc_center[a]) if a < len(f.sc_center) else 0.0
         s.A_const[a] = float(f.A_const[a]) if a < len(f.A_const) else 0.0
         s.Apw_k[a] = float(f.Apw_k[a]) if a < len(f.Apw_k) else 0.0
-    keep = None
+    keep = {}
     if f.V_static is not None:
-        keep = np.ascontiguousarray(f.V_static, dtype=np.float64)
-        s.V_static = keep.ctypes.data_as(_dp)
+        keep["V_static"] = np.ascontiguousarray(f.V_static, dtype=np.float64)
+        s.V_static = keep["V_static"].ctypes.data_as(_dp)
+    if getattr(f, "A_links", None) is not None:
+        keep["A_links"] = np.ascontiguousarray(f.A_links, dtype=np.float64)
+        s.A_links = keep["A_links"].ctypes.data_as(_dp)
+    s.Alink_amp = float(getattr(f, "Alink_amp", 0.0))
+    s.Alink_omega = float(getattr(f, "Alink_omega", 0.0))
     s.Vmod_amp, s.Vmod_omega = float(f.Vmod_amp), float(f.Vmod_omega)
     s.q = float(f.q)
     s.Apw_amp, s.Apw_omega, s.Apw_phase = float(f.Apw_amp), float(f.Apw_omega), float(f.Apw_phase)
@@ -176,8 +182,10 @@ class Sim:
         n = (C.c_int * 3)(*[int(v) for v in (list(prob.N) + [1, 1, 1])[:3]])
         dx = (C.c_double * 3)(*[float(v) for v in (list(prob.dx) + [1.0, 1.0, 1.0])[:3]])
         fs, keep = _fields_struct(prob.fields)
-        if keep is not None and keep.size != int(np.prod(prob.shape)):
+        if "V_static" in keep and keep["V_static"].size != int(np.prod(prob.shape)):
             raise ValueError("V_static must have one value per site (canonical layout)")
+        if "A_links" in keep and keep["A_links"].size != int(prob.dims) * int(np.prod(prob.shape)):
+            raise ValueError("A_links must have dims values per site (axis-major, canonical layout)")
         self._h = _vp()
         st = stream if stream is not None else _current_stream()
         rc = _lib.dirac_create(C.byref(self._h), int(prob.dims), n, dx, float(prob.dt), float(prob.m),

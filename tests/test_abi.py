@@ -64,6 +64,21 @@ def test_host_only_validation(lib):
         g.abs_W, g.abs_width, g.abs_axes = 0.5, width, axes
         assert L.dirac_create(C.byref(h), dims, N, dx, 0.5, 0.0, C.byref(g), 0, 0, None) == D.ERR_INVALID
     assert b"abs_axes" in L.dirac_last_error(None)
+    # link integrals need a finite modulation and charge
+    links = (C.c_double * (3 * 8 * 512))()
+    g = D.Fields()
+    L.dirac_fields_default(C.byref(g))
+    g.A_links = C.cast(links, C.POINTER(C.c_double))
+    g.Alink_amp = float("nan")
+    assert L.dirac_create(C.byref(h), 3, N, dx, 0.5, 0.0, C.byref(g), 0, 0, None) == D.ERR_INVALID
+    assert b"Alink_amp" in L.dirac_last_error(None)
+    # the allocation-free norm cannot take link integrals (rejected before any device work)
+    g.Alink_amp = 0.0
+    L.dirac_norm_noalloc.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_double,
+                                     C.c_double, C.c_void_p, C.c_int, C.POINTER(C.c_void_p),
+                                     C.c_void_p, C.c_void_p]
+    dummy = (C.c_void_p * 8)(*([16] * 8))  # never dereferenced
+    assert L.dirac_norm_noalloc(3, N, dx, 0.5, 0.0, C.byref(g), D.FP32, dummy, 16, None) == D.ERR_UNSUPPORTED
     # grids beyond the 32-bit row indexing of the kernels are refused before any device work
     big = (C.c_int * 3)(65536, 32768, 1)
     assert L.dirac_create(C.byref(h), 2, big, dx, 0.5, 0.0, None, 1, 0, None) == D.ERR_UNSUPPORTED
