@@ -247,9 +247,12 @@ __device__ __forceinline__ float2 apply(const F32::Coef& c, float2 F, float2 S) 
 // hi + lo pair of complex floats (FP32 kernels).  LINK_PLANE: a plane-wave vector potential whose wave vector lies
 // along one axis other than its polarisation; its link factors come from a
 // per-half-step table indexed by the half-lattice coordinate along that axis.
-// GENERAL: per-site FP64.
+// LINK_TABLE: any other time-independent vector potential (FP32 kernels): the
+// factors exp(-i phi) of every value's up and down link per axis, formed once
+// in FP64 from the same phases as the per-site path and kept as hi + lo
+// pairs.  GENERAL: per-site FP64.
 enum CoefMode { COEF_UNIFORM = 0, COEF_STEP = 1, COEF_GENERAL = 2, COEF_TABLE = 3 };
-enum LinkMode { LINK_NONE = 0, LINK_CONST = 1, LINK_GENERAL = 2, LINK_PLANE = 3 };
+enum LinkMode { LINK_NONE = 0, LINK_CONST = 1, LINK_GENERAL = 2, LINK_PLANE = 3, LINK_TABLE = 4 };
 
 // Analytic field description, FP64, for the per-site (general) paths.
 struct FieldDesc {
@@ -453,6 +456,11 @@ struct HalfFields {
   // half-lattice coordinate along ltab_axis; applies on axis lpol only
   const typename P::Link* ltab;
   int ltab_axis, lpol;
+  // LINK_TABLE: link factors [(2 axis + dir) * larr_n + plane * larr_ps + site],
+  // dir 0 = the value's own link upwards, 1 = the link from its lower
+  // neighbour (applied conjugated, like the per-site path)
+  const typename P::Link* larr;
+  long long larr_n, larr_ps;
 };
 
 // The tabulated-potential update (F32 only), the paper's form of the Cayley
@@ -516,6 +524,10 @@ __device__ __forceinline__ typename P::cplx site_update(
         up = link_mul(U, up);
         dn = link_mulc(U, dn);
       }
+    } else if (link == LINK_TABLE) {
+      const long long i = (long long)plane * h.larr_ps + site;
+      up = link_mul(h.larr[(2 * ax) * h.larr_n + i], up);
+      dn = link_mulc(h.larr[(2 * ax + 1) * h.larr_n + i], dn);
     } else if (LINK == kAnyMode && (link == LINK_GENERAL || link == LINK_PLANE)) {
       long long HH[3] = {H[0], H[1], H[2]};
       up = link_mul(link_from(link_phase_site(f, DIMS, HH, ax, +1, h.t, plane, site), (P*)nullptr), up);

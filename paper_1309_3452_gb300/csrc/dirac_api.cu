@@ -37,6 +37,7 @@ struct dirac_sim {
   double* Vstatic = nullptr;  // one real per site (plane-major, pstride)
   float4* b_tab = nullptr;    // COEF_TABLE: b = 1/(1 + i theta) per site as hi + lo (plane-major, pstride)
   double* Alink = nullptr;    // link integrals x q: 2 dims slots (up, down link per axis) of np * pstride
+  F32::Link* larr = nullptr;  // LINK_TABLE: link factors, same slots, FP32 hi + lo
   double* partials = nullptr;
   double* sums_dev = nullptr;
   double* sums_host = nullptr; // pinned
@@ -228,6 +229,11 @@ static HalfFields<P> half_fields(const dirac_sim* s, bool upper, double t) {
   // tabulated potential
   for (int k = 0; k < 8; ++k) h.b_tab[k] = s->b_tab && k < s->np ? s->b_tab + (long long)k * s->pstride : nullptr;
   split(rx, h.rx_hi, h.rx_lo);
+  if (s->link_mode == LINK_TABLE) {
+    h.larr = reinterpret_cast<const typename P::Link*>(s->larr);
+    h.larr_n = (long long)s->np * s->pstride;
+    h.larr_ps = s->pstride;
+  }
   if (s->link_mode == LINK_PLANE) {
     h.ltab = static_cast<typename P::Link*>(s->ltab) + (upper ? 0 : s->ltab_n);
     h.ltab_axis = s->ltab_axis;
@@ -422,6 +428,11 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
       s->ltab_n = 2 * s->N[along];
     }
   }
+  // any other time-independent vector potential: its link factors are
+  // tabulated once for the FP32 kernels instead of a sincos per link and step
+  const bool moving = (f.Apw_amp != 0.0 && f.Apw_omega != 0.0) ||
+                      (alinks && f.Alink_amp != 0.0 && f.Alink_omega != 0.0);
+  if (precision == DIRAC_FP32 && s->link_mode == LINK_GENERAL && !moving) s->link_mode = LINK_TABLE;
 
   auto cleanup_fail = [&](dirac_status st) {
     std::string msg = s->err;
@@ -470,6 +481,16 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     cudaFree(raw);
     if (e != cudaSuccess) return cleanup_fail(cuda_fail(s, e, "link integral table"));
+  }
+  if (s->link_mode == LINK_TABLE) {  // after the link integrals: the phases include them
+    const size_t tb = (size_t)2 * dims * s->np * s->pstride * sizeof(F32::Link);
+    if ((e = cudaMalloc(&s->larr, tb)) != cudaSuccess)
+      return cleanup_fail(cuda_fail(s, e, "cudaMalloc(link factor table)"));
+    if ((e = cudaMemsetAsync(s->larr, 0, tb, s->stream)) != cudaSuccess)
+      return cleanup_fail(cuda_fail(s, e, "cudaMemsetAsync(link factor table)"));
+    launch_link_factor_table(s->larr, field_desc(s), dims, s->N, s->pstride, s->stream);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cleanup_fail(cuda_fail(s, e, "link factor table"));
+    s->launches += 1;
   }
   if (s->coef_mode == COEF_TABLE) {
     if ((e = cudaMalloc(&s->b_tab, (size_t)s->np * s->pstride * sizeof(float4))) != cudaSuccess)
@@ -524,6 +545,7 @@ extern "C" void dirac_destroy(dirac_sim* s) {
   cudaFree(s->Vstatic);
   cudaFree(s->b_tab);
   cudaFree(s->Alink);
+  cudaFree(s->larr);
   cudaFree(s->ltab);
   cudaFree(s->e_partials);
   cudaFree(s->e_sums);
@@ -1273,7 +1295,8 @@ extern "C" dirac_status dirac_check(dirac_sim* s, double tol, dirac_check_report
   }
   // bounds of the functional as a quadratic form
   double lo = 0.0, hi = 0.0;
-  const int general_A = s->link_mode == LINK_GENERAL || s->link_mode == LINK_PLANE;
+  const int general_A = s->link_mode == LINK_GENERAL || s->link_mode == LINK_PLANE ||
+                        s->link_mode == LINK_TABLE;
   dirac_functional_bounds(s->dims, s->dx, s->dt, general_A, &lo, &hi);
   r.lower = 0.0;
   r.upper = INFINITY;
@@ -1308,6 +1331,7 @@ extern "C" double dirac_algorithmic_bytes(const dirac_sim* s) {
   double b = 2.0 * s->np * (double)s->elem;                    // every value read and written once
   if (s->coef_mode == COEF_TABLE) b += 16.0 * s->np;           // one coefficient per value read
   if (s->coef_mode == COEF_GENERAL && s->Vstatic) b += 8.0 * s->np;  // one real per value read
-  if (s->Alink) b += 16.0 * s->dims * s->np;                   // its up and down link integral per axis
+  if (s->link_mode == LINK_TABLE) b += 32.0 * s->dims * s->np;  // up and down link factor (hi + lo) per axis
+  else if (s->Alink) b += 16.0 * s->dims * s->np;              // up and down link integral per axis
   return b;
 }

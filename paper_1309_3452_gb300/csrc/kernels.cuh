@@ -124,6 +124,12 @@ void launch_coef_table(float4* tab, const FieldDesc& f, int dims, const int N[3]
 void launch_link_integral_table(double* out, const double* raw, int dims, const int N[3], long long pstride,
                                 double q, cudaStream_t s);
 
+// LINK_TABLE: exp(-i phi) of every value's up link (slot 2a) and down link
+// (slot 2a+1) of a time-independent vector potential, FP32 hi + lo pairs:
+// out[slot * P * pstride + plane * pstride + cell]
+void launch_link_factor_table(F32::Link* out, const FieldDesc& f, int dims, const int N[3], long long pstride,
+                              cudaStream_t s);
+
 // canonical complex128 plane <-> device plane of the simulation precision
 void launch_convert_in(const double2* src, float2* dst, long long n, cudaStream_t s);
 void launch_convert_out(const float2* src, double2* dst, long long n, cudaStream_t s);

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) observables_kernel(const ObsArgs<P> a) {
           C up = nb[cell + (long long)(jp - j[ax]) * stride[ax]];
           C dn = nb[cell + (long long)(jm - j[ax]) * stride[ax]];
           R re, im;
-          if (a.link_mode == LINK_GENERAL || a.link_mode == LINK_PLANE) {
+          if (a.link_mode == LINK_GENERAL || a.link_mode == LINK_PLANE || a.link_mode == LINK_TABLE) {
             double2 u = mul_expm(widen(up), link_phase_site(a.f, DIMS, H, ax, +1, a.t_links, plane, cell));
             double2 v = mul_expm(widen(dn), -link_phase_site(a.f, DIMS, H, ax, -1, a.t_links, plane, cell));
             re = (R)(u.x - v.x);
@@ -199,6 +199,25 @@ __global__ void link_integral_table_kernel(double* __restrict__ out, const doubl
   }
 }
 
+// LINK_TABLE: the link factors exp(-i phi) of every value of a time-independent
+// vector potential, phi from the same FP64 function as the per-site path
+// (dir 0: the value's up link; dir 1: the link from its lower neighbour)
+template <int DIMS>
+__global__ void link_factor_table_kernel(F32::Link* __restrict__ out, const FieldDesc f, int N0, int N1, int N2,
+                                         long long pstride) {
+  const int plane = blockIdx.y, slot = blockIdx.z, axis = slot >> 1, dir = (slot & 1) ? -1 : 1;
+  const long long ncell = (long long)N0 * N1 * N2;
+  const long long n = (long long)nplanes<DIMS>() * pstride;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    const long long x = c % N0, y = (c / N0) % N1, z = c / ((long long)N0 * N1);
+    const long long H[3] = {2 * x + plane_off<DIMS>(plane, 0), 2 * y + plane_off<DIMS>(plane, 1),
+                            DIMS == 3 ? 2 * z + plane_off<DIMS>(plane, 2) : 0};
+    const double phi = link_phase_site(f, DIMS, H, axis, dir, 0.0, plane, c);
+    out[slot * n + plane * pstride + c] = link_from(phi, (F32*)nullptr);
+  }
+}
+
 __global__ void finish_sums_kernel(const double* partials, int nblocks, double* out) {
   // warp k sums column k: lane-strided, then a fixed shuffle tree
   const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;
@@ -277,6 +296,18 @@ void launch_link_integral_table(double* out, const double* raw, int dims, const 
     link_integral_table_kernel<3><<<grid, 256, 0, s>>>(out, raw, N[0], N[1], N[2], pstride, q);
   else
     link_integral_table_kernel<2><<<grid, 256, 0, s>>>(out, raw, N[0], N[1], 1, pstride, q);
+}
+
+void launch_link_factor_table(F32::Link* out, const FieldDesc& f, int dims, const int N[3], long long pstride,
+                              cudaStream_t s) {
+  const long long ncell = (long long)N[0] * N[1] * (dims == 3 ? N[2] : 1);
+  long long bx = (ncell + 255) / 256;
+  if (bx > 152 * 16) bx = 152 * 16;
+  const dim3 grid((unsigned)bx, dims == 3 ? 8 : 4, 2 * dims);
+  if (dims == 3)
+    link_factor_table_kernel<3><<<grid, 256, 0, s>>>(out, f, N[0], N[1], N[2], pstride);
+  else
+    link_factor_table_kernel<2><<<grid, 256, 0, s>>>(out, f, N[0], N[1], 1, pstride);
 }
 
 void launch_finish_sums2(const double* partials, int nblocks, double* out, cudaStream_t s) {

@@ -753,6 +753,11 @@ template <int DIMS>
 int dispatch(const FusedArgs<F32>& a, cudaStream_t s) {
   const int c = a.hu.coef_mode, l = a.hu.link_mode;
   if (c == COEF_GENERAL || l == LINK_GENERAL) return launch_dims<DIMS, kAnyMode, kAnyMode>(a, s);
+  if (l == LINK_TABLE) {
+    if (c == COEF_UNIFORM) return launch_dims<DIMS, COEF_UNIFORM, LINK_TABLE>(a, s);
+    if (c == COEF_STEP) return launch_dims<DIMS, COEF_STEP, LINK_TABLE>(a, s);
+    return launch_dims<DIMS, COEF_TABLE, LINK_TABLE>(a, s);
+  }
   if (c == COEF_TABLE && l == LINK_NONE) return launch_dims<DIMS, COEF_TABLE, LINK_NONE>(a, s);
   if (c == COEF_TABLE && l == LINK_PLANE) return launch_dims<DIMS, COEF_TABLE, LINK_PLANE>(a, s);
   if (c == COEF_TABLE) return launch_dims<DIMS, kAnyMode, kAnyMode>(a, s);

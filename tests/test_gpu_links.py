@@ -9,7 +9,8 @@ GPU through the C ABI.
   psi_A(t) = exp(i q chi) psi_0(t).
 * The functional E stays conserved with static links (FP32 drift below
   1e-6, dirac_check passes) and the fused FP32 kernels agree bit for bit
-  with the one-kernel-per-half-step path.
+  with the one-kernel-per-half-step path (static links: FP32 link factors
+  tabulated once per simulation; modulated links: per-site FP64 phases).
 """
 import numpy as np
 import pytest
@@ -126,10 +127,17 @@ def test_fused_bit_identical_to_reference_kernels(D, dims, N, moving):
 def test_check_and_bytes_with_links(D, dims, N):
     prob = problem(dims, N, False, seed=11, link_amp=0.3)
     P = prob.n_planes
-    with D.Sim(prob, D.FP32) as s:
-        # state read and written (8 B each per value), the static potential's
-        # coefficient (16 B per value), 16 B of links per axis and value
+    # FP64: state (16 B each way per value), the static potential (8 B), the
+    # up and down link integral per axis (16 B) read by the per-site path
+    with D.Sim(prob, D.FP64) as s:
+        assert s.algorithmic_bytes == 2 * P * 16 + 8 * P + 16 * dims * P
+    # FP32 with a modulation: the per-site path as well (coefficient table 16 B)
+    with D.Sim(problem(dims, N, True, seed=11, link_amp=0.3), D.FP32) as s:
         assert s.algorithmic_bytes == 2 * P * 8 + 16 * P + 16 * dims * P
+    with D.Sim(prob, D.FP32) as s:
+        # static links in FP32: the tabulated factors, up and down link per axis as
+        # hi + lo complex floats (32 B per axis and value)
+        assert s.algorithmic_bytes == 2 * P * 8 + 16 * P + 32 * dims * P
         # a smooth packet, as in the workloads the 1e-6 drift bound is quoted on
         # (a white-noise state under white-noise links accumulates FP32 rounding
         # in E faster)

@@ -222,7 +222,8 @@ def test_unstable_is_rejected_and_diverges_when_forced(D):
 @pytest.mark.parametrize("dims,N", [(2, (37, 29)), (2, (64, 70)), (3, (13, 11, 9)), (3, (33, 17, 20)),
                                     (3, (2, 3, 2))])
 @pytest.mark.parametrize("case", ["free", "klein", "klein_y", "softcore", "A_const", "A_wave",
-                                  "Vstatic", "Vstatic_mod", "softcore_offgrid", "laser", "absorb"])
+                                  "A_wave_long", "Vstatic", "Vstatic_mod", "softcore_offgrid", "laser",
+                                  "absorb"])
 def test_fused_kernel_bit_identical_to_reference_kernels(D, dims, N, case):
     """The fused time-step kernel (out of place, tiles with recomputed halos,
     z/y marching) uses the same per-value arithmetic as the one-kernel-per-
@@ -298,7 +299,7 @@ def test_temporal_blocking_2d_bit_identical(D, N, case, monkeypatch):
 
 
 @pytest.mark.parametrize("dims,N", [(3, (33, 29, 21)), (2, (70, 45))])
-@pytest.mark.parametrize("case", ["free", "klein", "A_const", "softcore", "laser"])
+@pytest.mark.parametrize("case", ["free", "klein", "A_const", "A_wave_long", "softcore", "laser"])
 @pytest.mark.parametrize("nsteps", [7, 10])
 def test_fused_functional_matches_reduction(D, dims, N, case, nsteps, monkeypatch):
     """The last fused launch of dirac_step accumulates E of the new state
