@@ -47,6 +47,11 @@ MUTATIONS = [
      "if (V_fine) V += V_fine[f] * (1.0 + p->Vmod_amp * cos(p->Vmod_omega * (t + p->dt / 2)));"),
     ("link integrals not modulated in time", "double mod = 1.0 + p->Alink_amp * cos(p->Alink_omega * t);",
      "double mod = 1.0 + p->Alink_amp;"),
+    ("Klein step applied on the step itself", "x[p->step_axis] > p->step_x0", "x[p->step_axis] >= p->step_x0"),
+    ("soft core with a instead of a^2", "V -= p->sc_Z / sqrt(r2 + p->sc_a * p->sc_a);",
+     "V -= p->sc_Z / sqrt(r2 + p->sc_a);"),
+    ("absorbing layer only at the lower face", "double d = x[a] < L - x[a] ? x[a] : L - x[a];",
+     "double d = x[a];"),
 ]
 
 

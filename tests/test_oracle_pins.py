@@ -396,6 +396,42 @@ def test_uniform_time_dependent_scalar_potential_2d():
     assert np.max(np.abs(out - ref)) < 1e-12
 
 
+@pytest.mark.parametrize("dims", [2, 3])
+def test_potential_values_at_every_site(dims):
+    """Eqs. ss1-ss4: with every lower value zero, the upper half-step sees no
+    difference part, so one step multiplies every upper value F by its own
+    Cayley factor (1 - i theta)/(1 + i theta), theta = dt (m + V(x, t))/2, and
+    the lower half-step leaves it alone.  This fixes the value of V at every
+    upper site's own position: a Klein step H(x_a - x0) with a site exactly on
+    x0 (strict '>'), an off-grid soft core -Z/sqrt(|x - c|^2 + a^2) (plain
+    distance), a modulated static array and absorbing layers (Im V)."""
+    N = (7, 6, 5) if dims == 3 else (7, 6, 1)
+    prob = W.Problem(dims, N, (1.0, 1.0, 1.0), 0.9 * W.stability_limit(dims), 0.3)
+    Vs = W.random_potential(prob, 21, 0.4)
+    c = (2.3, 3.65, 1.8)
+    f = dict(V0=0.1, step_axis=1, step_x0=2.5, step_V=0.6, sc_Z=0.8, sc_a=1.1, sc_center=c, V_static=Vs,
+             Vmod_amp=0.3, Vmod_omega=0.7, V0_imag=-0.01, abs_W=0.5, abs_width=2.0, abs_axes=(1 << dims) - 1)
+    prob = prob.with_fields(**f)
+    P_up = prob.n_planes // 2  # upper planes come first
+    psi = W.random_state(prob, 22)
+    psi[P_up:] = 0.0
+    t0 = 0.4
+    out = O.step(prob, psi, 1, t0)
+    L = [prob.N[a] * prob.dx[a] for a in range(3)]
+    for pl in range(P_up):
+        x = W.site_positions(prob, pl)
+        V = 0.1 + 0.6 * (x[1] > 2.5) + Vs[pl] * (1 + 0.3 * math.cos(0.7 * t0))
+        V = V - 0.8 / np.sqrt(sum((x[a] - c[a]) ** 2 for a in range(dims)) + 1.1 ** 2)
+        Wl = np.zeros(V.shape)
+        for a in range(dims):
+            d = np.minimum(x[a], L[a] - x[a])
+            Wl += np.where(d < 2.0, (1 - d / 2.0) ** 2, 0.0)
+        th = prob.dt * (prob.m + V + 1j * (-0.01 - 0.5 * Wl)) / 2
+        assert np.max(np.abs(out[pl] - psi[pl] * (1 - 1j * th) / (1 + 1j * th))) < 1e-14
+    ys = np.concatenate([W.site_positions(prob, pl)[1].ravel() for pl in range(P_up)])
+    assert np.any(ys == 2.5) and np.any(ys == 3.0)  # upper sites on and just beyond the step
+
+
 # ---------------------------------------------------------------- T10
 def test_proposition_2_bound():
     """Prop. 2: for r_x + r_y + r_z < 1 the naive norm stays below
