@@ -69,6 +69,14 @@ def workload(name):
         n = 500
         desc = ("(2+1)D 4096^2 Klein refraction (Sect. 5): m=0, step V=2E at x0=N/2+1/4, packet sigma=64, "
                 "|k0|=0.25 at 37 deg to the step; 500 time steps + E per step")
+    elif name == "3d128links":
+        prob, psi, n = W.workload_links(3, 128, 200)
+        desc = ("(3+1)D 128^3 periodic, m=1, static vector potential given by seeded random link "
+                "integrals in [-0.3, 0.3] (q=1), packet as 3d128; 200 time steps + E per step")
+    elif name == "2d2048links":
+        prob, psi, n = W.workload_links(2, 2048, 200)
+        desc = ("(2+1)D 2048^2 periodic, m=1, static vector potential given by seeded random link "
+                "integrals in [-0.3, 0.3] (q=1), packet sigma=10; 200 time steps + E per step")
     elif name == "2d64":
         prob, psi, n = W.workload_2d64(0.5)
         desc = "(2+1)D 64^2, m=0.5, packet sigma=6, 200 time steps + E per step"
@@ -285,7 +293,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="3d128", choices=["3d128", "3d512", "3d512laser", "3d256laser", "2d4096", "2d4096k37", "2d64", "serve"])
+    ap.add_argument("--workload", default="3d128", choices=["3d128", "3d512", "3d512laser", "3d256laser", "2d4096", "2d4096k37", "3d128links",
+                             "2d2048links", "2d64", "serve"])
     ap.add_argument("--requests", type=int, default=40, help="serve: requests in the stream")
     ap.add_argument("--quantum", type=int, default=100, help="serve: steps per batching quantum")
     ap.add_argument("--seed", type=int, default=0, help="serve: request stream seed")

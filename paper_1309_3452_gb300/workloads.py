@@ -350,6 +350,19 @@ def workload_klein_oblique(N: int = 4096, steps: int = 3000, sigma: float = 64.0
     return prob, psi, steps
 
 
+def workload_links(dims: int = 3, N: int = 128, steps: int = 200, seed: int = 2, amplitude: float = 0.3):
+    """A static vector potential given only by its link integrals (Sect. 4),
+    drawn uniformly in [-a, a] per link (seeded), q = 1, m = 1, on the
+    periodic (3+1)D or (2+1)D grid of the free workloads with their packet."""
+    if dims == 3:
+        prob, psi, _ = workload_3d(N=N, steps=steps)
+    else:
+        prob = Problem(2, (N, N, 1), (1.0, 1.0, 1.0), 0.9 * stability_limit(2), 1.0)
+        psi = gaussian_packet(prob, 10.0, tuple(random_k0(0))[:2], (N / 2.0, N / 2.0))
+    prob = prob.with_fields(q=1.0, A_links=random_links(prob, seed, amplitude))
+    return prob, psi, steps
+
+
 def laser_fields(N: int) -> Fields:
     """Soft-core potential -1/sqrt(|x-c|^2 + 1) at the box centre plus a plane
     wave A_x = 0.5 cos(2 pi z / 64 - omega t), omega = 2 pi / 64."""
