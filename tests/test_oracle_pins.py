@@ -396,6 +396,53 @@ def test_uniform_time_dependent_scalar_potential_2d():
     assert np.max(np.abs(out - ref)) < 1e-12
 
 
+def test_uniform_time_dependent_fields_3d():
+    """Eqs. ss1-ss4 in (3+1)D with a spatially uniform V(t) and A(t) (a
+    constant A_x plus A_z = amp cos(phase - w t)): a lattice plane wave keeps
+    one amplitude per component A, B, C, D, and a step is the per-mode
+    recursion S_A = i dt (P_z c + (P_x - i P_y) d), S_B = i dt ((P_x + i P_y) c
+    - P_z d), S_C = i dt (P_z a + (P_x - i P_y) b), S_D = i dt ((P_x + i P_y) a
+    - P_z b), with P_a = (2/dx) sin((k_a - q A_a) dx/2) and every field taken
+    at its half-step's time sheet (upper t, lower t + dt/2)."""
+    N = (6, 5, 8)
+    dt = 0.9 * W.stability_limit(3)
+    m, q, V1, vamp, vom = 0.4, 0.9, 0.3, 0.5, 0.6
+    Ax, amp, om, ph = 0.25, 0.45, 0.35, 0.3
+    prob = W.Problem(3, N, (1.0, 1.0, 1.0), dt, m)
+    prob = prob.with_fields(V0=0.05, V_static=np.full(prob.shape, V1), Vmod_amp=vamp, Vmod_omega=vom,
+                            q=q, A_const=(Ax, 0.0, 0.0), Apw_amp=amp, Apw_k=(0.0, 0.0, 0.0), Apw_omega=om,
+                            Apw_phase=ph, Apw_pol=2)
+    k = (2 * math.pi * 1 / N[0], 2 * math.pi * -2 / N[1], 2 * math.pi * 3 / N[2])
+    amps = [0.3 + 0.2j, -0.5 + 0.1j, 0.2 - 0.6j, 0.4 + 0.4j]  # a, b, c, d
+    comp = [0, 0, 1, 1, 2, 2, 3, 3]  # planes A0 A1 B0 B1 C0 C1 D0 D1
+
+    def wave(ampl):
+        out = np.zeros(prob.shape, complex)
+        for pl in range(8):
+            xyz = W.site_positions(prob, pl)
+            out[pl] = ampl[comp[pl]] * np.exp(1j * sum(k[i] * xyz[i] for i in range(3)))
+        return out
+
+    V = lambda t: 0.05 + V1 * (1 + vamp * math.cos(vom * t))
+    P = lambda t: [2 * math.sin((k[0] - q * Ax) / 2), 2 * math.sin(k[1] / 2),
+                   2 * math.sin((k[2] - q * amp * math.cos(ph - om * t)) / 2)]
+    a, b, c, d = amps
+    n, t0 = 25, 0.15
+    t = t0
+    for _ in range(n):
+        Px, Py, Pz = P(t)
+        th = dt * (m + V(t)) / 2
+        a = ((1 - 1j * th) * a - 1j * dt * (Pz * c + (Px - 1j * Py) * d)) / (1 + 1j * th)
+        b = ((1 - 1j * th) * b - 1j * dt * ((Px + 1j * Py) * c - Pz * d)) / (1 + 1j * th)
+        Px, Py, Pz = P(t + dt / 2)
+        th = dt * (V(t + dt / 2) - m) / 2
+        c = ((1 - 1j * th) * c - 1j * dt * (Pz * a + (Px - 1j * Py) * b)) / (1 + 1j * th)
+        d = ((1 - 1j * th) * d - 1j * dt * ((Px + 1j * Py) * a - Pz * b)) / (1 + 1j * th)
+        t += dt
+    out = O.step(prob, wave(amps), n, t0)
+    assert np.max(np.abs(out - wave([a, b, c, d]))) < 1e-12
+
+
 @pytest.mark.parametrize("dims", [2, 3])
 def test_potential_values_at_every_site(dims):
     """Eqs. ss1-ss4: with every lower value zero, the upper half-step sees no
