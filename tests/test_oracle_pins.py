@@ -443,6 +443,75 @@ def test_uniform_time_dependent_fields_3d():
     assert np.max(np.abs(out - wave([a, b, c, d]))) < 1e-12
 
 
+def test_time_reversal_3d():
+    """Eqs. ss1-ss4 are explicit Cayley maps, each half-step reading only the
+    other time sheet, so the scheme runs backwards exactly: shifting the
+    lattice by dx/2 along z swaps the upper and lower sheets (A,B <-> C,D
+    without changing any value's sign class (x+y parity)), and stepping the
+    shifted state with -dt and -m applies the inverse half-steps in reverse
+    order.  n steps forward and n back recover the initial state to
+    rounding; an update that read its own sheet, or values of the other
+    sheet from the wrong step, would not."""
+    N = (6, 5, 7)
+    prob = W.Problem(3, N, (1.0, 1.0, 1.0), 0.9 * W.stability_limit(3), 0.5)
+    Vs = W.random_potential(prob, 31, 0.5)
+    prob = prob.with_fields(V_static=Vs, q=0.8, A_const=(0.3, -0.2, 0.1))
+    # plane -> (plane after the shift, cell shift along z): A0->C0, A1->C1,
+    # B0->D0(+1), B1->D1(+1), C0->A0(+1), C1->A1(+1), D0->B0, D1->B1
+    moves = {0: (4, 0), 1: (5, 0), 2: (6, 1), 3: (7, 1), 4: (0, 1), 5: (1, 1), 6: (2, 0), 7: (3, 0)}
+
+    def shift(a):
+        out = np.empty_like(a)
+        for p, (q, dz) in moves.items():
+            out[q] = np.roll(a[p], dz, axis=0)
+        return out
+
+    def unshift(a):
+        out = np.empty_like(a)
+        for p, (q, dz) in moves.items():
+            out[p] = np.roll(a[q], -dz, axis=0)
+        return out
+
+    psi0 = W.random_state(prob, 32)
+    n = 30
+    fwd = O.step(prob, psi0, n)
+    back = W.Problem(3, N, prob.dx, -prob.dt, -prob.m, prob.fields).with_fields(V_static=shift(Vs))
+    out = unshift(O.step(back, shift(fwd), n))
+    assert np.max(np.abs(fwd - psi0)) > 0.05
+    assert np.max(np.abs(out - psi0)) < 1e-13
+
+
+def test_klein_step_normal_incidence_nearly_transparent():
+    """Sect. 5 (soft check): at normal incidence with m = 0 a packet passes a
+    Klein step almost completely (in the continuum exactly: chirality
+    conservation).  On the lattice the abrupt step reflects a little; with
+    V dx = 0.5 and k0 dx = 0.25 the transmitted fraction, once the packet has
+    passed, exceeds 0.98 (measured 0.984), and halving V reduces the
+    reflection at least threefold."""
+    def transmitted(V):
+        N = 320
+        x0 = N / 2 + 0.25
+        prob = W.Problem(2, (N, 2, 1), (1.0, 1.0, 1.0), 0.9 * W.stability_limit(2), 0.0,
+                         W.Fields(step_axis=0, step_x0=x0, step_V=V))
+        sigma, kx = 16.0, 0.25
+        w = W.continuum_spinor(2, (kx, 0.0), 0.0)
+        _, _, _, comp = W.plane_tables(2)
+        psi = np.zeros(prob.shape, complex)
+        for pl in range(4):  # a packet uniform along y: normal incidence only
+            x = W.site_positions(prob, pl)[0]
+            ts = W.sheet_time(prob, pl, 0.0)
+            psi[pl] = w[comp[pl]] * np.exp(-(x - (x0 - 4 * sigma)) ** 2 / (2 * sigma ** 2)) * \
+                np.exp(1j * (kx * x - kx * ts))
+        psi /= np.linalg.norm(psi)
+        out = O.step(prob, psi, int(8 * sigma / (0.95 * prob.dt)))
+        right = sum(np.sum(np.abs(out[pl][W.site_positions(prob, pl)[0] > x0]) ** 2) for pl in range(4))
+        return right / np.sum(np.abs(out) ** 2)
+
+    T1, T2 = transmitted(0.5), transmitted(0.25)
+    assert T1 > 0.98
+    assert (1 - T2) < (1 - T1) / 3
+
+
 @pytest.mark.parametrize("dims", [2, 3])
 def test_potential_values_at_every_site(dims):
     """Eqs. ss1-ss4: with every lower value zero, the upper half-step sees no
