@@ -104,8 +104,13 @@ typedef enum {
  *   1 + Alink_amp * cos(Alink_omega * t).
  * A must be periodic on the box for the link factors at the wrap to be
  * consistent.  A_links: NULL or a host array of dims * P * cells reals, copied
- * during dirac_create; with it the link factors are evaluated per site in FP64
- * (the general field path) and dirac_norm_noalloc is unavailable.  The upper
+ * during dirac_create.  Link factors: a constant A, and a plane wave whose
+ * wave vector lies along one axis other than its polarisation, need no
+ * per-value data.  Any other A that does not change in time (Apw_omega = 0
+ * or Apw_amp = 0; Alink_omega = 0 or Alink_amp = 0) has its factors
+ * exp(-i phi) tabulated once per simulation for DIRAC_FP32 (FP64 phases,
+ * hi + lo float pairs); otherwise they are evaluated per site in FP64.
+ * dirac_norm_noalloc does not take A_links.  The upper
  * half-step uses the fields at time t, the lower half-step at t + dt/2 (the
  * time sheets of Eqs. ss1-ss4).
  * V_static: NULL, or a host array of one real per site (canonical layout);
@@ -319,9 +324,10 @@ dirac_status dirac_check(dirac_sim* sim, double tol, dirac_check_report* out);
 /* Algorithmic HBM bytes of one site update (one cell advanced one full time
    step) on this simulation's path: every value read and written once, plus
    a per-site coefficient (16 bytes) or static potential (8 bytes) read per
-   value where the potential needs one, and with A_links two link integrals
-   (16 bytes) per axis and value.  The roofline numerator of a time step.  0
-   for NULL. */
+   value where the potential needs one, and the vector potential's per-value
+   link data where it has some: two tabulated link factors (32 bytes) per axis
+   and value, or two link integrals (16 bytes) per axis and value on the
+   per-site path.  The roofline numerator of a time step.  0 for NULL. */
 double dirac_algorithmic_bytes(const dirac_sim* sim);
 
 /* device bytes a simulation of this shape and precision allocates for a
@@ -329,8 +335,9 @@ double dirac_algorithmic_bytes(const dirac_sim* sim);
    DIRAC_FP32 a second state buffer and one complex128 conversion plane.
    Other potentials add one double per value (DIRAC_FP64, or a time-
    dependent static array) or the coefficient table, 16 bytes per value
-   (DIRAC_FP32, time-independent), A_links 16 bytes per axis and value, and
-   every simulation a few KiB of reduction scratch. */
+   (DIRAC_FP32, time-independent), A_links 16 bytes per axis and value, a
+   tabulated static vector potential (DIRAC_FP32) 32 bytes per axis and
+   value, and every simulation a few KiB of reduction scratch. */
 size_t dirac_state_bytes(int dims, const int N[3], dirac_precision precision);
 
 /* human-readable description of the last failure on sim (or, when sim is
