@@ -386,7 +386,11 @@ dirac_status dirac_norm_noalloc(int dims, const int N[3], const double dx[3], do
                                 const dirac_fields* fields, dirac_precision precision,
                                 const void* const* planes, double* out_dev, void* cuda_stream);
 
-/* ABI version of this header */
+/* ABI version: DIRAC_ABI_VERSION of the header the library was built with.
+   A client checks it against the header it was compiled with; the version
+   changes whenever a structure or a signature does (2: dirac_fields gained
+   A_links, Alink_amp, Alink_omega). */
+#define DIRAC_ABI_VERSION 2
 int dirac_version(void);
 
 #ifdef __cplusplus

@@ -108,7 +108,7 @@ extern "C" void dirac_fields_default(dirac_fields* f) {
   f->sc_a = 1.0;
 }
 
-extern "C" int dirac_version(void) { return 1; }
+extern "C" int dirac_version(void) { return DIRAC_ABI_VERSION; }
 
 extern "C" const char* dirac_last_error(const dirac_sim* s) {
   return s ? s->err.c_str() : g_create_error.c_str();

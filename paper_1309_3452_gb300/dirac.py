@@ -88,6 +88,11 @@ _lib.dirac_last_error.restype = C.c_char_p
 _lib.dirac_destroy.argtypes = [_vp]
 _lib.dirac_fields_default.argtypes = [C.POINTER(Fields)]
 _lib.dirac_version.restype = C.c_int
+# the structures above mirror include/dirac.h of this ABI version
+ABI_VERSION = 2
+if _lib.dirac_version() != ABI_VERSION:
+    raise ImportError(f"{LIB_PATH} has ABI version {_lib.dirac_version()}, the binding expects "
+                      f"{ABI_VERSION}; rebuild it with `python -m paper_1309_3452_gb300.build`")
 _lib.dirac_get_plan.argtypes = [_vp, C.POINTER(Plan)]
 _lib.dirac_set_plan.argtypes = [_vp, C.POINTER(Plan)]
 _lib.dirac_autotune.argtypes = [_vp, C.POINTER(Plan)]

@@ -42,7 +42,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_host_only_validation(lib):
     from paper_1309_3452_gb300 import dirac as D
 
-    assert D.lib().dirac_version() == 1
+    assert D.lib().dirac_version() == D.ABI_VERSION == 2
     f = D.Fields()
     D.lib().dirac_fields_default(C.byref(f))
     assert f.q == 1.0 and f.step_axis == -1 and f.sc_a == 1.0 and f.V0 == 0.0
