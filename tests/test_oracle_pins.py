@@ -564,6 +564,58 @@ def test_proposition_2_bound():
         assert O.observables(prob, psi, t)["naive"] <= bound
 
 
+def _appendix_sums_3d(prob, psi):
+    """The appendix's sum of squares around the A and B sites at
+    r = 1/sqrt(3) (E-tilde) and the grid-averaged norm of (C, D) of Prop. 3,
+    evaluated on the half lattice (neighbours at +-1 with the periodic wrap)."""
+    M = [2 * prob.N[a] for a in range(3)]
+    f = np.zeros((M[2], M[1], M[0]), complex)
+    for pl in range(prob.n_planes):
+        X, Y, Z = W.half_lattice_points(prob, pl)
+        f[Z, Y, X] = psi[pl]
+    at = lambda d, ax: np.roll(f, -d, axis=2 - ax)  # the value at F + d e_ax
+    Z, Y, X = np.meshgrid(*[np.arange(n) for n in f.shape], indexing="ij")
+    A = ((X + Y) % 2 == 0) & (Z % 2 == 0)
+    B = ((X + Y) % 2 == 1) & (Z % 2 == 1)
+    s3 = math.sqrt(3.0)
+    aA = (at(1, 2) + at(1, 0) - 1j * at(1, 1)) / s3    # (C_{z+} + D_{x+} - i D_{y+}) / sqrt(3)
+    bA = (at(-1, 2) + at(-1, 0) - 1j * at(-1, 1)) / s3
+    aB = (at(1, 2) - at(1, 0) - 1j * at(1, 1)) / s3    # (D_{z+} - C_{x+} - i C_{y+}) / sqrt(3)
+    bB = (at(-1, 2) - at(-1, 0) - 1j * at(-1, 1)) / s3
+    E_tilde = 0.5 * np.sum(np.abs(aA - f)[A] ** 2 + np.abs(bA + f)[A] ** 2) + \
+        0.5 * np.sum(np.abs(aB + f)[B] ** 2 + np.abs(bB - f)[B] ** 2)
+    cd_avg = 0.25 * np.sum(np.abs(aA + bA)[A] ** 2) + 0.25 * np.sum(np.abs(aB + bB)[B] ** 2)
+    return E_tilde, cd_avg
+
+
+def test_appendix_sum_of_squares_and_proposition_3():
+    """Appendix A: at r = 1/sqrt(3) the functional equals a sum of squares
+    around the A and B sites (E-tilde, an algebraic identity for every
+    state), so E >= 0 and the grid-averaged norm of (C, D) of Prop. 3 never
+    exceeds E.  Checked on random states (identity to rounding) and along a
+    run with a random, time-dependent potential and a mass (the averaged
+    norm stays below the conserved E0)."""
+    N = (5, 4, 6)
+    prob = W.Problem(3, N, (1.0, 1.0, 1.0), 1 / math.sqrt(3), 0.7)
+    for seed in (3, 4):
+        psi = W.random_state(prob, seed)
+        ob = O.observables(prob, psi)
+        E_tilde, _ = _appendix_sums_3d(prob, psi)
+        assert abs(E_tilde - ob["E_upper"]) < 1e-14 and abs(E_tilde - ob["E"]) < 1e-14
+    prob = prob.with_fields(V_static=W.random_potential(prob, 5, 0.8), Vmod_amp=0.6, Vmod_omega=0.9,
+                            step_axis=0, step_x0=2.25, step_V=0.5)
+    psi = W.random_state(prob, 6)
+    E0 = O.observables(prob, psi)["E"]
+    t = 0.0
+    for _ in range(8):
+        psi = O.step(prob, psi, 25, t)
+        t += 25 * prob.dt
+        E = O.observables(prob, psi, t)["E"]
+        E_tilde, cd_avg = _appendix_sums_3d(prob, psi)
+        assert abs(E - E0) < 1e-12 and abs(E_tilde - E) < 1e-12
+        assert cd_avg <= E0 * (1 + 1e-12)
+
+
 def test_proposition_5_averaged_norm_2d():
     """Prop. 5 (Sect. 3): at r = 1/sqrt(2) the grid-averaged norm of u stays
     below E0 (so ||u~||^2 + ||v~||^2 <= 2 E0) for arbitrary V.  With the
