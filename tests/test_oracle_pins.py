@@ -616,6 +616,35 @@ def test_appendix_sum_of_squares_and_proposition_3():
         assert cd_avg <= E0 * (1 + 1e-12)
 
 
+def test_2d_functional_is_a_sum_of_squares_at_the_bound():
+    """Prop. 5's proof (Sect. 3): at r = 1/sqrt(2) the (2+1)D functional equals
+    the auxiliary E~ = sum over v sites G of 1/2 |a_G + v_G|^2 + 1/2 |b_G - v_G|^2,
+    a_G = (u_{G+x} + i u_{G+y})/sqrt(2), b_G = (u_{G-x} + i u_{G-y})/sqrt(2),
+    for every state (the u-u cross terms telescope).  With the delta_+ reading
+    of the functional the signs are +i; the printed -i would not reproduce E.
+    Checked on random states with the oracle's E."""
+    N = (7, 6)
+    prob = W.Problem(2, (N[0], N[1], 1), (1.0, 1.0, 1.0), 1.0 / math.sqrt(2.0), 0.4)
+    M = (2 * N[0], 2 * N[1])
+    for seed in (8, 9):
+        psi = W.random_state(prob, seed)
+        f = np.zeros((M[1], M[0]), complex)
+        for pl in range(4):
+            X, Y, _ = W.half_lattice_points(prob, pl)
+            f[Y[0], X[0]] = psi[pl, 0]
+        at = lambda d, ax: np.roll(f, -d, axis=1 - ax)  # the value at G + d e_ax
+        Y, X = np.meshgrid(np.arange(M[1]), np.arange(M[0]), indexing="ij")
+        v = (X + Y) % 2 == 1
+        a = (at(1, 0) + 1j * at(1, 1)) / math.sqrt(2)
+        b = (at(-1, 0) + 1j * at(-1, 1)) / math.sqrt(2)
+        E_tilde = 0.5 * np.sum(np.abs(a + f)[v] ** 2 + np.abs(b - f)[v] ** 2)
+        ob = O.observables(prob, psi)
+        assert abs(E_tilde - ob["E"]) < 1e-14 and abs(E_tilde - ob["E_upper"]) < 1e-14
+        printed = 0.5 * np.sum(np.abs((at(1, 0) - 1j * at(1, 1)) / math.sqrt(2) + f)[v] ** 2 +
+                               np.abs((at(-1, 0) - 1j * at(-1, 1)) / math.sqrt(2) - f)[v] ** 2)
+        assert abs(printed - ob["E"]) > 1e-3
+
+
 def test_proposition_5_averaged_norm_2d():
     """Prop. 5 (Sect. 3): at r = 1/sqrt(2) the grid-averaged norm of u stays
     below E0 (so ||u~||^2 + ||v~||^2 <= 2 E0) for arbitrary V.  With the
