@@ -202,6 +202,22 @@ def test_stability_bound(dims):
                 assert np.max(np.abs(lam)) > 1.05
 
 
+@pytest.mark.parametrize("dims,N,dx", [(3, (2, 2, 2), (1.0, 1.3, 0.8)), (2, (4, 4, 1), (1.0, 0.7, 1.0))])
+def test_stability_bound_anisotropic(dims, N, dx):
+    """The stability condition with r_a = dt/dx_a per axis (Sect. 2.2:
+    r_x^2 + r_y^2 + r_z^2 <= 1; Sect. 3: r_x^2 + r_y^2 <= 1) on an anisotropic
+    grid: |lambda| = 1 at 0.97 of the largest stable dt, |lambda| > 1 at 1.03
+    (a mistaken r_a on any axis moves the edge away from 1)."""
+    dt_max = 1.0 / math.sqrt(sum(1.0 / dx[a] ** 2 for a in range(dims)))
+    for f, stable in ((0.97, True), (1.03, False)):
+        prob = W.Problem(dims, N, dx, f * dt_max, 0.3)
+        lam = np.abs(np.linalg.eigvals(one_step_matrix(prob)))
+        if stable:
+            assert np.max(lam) - 1.0 < 1e-12
+        else:
+            assert np.max(lam) > 1.1
+
+
 def test_functional_positive_definite_3d():
     """Appendix A / Prop. 3: at r <= 1/sqrt(3) the functional E is a norm;
     above the bound it is indefinite (its Hermitian form gets a negative
