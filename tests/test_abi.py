@@ -57,6 +57,15 @@ def test_host_only_validation(lib):
     bad = (C.c_int * 3)(1, 8, 8)
     assert L.dirac_create(C.byref(h), 3, bad, dx, 0.5, 0.0, None, 0, 0, None) == D.ERR_INVALID
     assert L.dirac_create(C.byref(h), 2, N, dx, -0.1, 0.0, None, 0, 0, None) == D.ERR_INVALID
+    # the stability bound sum_a (dt/dx_a)^2 <= 1 with per-axis spacings
+    adx = (C.c_double * 3)(1.0, 1.3, 0.8)
+    dt_max = 1.0 / (1.0 + 1.0 / 1.3 ** 2 + 1.0 / 0.8 ** 2) ** 0.5
+    assert L.dirac_create(C.byref(h), 3, N, adx, 1.01 * dt_max, 0.0, None, 0, 0, None) == D.ERR_UNSTABLE
+    rc = L.dirac_create(C.byref(h), 3, N, adx, 0.99 * dt_max, 0.0, None, 0, 0, None)
+    assert rc != D.ERR_UNSTABLE  # accepted (without a device creation then fails later, with ERR_CUDA)
+    if rc == D.OK:
+        L.dirac_destroy(h)
+        h = C.c_void_p()
     # absorbing layers: a width and a non-empty mask of the grid's axes
     for width, axes, dims in ((0.0, 1, 3), (2.0, 0, 3), (2.0, 8, 3), (2.0, 4, 2)):
         g = D.Fields()
