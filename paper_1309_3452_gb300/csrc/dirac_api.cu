@@ -410,7 +410,7 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
   else s->coef_mode = f.step_axis >= 0 ? COEF_STEP : COEF_UNIFORM;
   if (f.step_axis >= 0) s->step_X = threshold_index(f.step_x0, s->dx[f.step_axis]);
   bool any_A = f.A_const[0] != 0.0 || f.A_const[1] != 0.0 || f.A_const[2] != 0.0;
-  // link integrals of an arbitrary A: per-site FP64 phases (the general path)
+  // link integrals of an arbitrary A: per-site phases (tabulated below when static)
   const bool alinks = f.A_links != nullptr;
   s->link_mode = (f.Apw_amp != 0.0 || alinks) ? LINK_GENERAL : (any_A ? LINK_CONST : LINK_NONE);
   if (f.Apw_amp != 0.0 && !alinks) {
@@ -639,7 +639,7 @@ extern "C" dirac_status dirac_get_spinor_device(dirac_sim* s, void* dev) {
   return DIRAC_OK;
 }
 
-// n time steps with one launch sequence each, on stream st
+// a vector potential that changes in time (its link factors too)
 static bool moving_vector_potential(const dirac_sim* s) {
   return (s->f.Apw_amp != 0.0 && s->f.Apw_omega != 0.0) ||
          (s->Alink && s->f.Alink_amp != 0.0 && s->f.Alink_omega != 0.0);
@@ -721,6 +721,7 @@ static dirac_status steps_fused(dirac_sim* s, long n, cudaStream_t st, bool want
   return DIRAC_OK;
 }
 
+// n time steps with one launch sequence each, on stream st
 static dirac_status steps_plain(dirac_sim* s, long n, cudaStream_t st, bool want_e = false) {
   if (s->prec == DIRAC_FP64) return steps_split<F64>(s, n, st);
   if (s->fused) return steps_fused<F32>(s, n, st, want_e);
