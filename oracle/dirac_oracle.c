@@ -19,10 +19,13 @@
  *  - The vector potential enters through exact Peierls link factors
  *    (Sect. 4): in a difference along axis a the neighbour at +dx_a/2 is
  *    multiplied by exp(-i phi) and the one at -dx_a/2 by exp(+i phi'), where
- *    phi = q A_a(link midpoint, t_nb) dx_a/2.  To first order in A this is the
- *    printed rule for spatial differences in Sect. 4; the printed rule for the
- *    time derivative belongs to the gauge-transformed picture and is not
- *    applied on top of the links.
+ *    phi = q times the line integral of A_a along that link (of length
+ *    dx_a/2) at the neighbours' time t_nb: A_const dx_a/2, the plane wave's
+ *    exact integral (its midpoint value times sin(k_a dx_a/4)/(k_a dx_a/4)),
+ *    and the caller's tabulated link integrals.  To first order in A this is
+ *    the printed rule for spatial differences in Sect. 4; the printed rule
+ *    for the time derivative belongs to the gauge-transformed picture and is
+ *    not applied on top of the links.
  *  - Boundaries are periodic in units of the cell.
  */
 #include "dirac_oracle.h"
