@@ -150,7 +150,8 @@ void dirac_fields_default(dirac_fields* f);
  * Create a simulation of the (dims+1)D scheme on an N[0] x N[1] (x N[2])
  * periodic grid of unit cells (each cell carries two sites of every
  * component), lattice constants dx[], time step dt, mass m.  fields may be
- * NULL (free particle).  Rejects N[a] < 2, dx[a] <= 0, dt <= 0 and (unless
+ * NULL (free particle).  Rejects N[a] < 2, dx[a] <= 0, dt <= 0, a NaN or an
+ * infinity in any real parameter of fields (DIRAC_ERR_INVALID) and (unless
  * DIRAC_FLAG_ALLOW_UNSTABLE) sum_a (dt/dx[a])^2 > 1.  cuda_stream is a
  * cudaStream_t (may be NULL).  The state starts at zero with t = 0.
  * On success *out owns the simulation; free it with dirac_destroy.
@@ -222,7 +223,9 @@ dirac_status dirac_batch_step(dirac_sim* const* sims, int nsims, long nsteps);
 dirac_status dirac_norm(dirac_sim* sim, double* E, double* naive);
 
 /* sum of |psi|^2 over the values whose position along axis exceeds x0
-   (transmitted probability for the Klein step, Sect. 5).  Synchronises. */
+   (transmitted probability for the Klein step, Sect. 5).  x0 must be finite
+   (else DIRAC_ERR_INVALID); beyond the box the sum is 0 or everything.
+   Synchronises. */
 dirac_status dirac_partial_density(dirac_sim* sim, int axis, double x0, double* out);
 
 /* simulation time t of the lower sheet (upper planes are at t - dt/2) */
@@ -376,11 +379,15 @@ void dirac_destroy(dirac_sim* sim);
  *   needs clearing between calls; calls that overlap on the GPU (other
  *   streams, or another host thread) race on it and must be serialised by
  *   the caller.
- * Set-up: the first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress, with that device current); make that first call
+ * Set-up: every call looks up the array's address on the current device
+ *   (cudaGetSymbolAddress, which allocates nothing), so a device reset or a
+ *   new context never leaves a stale address behind.  The first call on a
+ *   device may load the library's device code there; make that first call
  *   before any stream capture.
- * Returns DIRAC_ERR_INVALID for bad arguments, DIRAC_ERR_CUDA if the set-up
- *   or a launch fails.
+ * Returns DIRAC_ERR_INVALID for bad arguments (including non-finite q,
+ *   A_const or plane-wave parameters, and a plane wave whose Apw_pol is not
+ *   an axis of the grid, as dirac_create rejects them), DIRAC_ERR_CUDA if the
+ *   address lookup or a launch fails.
  */
 dirac_status dirac_norm_noalloc(int dims, const int N[3], const double dx[3], double dt, double t,
                                 const dirac_fields* fields, dirac_precision precision,

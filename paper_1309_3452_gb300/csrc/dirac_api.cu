@@ -114,13 +114,34 @@ extern "C" const char* dirac_last_error(const dirac_sim* s) {
   return s ? s->err.c_str() : g_create_error.c_str();
 }
 
-// smallest half-lattice index H with (double)H * dx / 2 > x0
+// smallest half-lattice index H >= 0 with (double)H * dx / 2 > x0, for a
+// finite x0 and dx > 0; INT_MAX when no index below 2^31 - 2 qualifies (the
+// threshold then selects no site).  Every half-lattice index is >= 0, so a
+// threshold below 0 is the same as 0.  At most a few loop iterations.
 static int threshold_index(double x0, double dx) {
-  double g = std::floor(2.0 * x0 / dx) - 4.0;
-  if (g < -4e9) g = -4e9;
-  long long H = (long long)g;
+  const double u = 2.0 * x0 / dx;
+  if (!(u < 2147483640.0)) return INT_MAX;
+  if (u < 0.0) return 0;
+  long long H = (long long)std::floor(u) - 4;
+  if (H < 0) H = 0;
   while (!((double)H * dx / 2.0 > x0)) ++H;
   return (int)H;
+}
+
+// the name of the first real parameter of dirac_fields that is a NaN or an
+// infinity (the field arithmetic would be undefined), or NULL
+static const char* nonfinite_field(const dirac_fields& f) {
+  const std::pair<double, const char*> v[] = {
+      {f.V0, "V0"}, {f.step_x0, "step_x0"}, {f.step_V, "step_V"}, {f.sc_Z, "sc_Z"}, {f.sc_a, "sc_a"},
+      {f.sc_center[0], "sc_center"}, {f.sc_center[1], "sc_center"}, {f.sc_center[2], "sc_center"},
+      {f.Vmod_amp, "Vmod_amp"}, {f.Vmod_omega, "Vmod_omega"}, {f.q, "q"}, {f.A_const[0], "A_const"},
+      {f.A_const[1], "A_const"}, {f.A_const[2], "A_const"}, {f.Apw_amp, "Apw_amp"}, {f.Apw_k[0], "Apw_k"},
+      {f.Apw_k[1], "Apw_k"}, {f.Apw_k[2], "Apw_k"}, {f.Apw_omega, "Apw_omega"}, {f.Apw_phase, "Apw_phase"},
+      {f.V0_imag, "V0_imag"}, {f.abs_W, "abs_W"}, {f.abs_width, "abs_width"}, {f.Alink_amp, "Alink_amp"},
+      {f.Alink_omega, "Alink_omega"}};
+  for (const auto& x : v)
+    if (!std::isfinite(x.first)) return x.second;
+  return nullptr;
 }
 
 template <class P> static typename P::Coef make_coef(double th_re, double th_im, double rx);
@@ -369,8 +390,8 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
   dirac_fields f;
   if (fields) f = *fields; else dirac_fields_default(&f);
   if (f.step_axis >= dims) return fail(nullptr, DIRAC_ERR_INVALID, "step_axis >= dims");
-  if (!std::isfinite(f.V0_imag) || !std::isfinite(f.abs_W))
-    return fail(nullptr, DIRAC_ERR_INVALID, "V0_imag and abs_W must be finite");
+  if (const char* bad = nonfinite_field(f))
+    return fail(nullptr, DIRAC_ERR_INVALID, std::string(bad) + " must be finite");
   if (f.abs_W != 0.0 && (!(f.abs_width > 0.0) || !std::isfinite(f.abs_width) || f.abs_axes <= 0 ||
                          f.abs_axes >= (1 << dims)))
     return fail(nullptr, DIRAC_ERR_INVALID,
@@ -1126,6 +1147,7 @@ extern "C" dirac_status dirac_norm(dirac_sim* s, double* E, double* naive) {
 extern "C" dirac_status dirac_partial_density(dirac_sim* s, int axis, double x0, double* out) {
   if (!s || !out) return fail(s, DIRAC_ERR_INVALID, "NULL argument");
   if (axis < 0 || axis >= s->dims) return fail(s, DIRAC_ERR_INVALID, "axis out of range");
+  if (!std::isfinite(x0)) return fail(s, DIRAC_ERR_INVALID, "x0 must be finite");
   dirac_status st = observe_any(s, axis, threshold_index(x0, s->dx[axis]));
   if (st != DIRAC_OK) return st;
   *out = s->sums_host[4];

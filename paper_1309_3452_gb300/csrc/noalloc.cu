@@ -13,7 +13,6 @@
 // loads the library holds that array until the process exits.
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "../../include/dirac.h"
 #include "kernels.cuh"
@@ -26,9 +25,6 @@ namespace {
 constexpr int kNoAllocMaxBlocks = 8192;
 static __device__ __align__(256) double g_noalloc_scratch[(kNoAllocMaxBlocks + 1) * kObsSums];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-double* g_scratch_addr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
 
 // E = naive + sum_a r_a B_a, written to the caller's output
 __global__ void combine_kernel(const double* sums, double r0, double r1, double r2, int dims,
@@ -109,26 +105,28 @@ extern "C" dirac_status dirac_norm_noalloc(int dims, const int N[3], const doubl
   if ((long long)N[0] * N[1] >= (1LL << 31)) return DIRAC_ERR_UNSUPPORTED;
   // link integrals would need a device copy of A_links (an allocation)
   if (fields && fields->A_links) return DIRAC_ERR_UNSUPPORTED;
+  dirac_fields f;
+  if (fields) f = *fields; else dirac_fields_default(&f);
+  // the parameters the functional reads: the vector potential's (as dirac_create checks them)
+  const double vals[] = {f.q, f.A_const[0], f.A_const[1], f.A_const[2], f.Apw_amp, f.Apw_k[0],
+                         f.Apw_k[1], f.Apw_k[2], f.Apw_omega, f.Apw_phase};
+  for (double v : vals)
+    if (!std::isfinite(v)) return DIRAC_ERR_INVALID;
+  if (f.Apw_amp != 0.0 && (f.Apw_pol < 0 || f.Apw_pol >= dims)) return DIRAC_ERR_INVALID;
   // the reduction grid of this size must fit the fixed scratch array
   const int blocks = observables_blocks(N, dims);
   if (blocks > kNoAllocMaxBlocks) return DIRAC_ERR_UNSUPPORTED;
 
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DIRAC_ERR_CUDA;
-  double* scratch;
+  // The host-side name of the array is not a device address: ask the runtime
+  // for the address of the current device's copy.  This allocates nothing
+  // and is done on every call, so a reset device or another context on the
+  // same ordinal never sees an address from before.
+  double* scratch = nullptr;
   {
-    // once per device, with that device current: the host-side name of the
-    // array is not a device address; ask the runtime for the real one
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return DIRAC_ERR_CUDA;
-      g_scratch_addr[dev] = static_cast<double*>(p);
-    }
-    scratch = g_scratch_addr[dev];
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return DIRAC_ERR_CUDA;
+    scratch = static_cast<double*>(p);
   }
-  dirac_fields f;
-  if (fields) f = *fields; else dirac_fields_default(&f);
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   // every reduction block overwrites its own partial slot and the final sums
   // are overwritten too, so nothing in the scratch needs clearing

@@ -700,6 +700,8 @@ int launch3d(FusedArgs<F32> a, cudaStream_t s) {
   if (a.chunk <= 0 || a.chunk > a.N[2]) a.chunk = fused_chunk(3, a.N);
   const long long items = items3d(a.N, a.chunk);
   a.workers = (int)(items < resident ? items : resident);
+  // one E partial per block: never more blocks than the partials hold
+  if (a.e_partials && a.workers > kFusedEMaxBlocks) a.workers = kFusedEMaxBlocks;
   k<<<(unsigned)a.workers, kThreads3d, kSmem3d, s>>>(a);
   return a.workers;
 }
@@ -710,7 +712,9 @@ int launch2d(FusedArgs<F32> a, cudaStream_t s) {
   const int warps = workers2d<fused2d_kernel<F32, COEF, LINK>>();
   if (a.chunk <= 0 || a.chunk > a.N[1]) a.chunk = fused_chunk(2, a.N);
   const long long items = items2d(a.N, a.chunk);
-  const long long w = items < warps ? items : warps;
+  long long w = items < warps ? items : warps;
+  // one E partial per block: never more blocks than the partials hold
+  if (a.e_partials && w > (long long)kFusedEMaxBlocks * kFused2dWarps) w = (long long)kFusedEMaxBlocks * kFused2dWarps;
   a.workers = (int)w;
   const int blocks = (int)((w + kFused2dWarps - 1) / kFused2dWarps);
   k<<<(unsigned)blocks, 32 * kFused2dWarps, 0, s>>>(a);
@@ -776,7 +780,8 @@ int launch2d_tb2(FusedArgs<F32> a, cudaStream_t s) {
   const long long strips = (a.N[0] + kCoreTb - 1) / kCoreTb;
   if (a.chunk <= 0 || a.chunk > a.N[1]) a.chunk = plan_chunk(strips, a.N[1], warps, 32, 1.0);
   const long long items = strips * ((a.N[1] + a.chunk - 1) / a.chunk);
-  const long long w = items < warps ? items : warps;
+  long long w = items < warps ? items : warps;
+  if (a.e_partials && w > (long long)kFusedEMaxBlocks * kFused2dWarps) w = (long long)kFusedEMaxBlocks * kFused2dWarps;
   a.workers = (int)w;
   const int blocks = (int)((w + kFused2dWarps - 1) / kFused2dWarps);
   k<<<(unsigned)blocks, 32 * kFused2dWarps, 0, s>>>(a);

@@ -88,6 +88,46 @@ def test_host_only_validation(lib):
                                      C.c_void_p, C.c_void_p]
     dummy = (C.c_void_p * 8)(*([16] * 8))  # never dereferenced
     assert L.dirac_norm_noalloc(3, N, dx, 0.5, 0.0, C.byref(g), D.FP32, dummy, 16, None) == D.ERR_UNSUPPORTED
+    # a non-finite Klein-step position or height is refused before any device work (a NaN
+    # threshold would otherwise never be found)
+    for name, val in (("step_x0", float("nan")), ("step_x0", float("inf")), ("step_x0", -float("inf")),
+                      ("step_V", float("nan")), ("sc_center", float("inf"))):
+        g = D.Fields()
+        L.dirac_fields_default(C.byref(g))
+        g.step_axis, g.step_x0, g.step_V = 0, 4.25, 0.5
+        if name == "sc_center":
+            g.sc_Z = 1.0
+            g.sc_center[1] = val
+        else:
+            setattr(g, name, val)
+        assert L.dirac_create(C.byref(h), 3, N, dx, 0.5, 0.0, C.byref(g), 0, 0, None) == D.ERR_INVALID
+        assert name.encode() in L.dirac_last_error(None)
+    # a huge but finite step position is accepted (no site lies beyond it)
+    g = D.Fields()
+    L.dirac_fields_default(C.byref(g))
+    g.step_axis, g.step_x0, g.step_V = 0, 1e300, 0.5
+    rc = L.dirac_create(C.byref(h), 3, N, dx, 0.5, 0.0, C.byref(g), 0, 0, None)
+    assert rc in (D.OK, D.ERR_CUDA)
+    if rc == D.OK:
+        L.dirac_destroy(h)
+        h = C.c_void_p()
+    # the allocation-free norm checks the vector potential as dirac_create does
+    for setup in ("pol", "nan_q", "inf_A", "nan_k"):
+        g = D.Fields()
+        L.dirac_fields_default(C.byref(g))
+        if setup == "pol":
+            g.Apw_amp, g.Apw_pol = 0.3, 3
+        elif setup == "nan_q":
+            g.q = float("nan")
+        elif setup == "inf_A":
+            g.A_const[2] = float("inf")
+        else:
+            g.Apw_amp, g.Apw_k[0] = 0.3, float("nan")
+        assert L.dirac_norm_noalloc(3, N, dx, 0.5, 0.0, C.byref(g), D.FP32, dummy, 16, None) == D.ERR_INVALID
+    g = D.Fields()
+    L.dirac_fields_default(C.byref(g))
+    g.Apw_amp, g.Apw_pol = 0.3, 2
+    assert L.dirac_norm_noalloc(2, N, dx, 0.5, 0.0, C.byref(g), D.FP32, dummy, 16, None) == D.ERR_INVALID
     # grids beyond the 32-bit row indexing of the kernels are refused before any device work
     big = (C.c_int * 3)(65536, 32768, 1)
     assert L.dirac_create(C.byref(h), 2, big, dx, 0.5, 0.0, None, 1, 0, None) == D.ERR_UNSUPPORTED

@@ -36,12 +36,14 @@ def device_planes(torch, prob, psi, precision, D):
     return t, (C.c_void_p * 8)(*ptrs)
 
 
-def noalloc_norm(torch, L, D, prob, ptrs, t, precision):
-    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+def noalloc_norm(torch, L, D, prob, ptrs, t, precision, out=None):
+    if out is None:
+        out = torch.zeros(2, dtype=torch.float64, device="cuda")
     N = (C.c_int * 3)(*[int(v) for v in (list(prob.N) + [1, 1, 1])[:3]])
     dx = (C.c_double * 3)(*[float(v) for v in (list(prob.dx) + [1.0] * 3)[:3]])
     stream = torch.cuda.current_stream()
-    rc = L.dirac_norm_noalloc(prob.dims, N, dx, prob.dt, t, None, precision, ptrs, out.data_ptr(),
+    fs, _ = D._fields_struct(prob.fields)
+    rc = L.dirac_norm_noalloc(prob.dims, N, dx, prob.dt, t, C.byref(fs), precision, ptrs, out.data_ptr(),
                               stream.cuda_stream)
     assert rc == D.OK
     stream.synchronize()
@@ -71,6 +73,54 @@ def test_noalloc_norm_matches_dirac_norm_twice(env, dims, precision):
             assert abs(E - E_ref) <= tol * abs(E_ref)
             assert abs(naive - naive_ref) <= tol * naive_ref
             s.step(13)
+
+
+@pytest.mark.parametrize("field", ["A_const", "plane_wave"])
+def test_noalloc_norm_with_vector_potentials(env, field):
+    """The constant-link and per-site plane-wave branches of the functional,
+    against dirac_norm on the same state (FP64: the same reduction, 1e-13)."""
+    torch, D, L = env
+    prob = W.Problem(3, (20, 17, 22), (1.0, 1.0, 1.0), 0.9 * W.stability_limit(3), 0.6)
+    if field == "A_const":
+        prob = prob.with_fields(q=1.0, A_const=(0.21, -0.13, 0.08))
+    else:  # a moving plane wave: the functional reads its link phases at t - dt/2
+        k = 2 * np.pi / 22.0
+        prob = prob.with_fields(q=1.0, Apw_amp=0.4, Apw_k=(0.0, 0.0, k), Apw_omega=k, Apw_phase=0.3,
+                                Apw_pol=0)
+    psi = W.random_state(prob, 37)
+    with D.Sim(prob, D.FP64) as s:
+        s.set_spinor(psi)
+        s.step(7)  # t != 0: the link time matters for the plane wave
+        for _ in range(2):
+            E_ref, naive_ref = s.norm()
+            tstate, ptrs = device_planes(torch, prob, s.get_spinor(), D.FP64, D)
+            E, naive = noalloc_norm(torch, L, D, prob, ptrs, s.time, D.FP64)
+            del tstate
+            assert abs(E - E_ref) <= 1e-13 * abs(E_ref)
+            assert abs(naive - naive_ref) <= 1e-13 * naive_ref
+            s.step(5)
+
+
+def test_noalloc_calls_allocate_nothing(env):
+    """After one warm call, further calls leave the device's free memory and
+    the caching allocator's reserved bytes unchanged."""
+    torch, D, L = env
+    prob = W.Problem(3, (24, 20, 18), (1.0, 1.0, 1.0), 0.9 * W.stability_limit(3), 0.5)
+    psi = W.random_state(prob, 41)
+    tstate, ptrs = device_planes(torch, prob, psi, D.FP32, D)
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    first = noalloc_norm(torch, L, D, prob, ptrs, 0.0, D.FP32, out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    reserved0 = torch.cuda.memory_reserved()
+    for _ in range(5):
+        again = noalloc_norm(torch, L, D, prob, ptrs, 0.0, D.FP32, out)
+        assert np.array_equal(again, first)  # same state, same scratch, same order
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_reserved() == reserved0
+    del tstate
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch(env):
