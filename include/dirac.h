@@ -47,6 +47,15 @@
  * and dirac_set_spinor(_device) only enqueue work; dirac_norm,
  * dirac_partial_density, dirac_get_spinor, dirac_check, dirac_autotune and
  * dirac_set_plan synchronise the stream before returning.
+ *
+ * Environment switches (read when the call runs; for comparisons and tests,
+ * results stay within the FP32 tolerances):
+ *   DIRAC_NO_GRAPHS             step loops as plain launches, no CUDA graphs
+ *   DIRAC_NO_FUSED_NORM         dirac_norm always reduces the stored state
+ *   DIRAC_NO_TEMPORAL_BLOCKING  (2+1)D FP32: one time step per pass
+ *   DIRAC_SOFTCORE_TABLE        (read by dirac_create) FP32 soft core through
+ *                               a per-site coefficient table instead of the
+ *                               per-value compensated evaluation
  * ---------------------------------------------------------------------------
  */
 #ifndef DIRAC_H

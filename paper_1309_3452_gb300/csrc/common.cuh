@@ -83,6 +83,13 @@ struct F32 {
   struct Ratio { float hi, lo; };
   struct Link { float2 hi, lo; };
 };
+// A plane-wave link factor exp(-i phi) = c - i s of the FP32 kernels' per-step
+// table (c = c_hi + c_lo, s = s_hi + s_lo), kept as the packed operand pairs
+// of plane_link_diff: ch = (c_hi, c_hi), cl = (c_lo, c_lo), sh = (s_hi, -s_hi),
+// sl = (s_lo, -s_lo)
+struct PlaneLink32 {
+  float2 ch, cl, sh, sl;
+};
 
 __device__ __forceinline__ double2 cmk(double a, double b) { return make_double2(a, b); }
 __device__ __forceinline__ float2 cmk(float a, float b) { return make_float2(a, b); }
@@ -241,6 +248,19 @@ __device__ __forceinline__ float2 apply(const F32::Coef& c, float2 F, float2 S) 
 }
 
 // ------------------------------------------------------------------ fields
+// copies of 8 or 16 bytes from global to shared memory that bypass the
+// registers (cp.async; completion by cp_async_wait_all of the issuing thread)
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // COEF_TABLE: a time-independent scalar potential (soft core, static array,
 // with V0 and a Klein step) whose coefficient b = 1/(1 + i theta), theta =
 // dt (beta m + V)/2, is tabulated per site at creation, in FP64 rounded to a
@@ -250,9 +270,16 @@ __device__ __forceinline__ float2 apply(const F32::Coef& c, float2 F, float2 S) 
 // LINK_TABLE: any other time-independent vector potential (FP32 kernels): the
 // factors exp(-i phi) of every value's up and down link per axis, formed once
 // in FP64 from the same phases as the per-site path and kept as hi + lo
-// pairs.  GENERAL: per-site FP64.
-enum CoefMode { COEF_UNIFORM = 0, COEF_STEP = 1, COEF_GENERAL = 2, COEF_TABLE = 3 };
+// pairs.  GENERAL: per-site FP64.  COEF_SOFTCORE (FP32 kernels): a soft-core
+// potential (with V0 and a Klein step, real) whose b is computed per value
+// in compensated FP32 from |x - c|^2 + a^2, itself summed from three small
+// per-axis tables of (X dx_a/2 - c_a)^2 (no per-site data).
+enum CoefMode { COEF_UNIFORM = 0, COEF_STEP = 1, COEF_GENERAL = 2, COEF_TABLE = 3, COEF_SOFTCORE = 4 };
 enum LinkMode { LINK_NONE = 0, LINK_CONST = 1, LINK_GENERAL = 2, LINK_PLANE = 3, LINK_TABLE = 4 };
+// Kernel-side specialisation of LINK_PLANE in the fused (3+1)D kernel: the
+// wave travels along z and is polarised along x; the kernel stages the link
+// factors of each z level and passes them in (never a simulation's link_mode)
+constexpr int LINK_PLANE_ZX = 5;
 
 // Analytic field description, FP64, for the per-site (general) paths.
 struct FieldDesc {
@@ -363,44 +390,102 @@ __device__ __forceinline__ double link_phase_site(const FieldDesc& f, int dims, 
   return phi;
 }
 
-// ------------------------------------------------------------------ double-float
-// Unevaluated sums hi + lo of two floats, with error-free transformations:
-// TwoSum (Knuth, TAOCP vol. 2), FastTwoSum and TwoProduct via FMA (Dekker
-// 1971; Ogita, Rump, Oishi 2005).  About 44 significant bits.
-struct DF {
-  float hi, lo;
+// ------------------------------------------------------------------ compensated pairs
+// Unevaluated sums hi + lo of two floats, two independent values at a time
+// (lane .x and lane .y of each float2, packed instructions).  The error-free
+// transformations are TwoSum (Knuth, TAOCP vol. 2, Sect. 4.2.2) and
+// TwoProduct by FMA (Ogita, Rump, Oishi, SIAM J. Sci. Comput. 26, 2005).
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 pneg(float2 a) { return make_float2(-a.x, -a.y); }
+// s + e = a + b exactly
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = padd(a, b);
+  const float2 bb = psub(s, a);
+  e = padd(psub(a, psub(s, bb)), psub(b, bb));
+}
+__device__ __forceinline__ float2 rsqrt2(float2 v) {
+  float2 r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(v.x));
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(v.y));
+  return r;
+}
+__device__ __forceinline__ float2 rcp2(float2 v) {
+  float2 r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(v.x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(v.y));
+  return r;
+}
+
+// Cayley coefficient b = 1/(1 + i theta) of a soft-core potential, for two
+// values at once (lanes), in compensated FP32:
+//   theta = th0 + K / sqrt(R),   R = Rh + Rl > 0,  th0 = t0h + t0l,  K = Kh + Kl
+// (K = -dt Z/2 for V = -Z/sqrt(|x - c|^2 + a^2), R = |x - c|^2 + a^2, th0 =
+// dt (beta m + V0 [+ V_step])/2).  1/sqrt(R) is the hardware estimate refined
+// by one Newton step y0 + y0 (1 - R y0^2)/2 whose residual is formed exactly
+// (TwoProduct), b = (1 - i theta)/(1 + theta^2) with the reciprocal refined
+// likewise.  Result: b = (re_hi + re_lo) + i (im_hi + im_lo), relative error
+// ~1e-13 for |theta| < 1, so |2b - 1| = 1 to that accuracy.
+struct SoftB2 {
+  float2 re_hi, re_lo, im_hi, im_lo;
 };
-__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {  // |a| >= |b|
-  const float s = radd(a, b);
-  return DF{s, rsub(b, rsub(s, a))};
+__device__ __forceinline__ SoftB2 softcore_b2(float2 Rh, float2 Rl, float2 t0h, float2 t0l, float Kh,
+                                              float Kl) {
+  // y = 1/sqrt(R) as y0 + yl
+  const float2 y0 = rsqrt2(Rh);
+  const float2 ph = pmul(y0, y0);
+  const float2 pl = pfma(y0, y0, pneg(ph));
+  const float2 qh = pmul(Rh, ph);
+  const float2 qe = pfma(Rh, ph, pneg(qh));
+  float2 e = psub(psub(f2(1.0f), qh), qe);       // 1 - qh is exact (qh ~ 1)
+  e = pfma(pneg(Rh), pl, e);
+  e = pfma(pneg(Rl), ph, e);                     // e = 1 - R y0^2
+  const float2 yl = pmul(pmul(f2(0.5f), y0), e);
+  // t = K y
+  const float2 th = pmul(f2(Kh), y0);
+  float2 tl = pfma(f2(Kh), y0, pneg(th));
+  tl = pfma(f2(Kh), yl, tl);
+  tl = pfma(f2(Kl), y0, tl);
+  // theta = th0 + t
+  float2 ah, ae;
+  two_sum2(t0h, th, ah, ae);
+  const float2 al = padd(ae, padd(t0l, tl));
+  // D = 1 + theta^2
+  const float2 sh = pmul(ah, ah);
+  float2 sl = pfma(ah, ah, pneg(sh));
+  sl = pfma(padd(ah, ah), al, sl);
+  float2 dh, de;
+  two_sum2(f2(1.0f), sh, dh, de);
+  const float2 dl = padd(de, sl);
+  // 1/D as r0 + rl
+  const float2 r0 = rcp2(dh);
+  float2 g = pfma(pneg(dh), r0, f2(1.0f));
+  g = pfma(pneg(dl), r0, g);
+  const float2 rl = pmul(r0, g);
+  // b = (1 - i theta)/D
+  const float2 mh = pmul(ah, r0);
+  float2 ml = pfma(ah, r0, pneg(mh));
+  ml = pfma(ah, rl, ml);
+  ml = pfma(al, r0, ml);
+  return SoftB2{r0, rl, pneg(mh), pneg(ml)};
 }
-__device__ __forceinline__ DF df_two_sum(float a, float b) {
-  const float s = radd(a, b);
-  const float bb = rsub(s, a);
-  return DF{s, radd(rsub(a, rsub(s, bb)), rsub(b, bb))};
+// one value's coefficient {re hi, re lo, im hi, im lo} from a lane of a pair
+__device__ __forceinline__ float4 lane_b(const SoftB2& b, int lane) {
+  return lane ? make_float4(b.re_hi.y, b.re_lo.y, b.im_hi.y, b.im_lo.y)
+              : make_float4(b.re_hi.x, b.re_lo.x, b.im_hi.x, b.im_lo.x);
 }
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-  const DF s = df_two_sum(a.hi, b.hi);
-  return df_fast_two_sum(s.hi, radd(s.lo, radd(a.lo, b.lo)));
-}
-__device__ __forceinline__ DF df_mul(DF a, DF b) {
-  const float p = rmul(a.hi, b.hi);
-  const float e = rfma(a.hi, b.hi, -p);
-  return df_fast_two_sum(p, rfma(a.hi, b.lo, rfma(a.lo, b.hi, e)));
-}
-__device__ __forceinline__ DF df_mulf(DF a, float b) {
-  const float p = rmul(a.hi, b);
-  const float e = rfma(a.hi, b, -p);
-  return df_fast_two_sum(p, rfma(a.lo, b, e));
-}
-// 1/q for q >= 1: the hardware estimate (rcp.approx, within one ulp) plus one
-// Newton step y + y (1 - q y) on the residual formed in double-float
-__device__ __forceinline__ DF df_rcp(DF q) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(q.hi));
-  const DF qy = df_mulf(q, y);
-  const float r = radd(rsub(1.0f, qy.hi), -qy.lo);    // 1 - q y (small)
-  return df_fast_two_sum(y, rmul(y, r));
+
+// F+ = b (2F - S) - F with S = r_x S' (Eqs. ss1-ss4 in the Cayley form with
+// b = 1/(1 + i theta)); b = {re hi, re lo, im hi, im lo}, r_x = rxh + rxl
+__device__ __forceinline__ float2 apply_b(float4 b, float rxh, float rxl, float2 F, float2 S) {
+  // w = 2F - r_x S'  (small product first)
+  const float2 w = pfma(f2(-rxh), S, pfma(f2(-rxl), S, padd(F, F)));
+  // b w = re(b) (wx, wy) + im(b) (-wy, wx), small (lo) products first
+  const float2 ws = make_float2(w.y, w.x);
+  float2 t = pmul(f2(b.y), w);
+  t = pfma(make_float2(-b.w, b.w), ws, t);
+  t = pfma(make_float2(-b.z, b.z), ws, t);
+  t = pfma(f2(b.x), w, t);
+  return psub(t, F);
 }
 
 // ------------------------------------------------------------------ site update
@@ -452,10 +537,20 @@ struct HalfFields {
   // per plane (cell index as in the state), and r_x as hi + lo
   const float4* b_tab[8];
   float rx_hi, rx_lo;
-  // LINK_PLANE: table of exp(-i phi) for this half-step, indexed by the
-  // half-lattice coordinate along ltab_axis; applies on axis lpol only
-  const typename P::Link* ltab;
+  // LINK_PLANE: table of the link factors exp(-i phi) for this half-step,
+  // indexed by the half-lattice coordinate along ltab_axis; applies on axis
+  // lpol only (FP64 kernels: F64::Link; FP32 kernels: PlaneLink32)
+  const void* ltab;
   int ltab_axis, lpol;
+  // COEF_SOFTCORE: theta_0 = dt (beta m + V0)/2 before the Klein step
+  // (sc_t0[0]) and beyond it (sc_t0[1]) as (hi, lo); K = -dt Z/2 as hi + lo;
+  // per-axis tables sc_sq[a][X] = (X dx_a/2 - c_a)^2 (+ a^2 on axis 0) as
+  // (hi, lo) for X in [0, 2 N_a), every hi a multiple of one power of two so
+  // that sums of hi parts are exact in FP32
+  float2 sc_t0[2];
+  int sc_step;              // a Klein step is present (else sc_t0[0] everywhere)
+  float sc_K_hi, sc_K_lo;
+  const float2* sc_sq[3];
   // LINK_TABLE: link factors [(2 axis + dir) * larr_n + plane * larr_ps + site],
   // dir 0 = the value's own link upwards, 1 = the link from its lower
   // neighbour (applied conjugated, like the per-site path)
@@ -491,6 +586,83 @@ __device__ __forceinline__ float2 apply_table<F32>(const HalfFields<F32>& h, flo
   return psub(make_float2(re, im), F);
 }
 
+// LINK_PLANE difference along the polarisation, both neighbours sharing the
+// link factor L = exp(-i phi) (the wave vector is perpendicular to the link):
+//   L up - conj(L) dn = c (up - dn) - i s (up + dn),  L = c - i s
+__device__ __forceinline__ double2 plane_link_diff(const F64::Link& L, double2 up, double2 dn) {
+  return csub(link_mul(L, up), link_mulc(L, dn));
+}
+__device__ __forceinline__ float2 plane_link_diff(const PlaneLink32& L, float2 up, float2 dn) {
+  const float2 D = psub(up, dn), Q = padd(up, dn);
+  const float2 Qs = make_float2(Q.y, Q.x);
+  // -i s Q = s (Q.y, -Q.x); small (lo) products first
+  float2 t = pmul(L.cl, D);
+  t = pfma(L.sl, Qs, t);
+  t = pfma(L.sh, Qs, t);
+  return pfma(L.ch, D, t);
+}
+template <class P> struct PlaneLinkOf { using type = F64::Link; };
+template <> struct PlaneLinkOf<F32> { using type = PlaneLink32; };
+
+// R = |x - c|^2 + a^2 of the value at half-lattice point H as (hi, lo):
+// the hi parts add exactly, the lo parts in FP32 (same order everywhere)
+template <int DIMS, class P>
+__device__ __forceinline__ void softcore_R(const HalfFields<P>& h, const int (&H)[3], float& Rh, float& Rl) {
+  float2 r = padd(__ldg(h.sc_sq[0] + H[0]), __ldg(h.sc_sq[1] + H[1]));
+  if (DIMS == 3) r = padd(r, __ldg(h.sc_sq[2] + H[2]));
+  Rh = r.x;
+  Rl = r.y;
+}
+// theta_0 of the value: beyond the Klein step (if any) or before it
+template <class P>
+__device__ __forceinline__ float2 softcore_t0(const HalfFields<P>& h, const int (&H)[3]) {
+  if (!h.sc_step) return h.sc_t0[0];
+  const int hs = h.step_axis == 0 ? H[0] : (h.step_axis == 1 ? H[1] : H[2]);
+  return hs >= h.step_X ? h.sc_t0[1] : h.sc_t0[0];
+}
+
+// COEF_SOFTCORE update (FP32 only): b of this value from the caller's pair
+// computation (bpre) or computed here (both lanes the same value, so the
+// result is bit-identical to the value's lane of a pair)
+template <int DIMS, class P>
+__device__ __forceinline__ typename P::cplx apply_softcore(const HalfFields<P>& h, typename P::cplx F,
+                                                           typename P::cplx S, const int (&H)[3],
+                                                           const float4* bpre);
+template <>
+__device__ __forceinline__ double2 apply_softcore<2, F64>(const HalfFields<F64>&, double2 F, double2,
+                                                          const int (&)[3], const float4*) {
+  return F;  // not used: FP64 kernels take the general path
+}
+template <>
+__device__ __forceinline__ double2 apply_softcore<3, F64>(const HalfFields<F64>&, double2 F, double2,
+                                                          const int (&)[3], const float4*) {
+  return F;
+}
+template <int DIMS>
+__device__ __forceinline__ float2 apply_softcore_f32(const HalfFields<F32>& h, float2 F, float2 S,
+                                                     const int (&H)[3], const float4* bpre) {
+  float4 b;
+  if (bpre) {
+    b = *bpre;
+  } else {
+    float Rh, Rl;
+    softcore_R<DIMS>(h, H, Rh, Rl);
+    const float2 t0 = softcore_t0(h, H);
+    b = lane_b(softcore_b2(f2(Rh), f2(Rl), f2(t0.x), f2(t0.y), h.sc_K_hi, h.sc_K_lo), 0);
+  }
+  return apply_b(b, h.rx_hi, h.rx_lo, F, S);
+}
+template <>
+__device__ __forceinline__ float2 apply_softcore<2, F32>(const HalfFields<F32>& h, float2 F, float2 S,
+                                                         const int (&H)[3], const float4* bpre) {
+  return apply_softcore_f32<2>(h, F, S, H, bpre);
+}
+template <>
+__device__ __forceinline__ float2 apply_softcore<3, F32>(const HalfFields<F32>& h, float2 F, float2 S,
+                                                         const int (&H)[3], const float4* bpre) {
+  return apply_softcore_f32<3>(h, F, S, H, bpre);
+}
+
 // Field-path selectors for site_update: a fixed CoefMode / LinkMode compiles
 // only that path; kAnyMode reads h.coef_mode / h.link_mode at run time and
 // includes the per-site FP64 (general) paths.
@@ -506,7 +678,8 @@ template <class P, int DIMS, int COEF, int LINK>
 __device__ __forceinline__ typename P::cplx site_update(
     const HalfFields<P>& h, const FieldDesc& f, bool iso, const typename P::Ratio& ry,
     const typename P::Ratio& rz, int plane, typename P::cplx F, typename P::cplx (&nb)[6],
-    const int (&H)[3], long long site, long long pstride, typename P::cplx* S_out = nullptr) {
+    const int (&H)[3], long long site, long long pstride, typename P::cplx* S_out = nullptr,
+    const float4* bpre = nullptr, const typename PlaneLinkOf<P>::type* lk = nullptr) {
   using C = typename P::cplx;
   const int link = LINK == kAnyMode ? h.link_mode : LINK;
   const int coef = COEF == kAnyMode ? h.coef_mode : COEF;
@@ -517,13 +690,6 @@ __device__ __forceinline__ typename P::cplx site_update(
     if (link == LINK_CONST) {
       up = link_mul(h.L[ax], up);
       dn = link_mulc(h.L[ax], dn);
-    } else if (LINK == LINK_PLANE) {
-      if (ax == h.lpol) {
-        const int hk = h.ltab_axis == 0 ? H[0] : (h.ltab_axis == 1 ? H[1] : H[2]);
-        const typename P::Link U = h.ltab[hk];
-        up = link_mul(U, up);
-        dn = link_mulc(U, dn);
-      }
     } else if (link == LINK_TABLE) {
       const long long i = (long long)plane * h.larr_ps + site;
       up = link_mul(h.larr[(2 * ax) * h.larr_n + i], up);
@@ -536,6 +702,24 @@ __device__ __forceinline__ typename P::cplx site_update(
     }
     d[ax] = csub(up, dn);
   }
+  if constexpr (LINK == LINK_PLANE_ZX) {
+    d[0] = plane_link_diff(*lk, nb[0], nb[1]);  // the factor of the value's z level, staged by the caller
+  }
+  if constexpr (LINK == LINK_PLANE) {
+    // the difference along the polarisation with the shared link factor of the
+    // value's neighbours: staged by the caller (lk), or from the step's table
+    using PL = typename PlaneLinkOf<P>::type;
+    PL L;
+    if (lk) {
+      L = *lk;
+    } else {
+      const int hk = h.ltab_axis == 0 ? H[0] : (h.ltab_axis == 1 ? H[1] : H[2]);
+      L = static_cast<const PL*>(h.ltab)[hk];
+    }
+    if (h.lpol == 0) d[0] = plane_link_diff(L, nb[0], nb[1]);
+    else if (h.lpol == 1) d[1] = plane_link_diff(L, nb[2], nb[3]);
+    else if (DIMS == 3) d[2] = plane_link_diff(L, nb[4], nb[5]);
+  }
   if (DIMS == 2) d[2] = d[0];
   const C S = combine<P, DIMS>(d[0], d[1], d[2], sign_class<DIMS>(plane), iso, ry, rz);
   if (S_out) *S_out = S;  // the difference part S' (S = r_x S'), for the conserved functional
@@ -545,6 +729,7 @@ __device__ __forceinline__ typename P::cplx site_update(
     return hs >= h.step_X ? apply(h.c_out, F, S) : apply(h.c_in, F, S);
   }
   if (coef == COEF_TABLE) return apply_table(h, F, S, plane, site);
+  if (coef == COEF_SOFTCORE) return apply_softcore<DIMS>(h, F, S, H, bpre);
   double V = potential_at(f, DIMS, H[0], H[1], H[2], site, pstride, plane, h.t);
   double th = f.dt * (h.beta * f.m + V) * 0.5;
   double th_im = f.dt * potential_imag_at(f, DIMS, H[0], H[1], H[2]) * 0.5;

@@ -1,4 +1,5 @@
 // Host side of libdirac: the C ABI declared in include/dirac.h.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -36,6 +37,7 @@ struct dirac_sim {
   double2* staging = nullptr; // one canonical plane (FP32 conversions)
   double* Vstatic = nullptr;  // one real per site (plane-major, pstride)
   float4* b_tab = nullptr;    // COEF_TABLE: b = 1/(1 + i theta) per site as hi + lo (plane-major, pstride)
+  float2* sc_sq = nullptr;    // COEF_SOFTCORE: (X dx_a/2 - c_a)^2 per axis and half-lattice index, hi + lo
   double* Alink = nullptr;    // link integrals x q: 2 dims slots (up, down link per axis) of np * pstride
   F32::Link* larr = nullptr;  // LINK_TABLE: link factors, same slots, FP32 hi + lo
   double* partials = nullptr;
@@ -186,6 +188,38 @@ template <> F32::Link make_link<F32>(double phi) {
   return L;
 }
 
+// COEF_SOFTCORE tables: for every axis a and half-lattice index X in
+// [0, 2 N_a), (X dx_a/2 - c_a)^2 (plus a^2 on axis 0) in FP64, stored as a
+// float hi part rounded to a multiple of q and the float lo rest.  q is the
+// power of two 2^(e - 22), 2^e >= the largest possible R = a^2 + sum_a max
+// (..)^2, so every hi part is below 2^22 q and any sum of three of them is
+// exact in FP32; only the lo parts (|lo| <= q/2) round.  Axes beyond dims
+// get one zero entry per index.
+static void softcore_tables(const dirac_sim* s, std::vector<float2>& out) {
+  double rmax = s->f.sc_a * s->f.sc_a;
+  for (int a = 0; a < s->dims; ++a) {
+    double m = 0.0;
+    for (long long X = 0; X < 2LL * s->N[a]; ++X) {
+      const double d = (double)X * s->dx[a] * 0.5 - s->f.sc_center[a];
+      m = std::max(m, d * d);
+    }
+    rmax += m;
+  }
+  const double q = std::ldexp(1.0, std::ilogb(rmax) + 1 - 22);
+  out.clear();
+  for (int a = 0; a < 3; ++a) {
+    for (long long X = 0; X < 2LL * s->N[a]; ++X) {
+      double v = 0.0;
+      if (a < s->dims) {
+        const double d = (double)X * s->dx[a] * 0.5 - s->f.sc_center[a];
+        v = d * d + (a == 0 ? s->f.sc_a * s->f.sc_a : 0.0);
+      }
+      const double hi = std::nearbyint(v / q) * q;
+      out.push_back(make_float2((float)hi, (float)(v - hi)));
+    }
+  }
+}
+
 static FieldDesc field_desc(const dirac_sim* s) {
   FieldDesc d;
   std::memset(&d, 0, sizeof(d));
@@ -250,13 +284,29 @@ static HalfFields<P> half_fields(const dirac_sim* s, bool upper, double t) {
   // tabulated potential
   for (int k = 0; k < 8; ++k) h.b_tab[k] = s->b_tab && k < s->np ? s->b_tab + (long long)k * s->pstride : nullptr;
   split(rx, h.rx_hi, h.rx_lo);
+  // analytic soft core: theta_0 on both sides of the Klein step, K = -dt Z/2
+  // and the per-axis square tables (axis a at offset 2 (N_0 + ... + N_{a-1}))
+  {
+    const double t_in = s->dt * (beta * s->m + s->f.V0) / 2.0;
+    const double t_out = s->f.step_axis >= 0 ? s->dt * (beta * s->m + s->f.V0 + s->f.step_V) / 2.0 : t_in;
+    split(t_in, h.sc_t0[0].x, h.sc_t0[0].y);
+    split(t_out, h.sc_t0[1].x, h.sc_t0[1].y);
+    h.sc_step = s->f.step_axis >= 0;
+    split(-s->dt * s->f.sc_Z / 2.0, h.sc_K_hi, h.sc_K_lo);
+    long long off = 0;
+    for (int a = 0; a < 3; ++a) {
+      h.sc_sq[a] = s->sc_sq ? s->sc_sq + off : nullptr;
+      off += 2LL * s->N[a];
+    }
+  }
   if (s->link_mode == LINK_TABLE) {
     h.larr = reinterpret_cast<const typename P::Link*>(s->larr);
     h.larr_n = (long long)s->np * s->pstride;
     h.larr_ps = s->pstride;
   }
   if (s->link_mode == LINK_PLANE) {
-    h.ltab = static_cast<typename P::Link*>(s->ltab) + (upper ? 0 : s->ltab_n);
+    h.ltab = static_cast<const char*>(s->ltab) +
+             (upper ? 0 : (size_t)s->ltab_n * sizeof(typename PlaneLinkOf<P>::type));
     h.ltab_axis = s->ltab_axis;
     h.lpol = s->f.Apw_pol;
   }
@@ -425,7 +475,12 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
   // kernels, evaluated per site in FP64 otherwise
   const bool vstatic = fields && fields->V_static;
   const bool layers = f.abs_W != 0.0;
-  if ((vstatic && f.Vmod_amp == 0.0) || (!vstatic && (f.sc_Z != 0.0 || layers)))
+  // a real soft core (with V0 and a Klein step, nothing else): analytic per
+  // value in the FP32 kernels, no per-site data
+  const bool softcore = f.sc_Z != 0.0 && f.sc_a != 0.0 && !vstatic && !layers && f.V0_imag == 0.0;
+  if (precision == DIRAC_FP32 && softcore && std::getenv("DIRAC_SOFTCORE_TABLE") == nullptr)
+    s->coef_mode = COEF_SOFTCORE;
+  else if ((vstatic && f.Vmod_amp == 0.0) || (!vstatic && (f.sc_Z != 0.0 || layers)))
     s->coef_mode = precision == DIRAC_FP32 ? COEF_TABLE : COEF_GENERAL;
   else if (vstatic || f.sc_Z != 0.0) s->coef_mode = COEF_GENERAL;
   else s->coef_mode = f.step_axis >= 0 ? COEF_STEP : COEF_UNIFORM;
@@ -513,6 +568,15 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
     if ((e = cudaGetLastError()) != cudaSuccess) return cleanup_fail(cuda_fail(s, e, "link factor table"));
     s->launches += 1;
   }
+  if (s->coef_mode == COEF_SOFTCORE) {
+    std::vector<float2> sq;
+    softcore_tables(s, sq);
+    if ((e = cudaMalloc(&s->sc_sq, sq.size() * sizeof(float2))) != cudaSuccess)
+      return cleanup_fail(cuda_fail(s, e, "cudaMalloc(soft-core tables)"));
+    // synchronous: the host vector goes out of scope
+    if ((e = cudaMemcpy(s->sc_sq, sq.data(), sq.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cleanup_fail(cuda_fail(s, e, "cudaMemcpy(soft-core tables)"));
+  }
   if (s->coef_mode == COEF_TABLE) {
     if ((e = cudaMalloc(&s->b_tab, (size_t)s->np * s->pstride * sizeof(float4))) != cudaSuccess)
       return cleanup_fail(cuda_fail(s, e, "cudaMalloc(coefficient table)"));
@@ -521,7 +585,8 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
     s->launches += 1;
   }
   if (s->link_mode == LINK_PLANE) {
-    size_t tb = (size_t)2 * s->ltab_n * (precision == DIRAC_FP32 ? sizeof(F32::Link) : sizeof(F64::Link));
+    size_t tb = (size_t)2 * s->ltab_n * (precision == DIRAC_FP32 ? sizeof(PlaneLinkOf<F32>::type)
+                                                                 : sizeof(PlaneLinkOf<F64>::type));
     if ((e = cudaMalloc(&s->ltab, tb)) != cudaSuccess) return cleanup_fail(cuda_fail(s, e, "cudaMalloc(link table)"));
   }
   if (s->fused) {
@@ -565,6 +630,7 @@ extern "C" void dirac_destroy(dirac_sim* s) {
   cudaFree(s->staging);
   cudaFree(s->Vstatic);
   cudaFree(s->b_tab);
+  cudaFree(s->sc_sq);
   cudaFree(s->Alink);
   cudaFree(s->larr);
   cudaFree(s->ltab);
@@ -673,8 +739,8 @@ static bool time_dependent_fields(const dirac_sim* s) {
 template <class P>
 static void link_table(dirac_sim* s, double t, cudaStream_t st) {
   if (s->link_mode != LINK_PLANE) return;
-  launch_link_table<P>(static_cast<typename P::Link*>(s->ltab), s->ltab_n, field_desc(s), s->dims,
-                       s->ltab_axis, s->f.Apw_pol, t, t + s->dt / 2.0, st);
+  launch_link_table<P>(s->ltab, s->ltab_n, field_desc(s), s->dims, s->ltab_axis, s->f.Apw_pol, t,
+                       t + s->dt / 2.0, st);
   s->launches += 1;
 }
 
@@ -1222,9 +1288,10 @@ extern "C" dirac_status dirac_autotune(dirac_sim* s, dirac_plan* out) {
   const int n1 = fused_candidates(s->dims, s->N, 0, c1, kCandidates);
   const bool tb_ok = s->dims == 2 && !time_dependent_fields(s) &&
                      (s->coef_mode == COEF_UNIFORM || s->coef_mode == COEF_STEP ||
-                      s->coef_mode == COEF_TABLE) &&
+                      s->coef_mode == COEF_TABLE || s->coef_mode == COEF_SOFTCORE) &&
                      (s->link_mode == LINK_NONE || s->link_mode == LINK_CONST) &&
-                     !(s->coef_mode == COEF_TABLE && s->link_mode == LINK_CONST);
+                     !((s->coef_mode == COEF_TABLE || s->coef_mode == COEF_SOFTCORE) &&
+                       s->link_mode == LINK_CONST);
   const int n2 = tb_ok ? fused_candidates(2, s->N, 1, c2, kCandidates) : 0;
   link_table<F32>(s, sim_time(s), s->stream);  // plane-wave links of the current step, if any
   cudaEvent_t e0, e1;

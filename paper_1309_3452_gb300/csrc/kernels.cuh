@@ -106,10 +106,11 @@ void launch_finish_sums(const double* partials, int nblocks, double* out, cudaSt
 void launch_finish_sums2(const double* partials, int nblocks, double* out, cudaStream_t s);
 
 // table of plane-wave link factors exp(-i phi) for both half-steps of one time
-// step: tab[half * n + H], H = half-lattice coordinate along `axis`, n = 2 N_axis
+// step: tab[half * n + H], H = half-lattice coordinate along `axis`, n = 2 N_axis;
+// elements of PlaneLinkOf<P>::type
 template <class P>
-void launch_link_table(typename P::Link* tab, int n, const FieldDesc& f, int dims, int axis, int pol,
-                       double t_up, double t_lo, cudaStream_t s);
+void launch_link_table(void* tab, int n, const FieldDesc& f, int dims, int axis, int pol, double t_up,
+                       double t_lo, cudaStream_t s);
 
 // coefficient table of a time-independent potential (COEF_TABLE): every
 // plane of the state layout (pstride), b = 1/(1 + i dt (beta m + V)/2) as

@@ -134,16 +134,32 @@ __global__ void finish_sums2_kernel(const double* partials, int nblocks, double*
   if (lane == 0) out[k] = x;
 }
 
+// exp(-i phi) in the plane-wave table's element type: F64::Link, or for the
+// FP32 kernels c - i s as hi + lo pairs of cos phi and sin phi
+__device__ __forceinline__ void plane_link_from(double phi, F64::Link* out) {
+  *out = link_from(phi, (F64*)nullptr);
+}
+__device__ __forceinline__ void plane_link_from(double phi, PlaneLink32* out) {
+  double sn, cs;
+  sincos(phi, &sn, &cs);
+  const float ch = __double2float_rn(cs), sh = __double2float_rn(sn);
+  const float cl = __double2float_rn(cs - (double)ch), sl = __double2float_rn(sn - (double)sh);
+  out->ch = make_float2(ch, ch);
+  out->cl = make_float2(cl, cl);
+  out->sh = make_float2(sh, -sh);
+  out->sl = make_float2(sl, -sl);
+}
+
 template <class P>
-__global__ void link_table_kernel(typename P::Link* tab, int n, const FieldDesc f, int dims, int axis,
-                                  int pol, double t_up, double t_lo) {
+__global__ void link_table_kernel(typename PlaneLinkOf<P>::type* tab, int n, const FieldDesc f, int dims,
+                                  int axis, int pol, double t_up, double t_lo) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 2 * n) return;
   const int half = i / n;
   long long HH[3] = {0, 0, 0};
   HH[axis] = i - half * n;
-  // the same phase function and conversion as the per-link FP64 path
-  tab[i] = link_from(link_phase(f, dims, HH, pol, +1, half ? t_lo : t_up), (P*)nullptr);
+  // the same phase function as the per-link FP64 path
+  plane_link_from(link_phase(f, dims, HH, pol, +1, half ? t_lo : t_up), tab + i);
 }
 
 // b = 1/(1 + i theta), theta = dt (beta m + V)/2 with V complex, of every site
@@ -265,14 +281,13 @@ template void launch_observables<F32, 2>(const ObsArgs<F32>&, int, cudaStream_t)
 template void launch_observables<F32, 3>(const ObsArgs<F32>&, int, cudaStream_t);
 
 template <class P>
-void launch_link_table(typename P::Link* tab, int n, const FieldDesc& f, int dims, int axis, int pol,
-                       double t_up, double t_lo, cudaStream_t s) {
-  link_table_kernel<P><<<(2 * n + 127) / 128, 128, 0, s>>>(tab, n, f, dims, axis, pol, t_up, t_lo);
+void launch_link_table(void* tab, int n, const FieldDesc& f, int dims, int axis, int pol, double t_up,
+                       double t_lo, cudaStream_t s) {
+  link_table_kernel<P><<<(2 * n + 127) / 128, 128, 0, s>>>(static_cast<typename PlaneLinkOf<P>::type*>(tab),
+                                                           n, f, dims, axis, pol, t_up, t_lo);
 }
-template void launch_link_table<F64>(F64::Link*, int, const FieldDesc&, int, int, int, double, double,
-                                     cudaStream_t);
-template void launch_link_table<F32>(F32::Link*, int, const FieldDesc&, int, int, int, double, double,
-                                     cudaStream_t);
+template void launch_link_table<F64>(void*, int, const FieldDesc&, int, int, int, double, double, cudaStream_t);
+template void launch_link_table<F32>(void*, int, const FieldDesc&, int, int, int, double, double, cudaStream_t);
 
 void launch_coef_table(float4* tab, const FieldDesc& f, int dims, const int N[3], long long pstride,
                        cudaStream_t s) {

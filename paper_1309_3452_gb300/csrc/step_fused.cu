@@ -138,6 +138,73 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
     const bool core = lx >= 1 && lx <= CX && ly >= 1 && ly <= CY && gx < Nx && gy < Ny;
     const long long cxy = (long long)y * Nx + x;
     const int hx = 2 * x, hy = 2 * y;
+    // COEF_SOFTCORE: the x-y part of R = |x - c|^2 + a^2 of this column, as
+    // (hi, lo) pairs of two values: lanes (A0/C0, A1/C1) at (hx, hy),
+    // (hx+1, hy+1) and (B0/D0, B1/D1) at (hx+1, hy), (hx, hy+1)
+    // (kept in shared memory, one slot per thread: sRxy[t] = {Rd_h, Rd_l},
+    // {Ra_h, Ra_l}, so that they take no registers through the z-march)
+    __shared__ __align__(16) float4 sRxy[COEF == COEF_SOFTCORE ? kThreads3d : 1][2];
+    if constexpr (COEF == COEF_SOFTCORE) {
+      const float2 x0 = __ldg(a.hu.sc_sq[0] + hx), x1 = __ldg(a.hu.sc_sq[0] + hx + 1);
+      const float2 y0 = __ldg(a.hu.sc_sq[1] + hy), y1 = __ldg(a.hu.sc_sq[1] + hy + 1);
+      const float2 d00 = padd(x0, y0), d11 = padd(x1, y1), a10 = padd(x1, y0), a01 = padd(x0, y1);
+      sRxy[threadIdx.x][0] = make_float4(d00.x, d11.x, d00.y, d11.y);
+      sRxy[threadIdx.x][1] = make_float4(a10.x, a01.x, a10.y, a01.y);
+    }
+    // Per-level field constants, the same for the whole block, staged in
+    // shared memory by threads 0..6 with copies that bypass the registers,
+    // double-buffered by level parity (level k's copies are issued after the
+    // first barrier of level k-1, when no thread reads that parity any more,
+    // and waited for before the first barrier of level k):
+    //   sLk[p][0..3]: plane-wave link factors along z (LINK_PLANE, table axis z)
+    //                 of A (upper half, Z = 2zn), B (upper, 2zk+1), C (lower,
+    //                 2zk+1), D (lower, 2zk)
+    //   sZq[p][0..2]: soft-core z terms sc_sq[2][Z] of Z = 2zn, 2zk+1, 2zk
+    using PL = typename PlaneLinkOf<P>::type;
+    __shared__ __align__(16) PL sLk[2][4];
+    __shared__ __align__(16) float2 sZq[2][3];
+    // (the (3+1)D launchers run a plane wave along z polarised along x as
+    // LINK_PLANE_ZX and send other plane waves to the general path)
+    constexpr bool lk_z = LINK == LINK_PLANE_ZX;
+    auto stage_level = [&](int k) {
+      const int tid = threadIdx.x;
+      if (tid >= 7) return;
+      const int p = k & 1;
+      const int zk = k < 0 ? k + Nz : (k >= Nz ? k - Nz : k);
+      const int zn = k + 1 >= Nz ? k + 1 - Nz : (k + 1 < 0 ? k + 1 + Nz : k + 1);
+      if constexpr (LINK == LINK_PLANE_ZX) {
+        if (tid < 4) {
+          const int Z = tid == 0 ? 2 * zn : (tid == 3 ? 2 * zk : 2 * zk + 1);
+          const PL* tab = static_cast<const PL*>(tid < 2 ? a.hu.ltab : a.hl.ltab);
+          static_assert(sizeof(PL) % 16 == 0, "16-byte copies");
+          for (int q = 0; q < (int)(sizeof(PL) / 16); ++q)
+            cp_async16(reinterpret_cast<char*>(&sLk[p][tid]) + 16 * q,
+                       reinterpret_cast<const char*>(tab + Z) + 16 * q);
+        }
+      }
+      if constexpr (COEF == COEF_SOFTCORE) {
+        if (tid >= 4) {
+          const int Z = tid == 4 ? 2 * zn : (tid == 5 ? 2 * zk + 1 : 2 * zk);
+          cp_async8(&sZq[p][tid - 4], a.hu.sc_sq[2] + Z);
+        }
+      }
+      cp_async_commit();
+    };
+    // the coefficients of a pair of values with the x-y parts (Rh, Rl), the z
+    // term z and positions H0, H1 (softcore_R's sums, same order)
+    auto pair_b = [&](const HalfFields<P>& h, int which, float2 z, const int (&H0)[3], const int (&H1)[3],
+                      float4 (&b)[2]) {
+      if constexpr (COEF == COEF_SOFTCORE) {
+        const float4 r = sRxy[threadIdx.x][which];  // which: 0 = (A, C) pairs, 1 = (B, D) pairs
+        const float2 Rh = make_float2(r.x, r.y), Rl = make_float2(r.z, r.w);
+        const float2 t0 = softcore_t0(h, H0), t1 = softcore_t0(h, H1);
+        const SoftB2 bb = softcore_b2(padd(Rh, f2(z.x)), padd(Rl, f2(z.y)), make_float2(t0.x, t1.x),
+                                      make_float2(t0.y, t1.y), h.sc_K_hi, h.sc_K_lo);
+        b[0] = lane_b(bb, 0);
+        b[1] = lane_b(bb, 1);
+      }
+    };
+    constexpr bool kPre = COEF == COEF_SOFTCORE;  // coefficients computed in pairs
 
     auto load = [&](int k) {
       const int zk = k < 0 ? k + Nz : k;
@@ -164,6 +231,8 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
       sD[p][1][t] = ld(a.in[7] + o);
     }
     LevelLoad<C> cur = load(z0 - 1);
+    constexpr bool kStage = LINK == LINK_PLANE_ZX || COEF == COEF_SOFTCORE;
+    if (kStage) stage_level(z0 - 1);
 
     for (int k = z0 - 1; k < z1; ++k) {
       const int zk = k < 0 ? k + Nz : k;
@@ -174,38 +243,46 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
       sC[pn][1][t] = cur.C1;  // own old values at the next level
       sD[pn][0][t] = cur.D0;
       sD[pn][1][t] = cur.D1;
-      // prefetch the next level while this one computes
+      // prefetch the next level while this one computes (the soft-core kernels,
+      // short of registers, issue it after the upper half-step instead)
+      constexpr bool kLate = COEF == COEF_SOFTCORE;
       LevelLoad<C> nxt = cur;
-      if (k + 1 < z1) nxt = load(k + 1);
+      if (!kLate && k + 1 < z1) nxt = load(k + 1);
+      if (kStage && threadIdx.x < 7) cp_async_wait_all();  // this level's staged constants
       __syncthreads();
+      if (kStage && k + 1 < z1) stage_level(k + 1);
+      const PL* lkA = lk_z ? &sLk[pk][0] : nullptr;  // compile-time choice: a shared-memory address
+      const PL* lkB = lk_z ? &sLk[pk][1] : nullptr;
 
       // upper half-step: A(k+1) from C(k+1), C(k), D(k+1); B(k) from D(k+1), D(k), C(k)
       const C oC0 = sC[pk][0][t], oC1 = sC[pk][1][t];
       C nA0n, nA1n, nB0k, nB1k;
+      float4 bv[2];
       {
-        C nb[6] = {cur.D0, sD[pn][0][sxm], cur.D1, sD[pn][1][sym], cur.C0, oC0};
-        const int H[3] = {hx, hy, 2 * zn};
-        nA0n = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 0, cur.A0, nb, H, on, a.pstride);
+        const int H0[3] = {hx, hy, 2 * zn}, H1[3] = {hx + 1, hy + 1, 2 * zn};
+        if constexpr (kPre) pair_b(a.hu, 0, sZq[pk][0], H0, H1, bv);
+        C nb0[6] = {cur.D0, sD[pn][0][sxm], cur.D1, sD[pn][1][sym], cur.C0, oC0};
+        nA0n = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 0, cur.A0, nb0, H0, on, a.pstride,
+                                             nullptr, kPre ? &bv[0] : nullptr, lkA);
+        C nb1[6] = {sD[pn][1][sxp], cur.D1, sD[pn][0][syp], cur.D0, cur.C1, oC1};
+        nA1n = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 1, cur.A1, nb1, H1, on, a.pstride,
+                                             nullptr, kPre ? &bv[1] : nullptr, lkA);
       }
       {
-        C nb[6] = {sD[pn][1][sxp], cur.D1, sD[pn][0][syp], cur.D0, cur.C1, oC1};
-        const int H[3] = {hx + 1, hy + 1, 2 * zn};
-        nA1n = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 1, cur.A1, nb, H, on, a.pstride);
-      }
-      {
-        C nb[6] = {sC[pk][0][sxp], oC0, oC1, sC[pk][1][sym], cur.D0, sD[pk][0][t]};
-        const int H[3] = {hx + 1, hy, 2 * zk + 1};
-        nB0k = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 2, cur.B0, nb, H, ok, a.pstride);
-      }
-      {
-        C nb[6] = {oC1, sC[pk][1][sxm], sC[pk][0][syp], oC0, cur.D1, sD[pk][1][t]};
-        const int H[3] = {hx, hy + 1, 2 * zk + 1};
-        nB1k = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 3, cur.B1, nb, H, ok, a.pstride);
+        const int H0[3] = {hx + 1, hy, 2 * zk + 1}, H1[3] = {hx, hy + 1, 2 * zk + 1};
+        if constexpr (kPre) pair_b(a.hu, 1, sZq[pk][1], H0, H1, bv);
+        C nb0[6] = {sC[pk][0][sxp], oC0, oC1, sC[pk][1][sym], cur.D0, sD[pk][0][t]};
+        nB0k = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 2, cur.B0, nb0, H0, ok, a.pstride,
+                                             nullptr, kPre ? &bv[0] : nullptr, lkB);
+        C nb1[6] = {oC1, sC[pk][1][sxm], sC[pk][0][syp], oC0, cur.D1, sD[pk][1][t]};
+        nB1k = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 3, cur.B1, nb1, H1, ok, a.pstride,
+                                             nullptr, kPre ? &bv[1] : nullptr, lkB);
       }
       sB[pk][0][t] = nB0k;
       sB[pk][1][t] = nB1k;
       sA[pn][0][t] = nA0n;
       sA[pn][1][t] = nA1n;
+      if (kLate && k + 1 < z1) nxt = load(k + 1);
       __syncthreads();
 
       // lower half-step: C(k) from A(k+1), A(k), B(k); D(k) from B(k), B(k-1), A(k)
@@ -219,29 +296,29 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
           const bool acc = want_e && core;  // this cell's new values count towards E
           float lc = 0.0f;
           {
-            C nb[6] = {nB0k, sB[pk][0][sxm], nB1k, sB[pk][1][sym], nA0n, nA0};
-            const int H[3] = {hx, hy, 2 * zk + 1};
-            nC0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 4, oC0, nb, H, ok, a.pstride, &S);
+            const int H0[3] = {hx, hy, 2 * zk + 1}, H1[3] = {hx + 1, hy + 1, 2 * zk + 1};
+            if constexpr (kPre) pair_b(a.hl, 0, sZq[pk][1], H0, H1, bv);
+            const PL* lkC = lk_z ? &sLk[pk][2] : nullptr;
+            C nb0[6] = {nB0k, sB[pk][0][sxm], nB1k, sB[pk][1][sym], nA0n, nA0};
+            nC0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 4, oC0, nb0, H0, ok, a.pstride, &S,
+                                                kPre ? &bv[0] : nullptr, lkC);
             if (acc) lc = fmaf(nC0.x, S.x, fmaf(nC0.y, S.y, lc));
-          }
-          {
-            C nb[6] = {sB[pk][1][sxp], nB1k, sB[pk][0][syp], nB0k, nA1n, nA1};
-            const int H[3] = {hx + 1, hy + 1, 2 * zk + 1};
-            nC1 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 5, oC1, nb, H, ok, a.pstride, &S);
+            C nb1[6] = {sB[pk][1][sxp], nB1k, sB[pk][0][syp], nB0k, nA1n, nA1};
+            nC1 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 5, oC1, nb1, H1, ok, a.pstride, &S,
+                                                kPre ? &bv[1] : nullptr, lkC);
             if (acc) lc = fmaf(nC1.x, S.x, fmaf(nC1.y, S.y, lc));
           }
           {
-            C nb[6] = {sA[pk][0][sxp], nA0, nA1, sA[pk][1][sym], nB0k, sB[pm][0][t]};
-            const int H[3] = {hx + 1, hy, 2 * zk};
-            nD0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 6, sD[pk][0][t], nb, H, ok,
-                                                a.pstride, &S);
+            const int H0[3] = {hx + 1, hy, 2 * zk}, H1[3] = {hx, hy + 1, 2 * zk};
+            if constexpr (kPre) pair_b(a.hl, 1, sZq[pk][2], H0, H1, bv);
+            const PL* lkD = lk_z ? &sLk[pk][3] : nullptr;
+            C nb0[6] = {sA[pk][0][sxp], nA0, nA1, sA[pk][1][sym], nB0k, sB[pm][0][t]};
+            nD0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 6, sD[pk][0][t], nb0, H0, ok,
+                                                a.pstride, &S, kPre ? &bv[0] : nullptr, lkD);
             if (acc) lc = fmaf(nD0.x, S.x, fmaf(nD0.y, S.y, lc));
-          }
-          {
-            C nb[6] = {nA1, sA[pk][1][sxm], sA[pk][0][syp], nA0, nB1k, sB[pm][1][t]};
-            const int H[3] = {hx, hy + 1, 2 * zk};
-            nD1 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 7, sD[pk][1][t], nb, H, ok,
-                                                a.pstride, &S);
+            C nb1[6] = {nA1, sA[pk][1][sxm], sA[pk][0][syp], nA0, nB1k, sB[pm][1][t]};
+            nD1 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 7, sD[pk][1][t], nb1, H1, ok,
+                                                a.pstride, &S, kPre ? &bv[1] : nullptr, lkD);
             if (acc) lc = fmaf(nD1.x, S.x, fmaf(nD1.y, S.y, lc));
           }
           if (acc) {  // this level's few terms in FP32, the running sums in FP64 (shared memory)
@@ -749,14 +826,35 @@ void launch2d_tb2_batch(BatchArgs<F32> b, long long total, cudaStream_t s) {
 
 template <int DIMS, int COEF, int LINK>
 int launch_dims(const FusedArgs<F32>& a, cudaStream_t s) {
-  if (DIMS == 3) return launch3d<COEF, LINK>(a, s);
-  return launch2d<COEF, LINK>(a, s);
+  if constexpr (DIMS == 3) {
+    // (3+1)D plane waves are dispatched before reaching here (LINK_PLANE_ZX)
+    if constexpr (LINK == LINK_PLANE) return launch3d<kAnyMode, kAnyMode>(a, s);
+    else return launch3d<COEF, LINK>(a, s);
+  } else {
+    return launch2d<COEF, LINK>(a, s);
+  }
 }
 
 template <int DIMS>
 int dispatch(const FusedArgs<F32>& a, cudaStream_t s) {
   const int c = a.hu.coef_mode, l = a.hu.link_mode;
   if (c == COEF_GENERAL || l == LINK_GENERAL) return launch_dims<DIMS, kAnyMode, kAnyMode>(a, s);
+  // the fused (3+1)D kernel stages plane-wave link factors per z level: a wave
+  // along z polarised along x runs as LINK_PLANE_ZX, other plane waves take
+  // the general path there
+  if (DIMS == 3 && l == LINK_PLANE) {
+    if (a.hu.ltab_axis != 2 || a.hu.lpol != 0) return launch3d<kAnyMode, kAnyMode>(a, s);
+    if (c == COEF_UNIFORM) return launch3d<COEF_UNIFORM, LINK_PLANE_ZX>(a, s);
+    if (c == COEF_STEP) return launch3d<COEF_STEP, LINK_PLANE_ZX>(a, s);
+    if (c == COEF_TABLE) return launch3d<COEF_TABLE, LINK_PLANE_ZX>(a, s);
+    if (c == COEF_SOFTCORE) return launch3d<COEF_SOFTCORE, LINK_PLANE_ZX>(a, s);
+    return launch3d<kAnyMode, kAnyMode>(a, s);
+  }
+  if (c == COEF_SOFTCORE) {
+    if (l == LINK_NONE) return launch_dims<DIMS, COEF_SOFTCORE, LINK_NONE>(a, s);
+    if (l == LINK_PLANE) return launch_dims<DIMS, COEF_SOFTCORE, LINK_PLANE>(a, s);
+    return launch_dims<DIMS, kAnyMode, kAnyMode>(a, s);
+  }
   if (l == LINK_TABLE) {
     if (c == COEF_UNIFORM) return launch_dims<DIMS, COEF_UNIFORM, LINK_TABLE>(a, s);
     if (c == COEF_STEP) return launch_dims<DIMS, COEF_STEP, LINK_TABLE>(a, s);
@@ -803,6 +901,7 @@ int launch_fused2d_tb2(const FusedArgs<F32>& a, cudaStream_t s) {
   if (c == COEF_UNIFORM && l == LINK_CONST) return launch2d_tb2<COEF_UNIFORM, LINK_CONST>(a, s);
   if (c == COEF_STEP && l == LINK_CONST) return launch2d_tb2<COEF_STEP, LINK_CONST>(a, s);
   if (c == COEF_TABLE && l == LINK_NONE) return launch2d_tb2<COEF_TABLE, LINK_NONE>(a, s);
+  if (c == COEF_SOFTCORE && l == LINK_NONE) return launch2d_tb2<COEF_SOFTCORE, LINK_NONE>(a, s);
   return 0;
 }
 

@@ -60,6 +60,10 @@ void launch_one(const HalfStepArgs<P>& a, cudaStream_t s) {
     half_step_kernel<P, DIMS, UPPER, COEF_STEP, LINK_NONE><<<grid, block, 0, s>>>(a);
   else if (f32 && c == COEF_TABLE && l == LINK_NONE)  // the FP32 tabulated-potential paths
     half_step_kernel<P, DIMS, UPPER, COEF_TABLE, LINK_NONE><<<grid, block, 0, s>>>(a);
+  else if (f32 && c == COEF_SOFTCORE && l == LINK_NONE)  // the FP32 analytic soft core
+    half_step_kernel<P, DIMS, UPPER, COEF_SOFTCORE, LINK_NONE><<<grid, block, 0, s>>>(a);
+  else if (f32 && c == COEF_SOFTCORE && l == LINK_PLANE)
+    half_step_kernel<P, DIMS, UPPER, COEF_SOFTCORE, LINK_PLANE><<<grid, block, 0, s>>>(a);
   else if (f32 && c == COEF_TABLE && l == LINK_PLANE)
     half_step_kernel<P, DIMS, UPPER, COEF_TABLE, LINK_PLANE><<<grid, block, 0, s>>>(a);
   else if (f32 && c == COEF_UNIFORM && l == LINK_PLANE)
