@@ -2,18 +2,28 @@
 
 * dirac_batch_step packs simulations of different sizes, masses and fields
   into one persistent launch per time step; every simulation's result must
-  equal, bit for bit, the result of stepping it alone.
+  equal, bit for bit, the result of stepping it alone, and the FP64 oracle
+  within the FP32 (1e-5 rel L2) or FP64 (1e-12) tolerance.
 * The serving loop admits requests as they arrive and HBM allows, batches
-  the resident ones and retires them; each result keeps E to FP32 accuracy.
+  the resident ones and retires them; each result keeps E to FP32 accuracy
+  and its final state matches the oracle.
 """
 import math
 
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_1309_3452_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+FP64_TOL = 1e-12
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 @pytest.fixture(scope="module")
@@ -70,6 +80,10 @@ def test_batch_equals_alone_bitwise(D):
     finally:
         for s in sims:
             s.close()
+    # every member against the FP64 oracle on the same input
+    for (p, prec), psi, got in zip(probs, states, alone):
+        ref = O.step(p, psi, 63)
+        assert rel(got, ref) < (FP64_TOL if prec else FP32_TOL), p
 
 
 def test_batch_rejects_mixed_streams_and_duplicates(D):
@@ -94,7 +108,7 @@ def test_serving_loop_small_stream(D):
                                min_steps=20, max_steps=200)
     srv = serve.Server(hbm_budget=2 << 30, quantum=50)
     out = srv.run(reqs)
-    assert out["requests"] == len(reqs)
+    assert out["requests"] == out["served"] == len(reqs)
     assert out["max_E_drift"] < 1e-6
     assert out["p99_s"] >= out["p50_s"] > 0.0
     for r in out["results"]:
@@ -159,8 +173,9 @@ def test_serving_results_equal_stepping_alone(D, monkeypatch):
     monkeypatch.setenv("DIRAC_NO_FUSED_NORM", "1")  # both sides reduce the stored state
     reqs = serve.make_requests(24, seed=5, rate=40.0, max_side_3d=40, max_side_2d=192,
                                min_steps=30, max_steps=700)
-    srv = serve.Server(hbm_budget=3 << 30, quantum=50)
+    srv = serve.Server(hbm_budget=3 << 30, quantum=50, keep_states=True)
     out = srv.run(reqs)
+    assert out["served"] == len(reqs)
     byid = {r.rid: r for r in reqs}
     import torch
     for res in out["results"]:
@@ -173,3 +188,25 @@ def test_serving_results_equal_stepping_alone(D, monkeypatch):
             E1, _ = s.norm()
         torch.cuda.synchronize()
         assert E0 == res.E0 and E1 == res.E1, res.rid
+        # the served state against the FP64 oracle from the same initial packet
+        ref = O.step(req.prob, psi.cpu().numpy(), req.steps)
+        assert rel(res.state, ref) < FP32_TOL, res.rid
+
+
+def test_allocation_refusal_is_reported_not_faulted(D):
+    """A grid beyond the device's memory: dirac_create's cudaMalloc fails and
+    the call returns DIRAC_ERR_OOM with nothing left allocated (no device
+    fault; the context stays usable)."""
+    import torch
+    free0, _ = torch.cuda.mem_get_info()
+    p = W.Problem(3, (2048, 2048, 2048), (1.0, 1.0, 1.0), 0.5, 0.5)  # 550 GB per FP32 state buffer
+    with pytest.raises(D.DiracError) as e:
+        D.Sim(p, D.FP32)
+    assert e.value.status == D.ERR_OOM
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (64 << 20)
+    q = W.Problem(2, (64, 64, 1), (1.0, 1.0, 1.0), 0.5, 0.5)
+    with D.Sim(q, D.FP32) as s:  # the device still works
+        s.set_spinor(W.random_state(q, 1))
+        s.step(3)
+        assert np.isfinite(s.norm()[0])

@@ -111,7 +111,7 @@ def test_workload_klein4096_windows_and_conservation(env):
 
 def test_workload_laser512_windows(env):
     torch, D = env
-    prob, _, _ = W.workload_laser(N=512, steps=2000, seed=1, sigma=24.0)
+    prob, _, _ = W.workload_laser(N=512, steps=2000, seed=1, sigma=24.0, packet=False)
     c = 256.0
     psi0 = W.gaussian_packet_torch(prob, 24.0, W.random_k0(1), (c, c, c), "cuda")
     n = 5

@@ -1,0 +1,131 @@
+"""FP32 parity at the accuracy target's length: every FP32 field path of the
+fused kernels stepped 1000 time steps and compared with the FP64 oracle over
+the whole state, element by element.
+
+The target is rel L2 <= 1e-5 against the oracle after 1000 steps and a
+relative drift of the conserved functional E <= 1e-6 (where E is conserved:
+real potentials and static vector potentials, Sect. 2 Lemma / Eq. EPM).  A
+rounded FP32 coefficient biases every step the same way, so its error grows
+linearly with the number of steps; 1000 steps is where such a bias would
+show (the compensated hi + lo coefficients keep it out).
+
+Grids: (3+1)D 40 x 36 x 34 (2 x 3 tiles of 32 x 13 interior cells, ragged in
+x and y, 34 z levels in several work items) and (2+1)D 300 x 260 (ten
+30-lane strips with a ragged last one).  Inputs: Gaussian packets (the
+workloads' shape) with seeded momenta, positive-energy spinors.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1309_3452_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 1000
+FP32_TOL = 1e-5      # rel L2 against the oracle after 1000 steps
+FP32_EDRIFT = 1e-6   # relative drift of E where it is conserved
+N3 = (40, 36, 34)
+N2 = (300, 260, 1)
+
+
+@pytest.fixture(scope="module")
+def D():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1309_3452_gb300 import dirac
+    return dirac
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def fields3(name, prob):
+    N = prob.N
+    c = (N[0] / 2.0, N[1] / 2.0, N[2] / 2.0)
+    kz = 2 * math.pi / N[2]
+    return {
+        "V0": W.Fields(V0=0.21),
+        "klein_z": W.Fields(V0=0.05, step_axis=2, step_x0=N[2] / 2 + 0.25, step_V=0.9),
+        "softcore": W.Fields(sc_Z=1.0, sc_a=1.0, sc_center=c),
+        "softcore_offgrid_step": W.Fields(sc_Z=0.8, sc_a=1.3, sc_center=(c[0] - 0.37, c[1] + 0.61, 9.13),
+                                          V0=-0.1, step_axis=0, step_x0=N[0] / 2 + 0.25, step_V=0.4),
+        "softcore_table": W.Fields(sc_Z=1.0, sc_a=1.0, sc_center=c),
+        "Vstatic": W.Fields(V_static=W.random_potential(prob, 6, 0.4)),
+        "absorb": W.Fields(V0=0.05, V0_imag=-0.002, abs_W=0.3, abs_width=4.0, abs_axes=7),
+        "A_const": W.Fields(q=1.0, A_const=(0.3, -0.25, 0.15)),
+        "A_wave": W.Fields(q=1.0, Apw_amp=0.5, Apw_k=(0.0, 0.0, kz), Apw_omega=kz, Apw_pol=0),
+        "links": W.Fields(q=1.0, A_links=W.random_links(prob, 9, 0.3)),
+        "laser": W.Fields(sc_Z=1.0, sc_a=1.0, sc_center=c, q=1.0, Apw_amp=0.5, Apw_k=(0.0, 0.0, kz),
+                          Apw_omega=kz, Apw_pol=0),
+        "laser_table": W.Fields(sc_Z=1.0, sc_a=1.0, sc_center=c, q=1.0, Apw_amp=0.5, Apw_k=(0.0, 0.0, kz),
+                                Apw_omega=kz, Apw_pol=0),
+    }[name]
+
+
+def fields2(name, prob):
+    N = prob.N
+    c = (N[0] / 2.0, N[1] / 2.0, 0.0)
+    ky = 2 * math.pi / N[1]
+    return {
+        "klein": W.Fields(step_axis=0, step_x0=N[0] / 2 + 0.25, step_V=0.9),
+        "softcore": W.Fields(sc_Z=1.0, sc_a=1.0, sc_center=c),
+        "Vstatic": W.Fields(V_static=W.random_potential(prob, 6, 0.4)),
+        "absorb": W.Fields(V0_imag=-0.002, abs_W=0.3, abs_width=8.0, abs_axes=3),
+        "A_const": W.Fields(q=1.0, A_const=(0.3, -0.25, 0.0)),
+        "A_wave": W.Fields(q=1.0, Apw_amp=0.5, Apw_k=(0.0, ky, 0.0), Apw_omega=ky, Apw_pol=0),
+        "links": W.Fields(q=1.0, A_links=W.random_links(prob, 9, 0.3)),
+        "laser": W.Fields(sc_Z=1.0, sc_a=1.0, sc_center=c, q=1.0, Apw_amp=0.5, Apw_k=(0.0, ky, 0.0),
+                          Apw_omega=ky, Apw_pol=0),
+    }[name]
+
+
+# what each case runs on in the FP32 library (for the reader; the modes are
+# chosen by dirac_create from the fields)
+CONSERVED = {"V0", "klein_z", "klein", "softcore", "softcore_offgrid_step", "softcore_table", "Vstatic",
+             "A_const", "links"}
+
+
+def check_long(D, prob, name, seed, monkeypatch):
+    if name.endswith("_table"):
+        monkeypatch.setenv("DIRAC_SOFTCORE_TABLE", "1")  # the tabulated-coefficient path instead
+    c = [n / 2.0 for n in prob.N]
+    sigma = 5.0 if prob.dims == 3 else 14.0
+    k0 = W.random_k0(seed)
+    psi = W.gaussian_packet(prob, sigma, k0[:prob.dims], c[:prob.dims])
+    ref = O.step(prob, psi, STEPS)
+    ob0 = O.observables(prob, psi, 0.0)
+    ob1 = O.observables(prob, ref, STEPS * prob.dt)
+    with D.Sim(prob, D.FP32) as s:
+        s.set_spinor(psi)
+        E0, _ = s.norm()
+        s.step(STEPS)
+        E1, _ = s.norm()
+        out = s.get_spinor()
+    err = rel(out, ref)
+    assert err < FP32_TOL, (name, err)
+    assert abs(E0 - ob0["E"]) < 1e-7 * abs(ob0["E"])
+    assert abs(E1 - ob1["E"]) < (FP32_EDRIFT if name in CONSERVED else FP32_TOL) * abs(ob1["E"]), name
+    if name in CONSERVED:
+        assert abs(E1 - E0) < FP32_EDRIFT * abs(E0), (name, abs(E1 - E0) / abs(E0))
+
+
+@pytest.mark.parametrize("name", ["V0", "klein_z", "softcore", "softcore_offgrid_step", "softcore_table",
+                                  "Vstatic", "absorb", "A_const", "A_wave", "links", "laser",
+                                  "laser_table"])
+def test_fp32_1000_steps_3d(D, name, monkeypatch):
+    prob = W.Problem(3, N3, (1.0, 1.0, 1.0), 0.9 * W.stability_limit(3), 1.0)
+    prob = prob.with_fields(**vars(fields3(name, prob)))
+    check_long(D, prob, name, 11, monkeypatch)
+
+
+@pytest.mark.parametrize("name", ["klein", "softcore", "Vstatic", "absorb", "A_const", "A_wave", "links",
+                                  "laser"])
+def test_fp32_1000_steps_2d(D, name, monkeypatch):
+    prob = W.Problem(2, N2, (1.0, 1.0, 1.0), 0.9 * W.stability_limit(2), 0.4)
+    prob = prob.with_fields(**vars(fields2(name, prob)))
+    check_long(D, prob, name, 12, monkeypatch)
