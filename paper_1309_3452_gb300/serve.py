@@ -7,8 +7,19 @@ simulations already resident, keeps every admitted state resident until its
 steps are done, and advances all resident simulations together with
 dirac_batch_step in quanta of at most `quantum` steps (shortened so the
 request that finishes first finishes exactly).  Between quanta finished
-requests leave (their conserved functional is read and checked) and waiting
-ones join.  Latency = finish - arrival on the wall clock.
+requests leave (their conserved functional is read and checked against the
+value reduced when their state was set) and waiting ones join.  Latency =
+finish - arrival on the wall clock.
+
+Admission never waits for the device: the initial packet is built and set on
+the server's stream, and the functional of the initial state, reduced there
+by dirac_set_spinor, is read only when the request retires.  A request that
+can never fit the budget is rejected; one whose creation fails with
+DIRAC_ERR_OOM (the device has less free memory than the budget assumed) waits
+until a resident request has retired and is then tried again (rejected if
+nothing else is resident); a request may be cancelled by its client or time
+out, before or after admission, and then leaves between quanta, freeing its
+memory.
 
 The stepping, the norms and the state set-up all run in libdirac; this
 module only schedules.
@@ -38,6 +49,8 @@ class Request:
     center: tuple
     steps: int
     precision: int = D.FP32
+    cancel_after: Optional[float] = None  # the client cancels this long after arrival (s)
+    timeout: Optional[float] = None       # dropped once its latency would exceed this (s)
 
     @property
     def lups(self) -> float:
@@ -80,11 +93,13 @@ def make_requests(n: int, seed: int = 0, rate: float = 1.0, max_side_3d: int = 3
 class Result:
     rid: int
     arrival: float
-    admitted: float
-    finished: float
-    lups: float
+    admitted: float          # nan if never admitted
+    finished: float          # when it retired, was rejected, cancelled or timed out
+    lups: float              # site updates done for it
     E0: float
     E1: float
+    status: str = "ok"       # ok | rejected | oom | cancelled | timeout
+    state: Optional[np.ndarray] = None  # the final state (Server(keep_states=True))
 
     @property
     def latency(self) -> float:
@@ -92,45 +107,91 @@ class Result:
 
 
 class Server:
-    def __init__(self, hbm_budget: int, quantum: int = 100, stream=None, device="cuda"):
+    def __init__(self, hbm_budget: int, quantum: int = 100, stream=None, device="cuda",
+                 keep_states: bool = False, drift_tol: float = 1e-6):
         import torch
         self.torch = torch
         self.budget = int(hbm_budget)
         self.quantum = int(quantum)
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.device = device
+        self.keep_states = keep_states
+        self.drift_tol = drift_tol
 
     def _admit(self, req: Request):
+        """Create the request's simulation and enqueue its initial state on the
+        server's stream; nothing here waits for the device.  The packet tensor
+        belongs to the stream (caching allocator), so releasing it right away
+        is safe: its memory is reused only by later work on that stream."""
         torch = self.torch
         with torch.cuda.stream(self.stream):
             psi = W.gaussian_packet_torch(req.prob, req.sigma, req.k0, req.center, self.device)
         sim = D.Sim(req.prob, req.precision, stream=self.stream.cuda_stream)
-        sim.set_spinor_device(psi.data_ptr())
-        E0, _ = sim.norm()  # synchronises: psi may be released
+        try:
+            sim.set_spinor_device(psi.data_ptr())
+        except Exception:
+            sim.close()
+            raise
         del psi
-        return sim, E0
+        return sim
+
+    def _retire(self, sim):
+        """(E0, E1, state): the functional of the initial state (reduced when it
+        was set) and of the final one (dirac_check, which also tests the
+        paper's bounds); synchronises the stream."""
+        _, r = sim.check(self.drift_tol)
+        state = sim.get_spinor() if self.keep_states else None
+        return r["E_ref"], r["E"], state
 
     def run(self, requests: List[Request], log=None) -> dict:
-        torch = self.torch
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
-        resident = []  # [req, sim, remaining, admitted, E0, bytes]
+        resident = []  # [req, sim, remaining, admitted, bytes]
         used = 0
         results: List[Result] = []
         launches = 0
+        self.oom_backoffs = 0
+        hold = False  # an admission failed with DIRAC_ERR_OOM: wait for a retirement
+        nan = float("nan")
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0
+
+        def gone(req, t):
+            """the client's cancel time or the timeout has passed at time t"""
+            if req.cancel_after is not None and t >= req.arrival + req.cancel_after:
+                return "cancelled"
+            if req.timeout is not None and t >= req.arrival + req.timeout:
+                return "timeout"
+            return None
+
         while pending or resident:
+            # drop waiting requests that were cancelled or timed out
+            for req in [r for r in pending if r.arrival <= now() and gone(r, now())]:
+                pending.remove(req)
+                results.append(Result(req.rid, req.arrival, nan, now(), 0.0, nan, nan, gone(req, now())))
             # admit every arrived request that fits
-            while pending and pending[0].arrival <= now():
+            while pending and pending[0].arrival <= now() and not hold:
                 req = pending[0]
                 need = D.state_bytes(req.prob.dims, req.prob.N, req.precision)
-                if need > self.budget:
-                    raise ValueError(f"request {req.rid} needs {need} B > budget {self.budget} B")
+                if need > self.budget:  # can never fit
+                    pending.popleft()
+                    results.append(Result(req.rid, req.arrival, nan, now(), 0.0, nan, nan, "rejected"))
+                    continue
                 if used + need > self.budget:
                     break
+                try:
+                    sim = self._admit(req)
+                except D.DiracError as e:
+                    if e.status != D.ERR_OOM:
+                        raise
+                    self.oom_backoffs += 1
+                    if not resident:  # nothing will free memory for it
+                        pending.popleft()
+                        results.append(Result(req.rid, req.arrival, nan, now(), 0.0, nan, nan, "oom"))
+                        continue
+                    hold = True
+                    break
                 pending.popleft()
-                sim, E0 = self._admit(req)
-                resident.append([req, sim, req.steps, now(), E0, need])
+                resident.append([req, sim, req.steps, now(), need])
                 used += need
             if not resident:
                 if pending:
@@ -143,28 +204,38 @@ class Server:
             launches += sum(s.launches for s in sims) - before
             for r in resident:
                 r[2] -= q
-            done = [r for r in resident if r[2] == 0]
-            if done:
-                for r in done:
-                    req, sim, _, adm, E0, need = r
-                    E1, _ = sim.norm()  # synchronises the stream
-                    results.append(Result(req.rid, req.arrival, adm, now(), req.lups, E0, E1))
+            leaving = [r for r in resident if r[2] == 0 or gone(r[0], now())]
+            if leaving:
+                for r in leaving:
+                    req, sim, left, adm, need = r
+                    status = "ok" if left == 0 else gone(req, now())
+                    if status == "ok":
+                        E0, E1, state = self._retire(sim)
+                    else:
+                        E0, E1, state = nan, nan, None
+                    results.append(Result(req.rid, req.arrival, adm, now(), req.prob.cells * (req.steps - left),
+                                          E0, E1, status, state))
                     sim.close()
                     used -= need
                     if log:
-                        log(f"done {req.rid}: {req.prob.dims}D N={req.prob.N[0]} steps={req.steps} "
+                        log(f"{status} {req.rid}: {req.prob.dims}D N={req.prob.N[0]} steps={req.steps} "
                             f"latency {results[-1].latency:.2f}s")
-                resident = [r for r in resident if r[2] > 0]
+                resident = [r for r in resident if not any(r is x for x in leaving)]
+                hold = False
             else:
                 self.stream.synchronize()
         makespan = now()
-        lat = sorted(r.latency for r in results)
+        ok = [r for r in results if r.status == "ok"]
+        lat = sorted(r.latency for r in ok)
         total = sum(r.lups for r in results)
-        drift = max(abs(r.E1 - r.E0) / abs(r.E0) for r in results)
-        return {"requests": len(results), "makespan_s": makespan, "glups": total / makespan / 1e9,
-                "p50_s": percentile(lat, 50), "p99_s": percentile(lat, 99), "mean_s": statistics.mean(lat),
+        drift = max((abs(r.E1 - r.E0) / abs(r.E0) for r in ok), default=nan)
+        counts = collections.Counter(r.status for r in results)
+        return {"requests": len(results), "served": len(ok), "status_counts": dict(counts),
+                "makespan_s": makespan, "glups": total / makespan / 1e9,
+                "p50_s": percentile(lat, 50), "p99_s": percentile(lat, 99),
+                "mean_s": statistics.mean(lat) if lat else nan,
                 "max_E_drift": drift, "gpu_launches": launches, "total_lups": total,
-                "results": results}
+                "oom_backoffs": self.oom_backoffs, "results": results}
 
 
 def percentile(sorted_vals, p):

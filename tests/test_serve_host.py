@@ -34,6 +34,9 @@ class FakeSim:
     def norm(self):
         return 1.0, 1.0
 
+    def check(self, tol):
+        return True, {"E": 1.0, "E_ref": 1.0}
+
     def close(self):
         self.closed = True
         FakeSim.alive.remove(self)
@@ -52,7 +55,7 @@ def test_serving_schedule(monkeypatch):
         sims[req.rid] = FakeSim(req, needs[req.rid])
         sims[req.rid].admitted_wall = time.perf_counter()
         assert sum(s.need for s in FakeSim.alive) <= budget
-        return sims[req.rid], 1.0
+        return sims[req.rid]
 
     def batch_step(group, n):
         calls.append((len(group), n))
@@ -102,3 +105,103 @@ def test_percentile():
     assert serve.percentile([1.0, 2.0, 3.0, 4.0], 50) == pytest.approx(2.5)
     assert serve.percentile([5.0], 99) == 5.0
     assert serve.percentile([1.0, 2.0], 100) == 2.0
+
+
+def fake_device(monkeypatch, needs, oom_at=(), steps_seen=None):
+    """Patch the server's device work: admissions create FakeSims (raising
+    DIRAC_ERR_OOM, as dirac_create does when cudaMalloc fails, on the
+    admission attempts listed in oom_at), batch steps count steps."""
+    sims, attempts = {}, []
+
+    def admit(self, req):
+        attempts.append(req.rid)
+        if len(attempts) in oom_at:
+            raise D.DiracError(D.ERR_OOM, "cudaMalloc(state): out of memory (injected)")
+        sims[req.rid] = FakeSim(req, needs[req.rid])
+        return sims[req.rid]
+
+    def batch_step(group, n):
+        for s in group:
+            assert not s.closed
+            s.steps += n
+            s.launches += 1
+            assert s.steps <= s.req.steps
+
+    monkeypatch.setattr(serve.Server, "_admit", admit)
+    monkeypatch.setattr(serve.D, "batch_step", batch_step)
+    return sims, attempts
+
+
+def test_oversize_request_is_rejected_not_raised(monkeypatch):
+    FakeSim.alive = []
+    reqs = serve.make_requests(8, seed=2, rate=500.0, max_side_3d=48, max_side_2d=256,
+                               min_steps=10, max_steps=50)
+    needs = {r.rid: D.state_bytes(r.prob.dims, r.prob.N, r.precision) for r in reqs}
+    big = max(needs, key=needs.get)
+    budget = max(v for k, v in needs.items() if k != big)  # everything fits but the largest
+    sims, _ = fake_device(monkeypatch, needs)
+    out = serve.Server(hbm_budget=budget, quantum=16, stream=FakeStream()).run(reqs)
+    st = {r.rid: r.status for r in out["results"]}
+    assert st[big] == "rejected" and big not in sims
+    assert all(st[r.rid] == "ok" for r in reqs if r.rid != big)
+    assert out["served"] == len(reqs) - 1 and not FakeSim.alive
+
+
+def test_allocation_refusal_backs_off_until_a_request_retires(monkeypatch):
+    """An injected DIRAC_ERR_OOM at admission: the request waits (no crash,
+    no retry storm) until a resident request retires, then is admitted; an
+    OOM with nothing resident rejects the request."""
+    FakeSim.alive = []
+    reqs = serve.make_requests(10, seed=4, rate=1000.0, max_side_3d=40, max_side_2d=128,
+                               min_steps=20, max_steps=60)
+    for r in reqs:
+        r.arrival = 0.0  # all waiting at once: the first two are resident when the third fails
+    needs = {r.rid: D.state_bytes(r.prob.dims, r.prob.N, r.precision) for r in reqs}
+    sims, attempts = fake_device(monkeypatch, needs, oom_at=(3, 4))
+    srv = serve.Server(hbm_budget=10 * sum(needs.values()), quantum=8, stream=FakeStream())
+    out = srv.run(reqs)
+    assert srv.oom_backoffs == 2
+    # the third attempt failed; the same request came back only after a retirement
+    refused = attempts[2]
+    assert attempts[3] == refused  # retried: the 4th attempt is the same request (and failed again)
+    assert attempts.count(refused) == 3
+    assert all(r.status == "ok" for r in out["results"])
+    assert all(sims[r.rid].steps == r.steps for r in reqs) and not FakeSim.alive
+    # nothing resident: the OOM request cannot wait for memory to come back
+    FakeSim.alive = []
+    one = serve.make_requests(1, seed=4, rate=1000.0, max_side_3d=40, max_side_2d=128,
+                              min_steps=20, max_steps=60)
+    fake_device(monkeypatch, {one[0].rid: needs[one[0].rid]}, oom_at=(1,))
+    out = serve.Server(hbm_budget=1 << 40, quantum=8, stream=FakeStream()).run(one)
+    assert [r.status for r in out["results"]] == ["oom"]
+
+
+def test_cancelled_and_timed_out_requests_free_their_slots(monkeypatch):
+    FakeSim.alive = []
+    reqs = serve.make_requests(12, seed=6, rate=2000.0, max_side_3d=40, max_side_2d=128,
+                               min_steps=400, max_steps=500)
+    needs = {r.rid: D.state_bytes(r.prob.dims, r.prob.N, r.precision) for r in reqs}
+    reqs[0].cancel_after = 0.0   # cancelled as soon as it arrives
+    reqs[1].timeout = 0.0        # times out before it can be admitted
+    budget = needs[reqs[2].rid] + needs[reqs[3].rid]
+    sims, _ = fake_device(monkeypatch, needs)
+    # a client that cancels request 2 while it is resident
+    real_batch = serve.D.batch_step
+    quanta = []
+
+    def batch_step(group, n):
+        quanta.append([s.req.rid for s in group])
+        if len(quanta) == 2:
+            reqs[2].cancel_after = 0.0  # the client cancels now
+        real_batch(group, n)
+
+    monkeypatch.setattr(serve.D, "batch_step", batch_step)
+    out = serve.Server(hbm_budget=max(budget, max(needs.values())), quantum=8, stream=FakeStream()).run(reqs)
+    st = {r.rid: r for r in out["results"]}
+    assert st[reqs[0].rid].status == "cancelled" and reqs[0].rid not in sims
+    assert st[reqs[1].rid].status == "timeout" and reqs[1].rid not in sims
+    assert st[reqs[2].rid].status == "cancelled" and sims[reqs[2].rid].closed
+    assert 0 < st[reqs[2].rid].lups < reqs[2].lups  # it had run a few quanta
+    assert all(st[r.rid].status == "ok" for r in reqs[3:])
+    assert not FakeSim.alive
+    assert out["served"] == len(reqs) - 3 and out["status_counts"]["cancelled"] == 2
