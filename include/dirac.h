@@ -53,9 +53,12 @@
  *   DIRAC_NO_GRAPHS             step loops as plain launches, no CUDA graphs
  *   DIRAC_NO_FUSED_NORM         dirac_norm always reduces the stored state
  *   DIRAC_NO_TEMPORAL_BLOCKING  (2+1)D FP32: one time step per pass
- *   DIRAC_SOFTCORE_TABLE        (read by dirac_create) FP32 soft core through
- *                               a per-site coefficient table instead of the
- *                               per-value compensated evaluation
+ *   DIRAC_SOFTCORE              (read by dirac_create) how the FP32 kernels
+ *                               evaluate a soft-core potential's Cayley
+ *                               coefficients: "analytic" (default; compensated
+ *                               FP32 per value, no table), "corrected" (an FP32
+ *                               estimate plus a 4-byte tabulated correction per
+ *                               value) or "table" (16 bytes per value)
  * ---------------------------------------------------------------------------
  */
 #ifndef DIRAC_H
@@ -401,6 +404,48 @@ void dirac_destroy(dirac_sim* sim);
 dirac_status dirac_norm_noalloc(int dims, const int N[3], const double dx[3], double dt, double t,
                                 const dirac_fields* fields, dirac_precision precision,
                                 const void* const* planes, double* out_dev, void* cuda_stream);
+
+/*
+ * Sub-domain decomposition (Sect. 6: the scheme is parallelised by spatial
+ * sub-domains that exchange their boundary values).  A (3+1)D grid is split
+ * along z into nslabs slabs of consecutive levels (dirac_slab_partition);
+ * every slab is stepped by the fused kernel as its own sub-domain, which
+ * stores one halo level on either side, and after every time step each slab's
+ * first and last own levels are copied into its neighbours' halo levels
+ * (periodic along z).  Fields are evaluated at every value's position on the
+ * whole grid, so the stepped state equals, bit for bit, that of the whole
+ * grid stepped as one simulation.  All slabs live on the calling device and
+ * run on cuda_stream; the halo copies are device-to-device copies of Nx*Ny
+ * values per plane and level, the data a multi-device split would exchange.
+ *
+ * dirac_slabs_create: as dirac_create for the whole grid N (dims == 3, FP32
+ *   only, 1 <= nslabs <= N[2]); fields given per site (V_static, A_links) and
+ *   absorbing layers are not decomposed, and a vector potential must be
+ *   constant or a plane wave with its wave vector along z
+ *   (DIRAC_ERR_UNSUPPORTED); a soft core is evaluated analytically.
+ * set/get_spinor: the whole grid in the canonical host layout (as
+ *   dirac_set_spinor / dirac_get_spinor; get synchronises).
+ * step: nsteps time steps of every slab, each followed by the halo exchange.
+ * norm: E and the naive norm summed over the slabs' own values (synchronises).
+ * dirac_slab_partition (host only): slab k of nslabs over Nz levels starts at
+ *   level *z0 and has *nz levels; the first Nz mod nslabs slabs are one level
+ *   longer.  Out-of-range arguments give *z0 = *nz = 0.
+ * Errors: dirac_slabs_last_error (NULL: the last failed creation).
+ */
+typedef struct dirac_slabs dirac_slabs;
+void dirac_slab_partition(int Nz, int nslabs, int k, int* z0, int* nz);
+dirac_status dirac_slabs_create(dirac_slabs** out, int nslabs, int dims, const int N[3], const double dx[3],
+                                double dt, double m, const dirac_fields* fields, dirac_precision precision,
+                                unsigned flags, void* cuda_stream);
+dirac_status dirac_slabs_set_spinor(dirac_slabs* g, const double* host);
+dirac_status dirac_slabs_get_spinor(dirac_slabs* g, double* host);
+dirac_status dirac_slabs_step(dirac_slabs* g, long nsteps);
+dirac_status dirac_slabs_norm(dirac_slabs* g, double* E, double* naive);
+dirac_status dirac_slabs_info(const dirac_slabs* g, int k, int* z0, int* nz);
+dirac_status dirac_slabs_get_time(const dirac_slabs* g, double* t);
+long long dirac_slabs_kernel_launches(const dirac_slabs* g);
+const char* dirac_slabs_last_error(const dirac_slabs* g);
+void dirac_slabs_destroy(dirac_slabs* g);
 
 /* ABI version: DIRAC_ABI_VERSION of the header the library was built with.
    A client checks it against the header it was compiled with; the version

@@ -274,7 +274,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // potential (with V0 and a Klein step, real) whose b is computed per value
 // in compensated FP32 from |x - c|^2 + a^2, itself summed from three small
 // per-axis tables of (X dx_a/2 - c_a)^2 (no per-site data).
-enum CoefMode { COEF_UNIFORM = 0, COEF_STEP = 1, COEF_GENERAL = 2, COEF_TABLE = 3, COEF_SOFTCORE = 4 };
+// COEF_SOFTCORR (FP32 kernels): the same soft core with b formed in plain FP32
+// (softcore_fast2) and completed by a per-value correction from a table of
+// scaled 16-bit integer pairs (4 bytes per value; see softcore_corr_index).
+enum CoefMode { COEF_UNIFORM = 0, COEF_STEP = 1, COEF_GENERAL = 2, COEF_TABLE = 3, COEF_SOFTCORE = 4,
+                COEF_SOFTCORR = 5 };
 enum LinkMode { LINK_NONE = 0, LINK_CONST = 1, LINK_GENERAL = 2, LINK_PLANE = 3, LINK_TABLE = 4 };
 // Kernel-side specialisation of LINK_PLANE in the fused (3+1)D kernel: the
 // wave travels along z and is polarised along x; the kernel stages the link
@@ -468,6 +472,26 @@ __device__ __forceinline__ SoftB2 softcore_b2(float2 Rh, float2 Rl, float2 t0h, 
   ml = pfma(al, r0, ml);
   return SoftB2{r0, rl, pneg(mh), pneg(ml)};
 }
+// The plain FP32 estimate of the soft-core b = 1/(1 + i theta) of two values
+// (lanes): R = Rh + Rl rounded once, theta = K y + th0 with y the hardware
+// 1/sqrt(R) estimate, b = (1 - i theta) r with r the hardware estimate of
+// 1/(1 + theta^2).  Relative error below ~5e-7; COEF_SOFTCORR adds the
+// tabulated difference to the exact b (the table is built with this very
+// function, so the two agree bit for bit).
+__device__ __forceinline__ void softcore_fast2(float2 Rh, float2 Rl, float2 t0h, float Kh, float2& re,
+                                               float2& im) {
+  const float2 y = rsqrt2(padd(Rh, Rl));
+  const float2 th = pfma(f2(Kh), y, t0h);
+  re = rcp2(pfma(th, th, f2(1.0f)));
+  im = pmul(pneg(th), re);
+}
+// scale of the tabulated corrections: exact b - FP32 estimate = q * 2^-35
+// per component, q a 16-bit integer (|difference| < 2^-20 ~ 9.5e-7)
+constexpr float kCorrScale = 2.9103830456733704e-11f;  // 2^-35
+__device__ __forceinline__ float2 corr_decode(unsigned w) {
+  return make_float2(rmul((float)(short)(w & 0xffffu), kCorrScale), rmul((float)(short)(w >> 16), kCorrScale));
+}
+
 // one value's coefficient {re hi, re lo, im hi, im lo} from a lane of a pair
 __device__ __forceinline__ float4 lane_b(const SoftB2& b, int lane) {
   return lane ? make_float4(b.re_hi.y, b.re_lo.y, b.im_hi.y, b.im_lo.y)
@@ -551,6 +575,8 @@ struct HalfFields {
   int sc_step;              // a Klein step is present (else sc_t0[0] everywhere)
   float sc_K_hi, sc_K_lo;
   const float2* sc_sq[3];
+  // COEF_SOFTCORR: the correction records (softcore_corr_index), 32-bit words
+  const unsigned* sc_corr;
   // LINK_TABLE: link factors [(2 axis + dir) * larr_n + plane * larr_ps + site],
   // dir 0 = the value's own link upwards, 1 = the link from its lower
   // neighbour (applied conjugated, like the per-site path)
@@ -621,6 +647,25 @@ __device__ __forceinline__ float2 softcore_t0(const HalfFields<P>& h, const int 
   return hs >= h.step_X ? h.sc_t0[1] : h.sc_t0[0];
 }
 
+// COEF_SOFTCORR correction records: one record of nplanes 32-bit words per
+// cell, in the order a z-level (y-row in (2+1)D) iteration of the fused
+// kernels uses them: record r holds the upper values of level r+1 planes
+// A0, A1 (u0) and the values of level r of every other plane.  So the value
+// of plane p in cell (x, y, z) has its word at
+//   ((z' Ny + y') Nx + x) * nplanes + p,  with z' = z - 1 (wrapped) for A0, A1
+// ((2+1)D: y' = y - 1 for u0) and z' = z (y' = y) otherwise.
+template <int DIMS>
+__device__ __forceinline__ long long softcore_corr_index(int plane, const int (&H)[3], const int (&N)[3]) {
+  const int x = H[0] >> 1, y = H[1] >> 1, z = H[2] >> 1;
+  const bool shifted = DIMS == 3 ? plane < 2 : plane == 0;
+  if (DIMS == 3) {
+    const int zr = shifted ? (z == 0 ? N[2] - 1 : z - 1) : z;
+    return (((long long)zr * N[1] + y) * N[0] + x) * 8 + plane;
+  }
+  const int yr = shifted ? (y == 0 ? N[1] - 1 : y - 1) : y;
+  return ((long long)yr * N[0] + x) * 4 + plane;
+}
+
 // COEF_SOFTCORE update (FP32 only): b of this value from the caller's pair
 // computation (bpre) or computed here (both lanes the same value, so the
 // result is bit-identical to the value's lane of a pair)
@@ -652,6 +697,25 @@ __device__ __forceinline__ float2 apply_softcore_f32(const HalfFields<F32>& h, f
   }
   return apply_b(b, h.rx_hi, h.rx_lo, F, S);
 }
+// COEF_SOFTCORR: the FP32 estimate of this value plus its tabulated correction
+// (or the caller's pair computation, bpre)
+template <int DIMS>
+__device__ __forceinline__ float2 apply_softcorr_f32(const HalfFields<F32>& h, float2 F, float2 S,
+                                                     const int (&H)[3], const float4* bpre, int plane,
+                                                     const int (&N)[3]) {
+  float4 b;
+  if (bpre) {
+    b = *bpre;
+  } else {
+    float Rh, Rl;
+    softcore_R<DIMS>(h, H, Rh, Rl);
+    float2 re, im;
+    softcore_fast2(f2(Rh), f2(Rl), f2(softcore_t0(h, H).x), h.sc_K_hi, re, im);
+    const float2 c = corr_decode(__ldg(h.sc_corr + softcore_corr_index<DIMS>(plane, H, N)));
+    b = make_float4(re.x, c.x, im.x, c.y);
+  }
+  return apply_b(b, h.rx_hi, h.rx_lo, F, S);
+}
 template <>
 __device__ __forceinline__ float2 apply_softcore<2, F32>(const HalfFields<F32>& h, float2 F, float2 S,
                                                          const int (&H)[3], const float4* bpre) {
@@ -679,7 +743,10 @@ __device__ __forceinline__ typename P::cplx site_update(
     const HalfFields<P>& h, const FieldDesc& f, bool iso, const typename P::Ratio& ry,
     const typename P::Ratio& rz, int plane, typename P::cplx F, typename P::cplx (&nb)[6],
     const int (&H)[3], long long site, long long pstride, typename P::cplx* S_out = nullptr,
-    const float4* bpre = nullptr, const typename PlaneLinkOf<P>::type* lk = nullptr) {
+    const float4* bpre = nullptr, const typename PlaneLinkOf<P>::type* lk = nullptr,
+    const int* Ngrid_p = nullptr) {
+  // grid extent (cells per axis) for the soft-core correction index
+  const int Ngrid[3] = {Ngrid_p ? Ngrid_p[0] : 1, Ngrid_p ? Ngrid_p[1] : 1, Ngrid_p ? Ngrid_p[2] : 1};
   using C = typename P::cplx;
   const int link = LINK == kAnyMode ? h.link_mode : LINK;
   const int coef = COEF == kAnyMode ? h.coef_mode : COEF;
@@ -730,6 +797,10 @@ __device__ __forceinline__ typename P::cplx site_update(
   }
   if (coef == COEF_TABLE) return apply_table(h, F, S, plane, site);
   if (coef == COEF_SOFTCORE) return apply_softcore<DIMS>(h, F, S, H, bpre);
+  if (coef == COEF_SOFTCORR) {
+    if constexpr (sizeof(typename P::real) == 4) return apply_softcorr_f32<DIMS>(h, F, S, H, bpre, plane, Ngrid);
+    else return F;  // not used: FP64 kernels take the general path
+  }
   double V = potential_at(f, DIMS, H[0], H[1], H[2], site, pstride, plane, h.t);
   double th = f.dt * (h.beta * f.m + V) * 0.5;
   double th_im = f.dt * potential_imag_at(f, DIMS, H[0], H[1], H[2]) * 0.5;

@@ -26,6 +26,10 @@ struct dirac_sim {
   dirac_fields f{};
   cudaStream_t stream = nullptr;
   long long ncell = 0, pstride = 0;
+  // levels along the marching axis ((3+1)D): updated range, global origin and
+  // extent (a whole grid: 0, N[2], 0, N[2]; see FusedArgs)
+  int zlo = 0, nzu = 1, zorg = 0, Nzg = 1;
+  int Nf[3] = {1, 1, 1};      // extent of the grid the fields live on (a slab's whole grid; else N)
   int np = 0;
   size_t elem = 0;            // bytes per complex value
   void* state = nullptr;      // np * pstride values: the current state
@@ -37,7 +41,8 @@ struct dirac_sim {
   double2* staging = nullptr; // one canonical plane (FP32 conversions)
   double* Vstatic = nullptr;  // one real per site (plane-major, pstride)
   float4* b_tab = nullptr;    // COEF_TABLE: b = 1/(1 + i theta) per site as hi + lo (plane-major, pstride)
-  float2* sc_sq = nullptr;    // COEF_SOFTCORE: (X dx_a/2 - c_a)^2 per axis and half-lattice index, hi + lo
+  float2* sc_sq = nullptr;    // COEF_SOFTCORE/CORR: (X dx_a/2 - c_a)^2 per axis and half-lattice index, hi + lo
+  unsigned* sc_corr = nullptr; // COEF_SOFTCORR: one 32-bit correction word per value
   double* Alink = nullptr;    // link integrals x q: 2 dims slots (up, down link per axis) of np * pstride
   F32::Link* larr = nullptr;  // LINK_TABLE: link factors, same slots, FP32 hi + lo
   double* partials = nullptr;
@@ -76,6 +81,10 @@ static dirac_status fail(dirac_sim* s, dirac_status st, const std::string& msg) 
   return st;
 }
 static dirac_status cuda_fail(dirac_sim* s, cudaError_t e, const char* what) {
+  // a failed call also leaves its (non-sticky) error as the runtime's last
+  // error: clear it, so that later calls of this or another simulation do not
+  // report it again
+  cudaGetLastError();
   std::string m = std::string(what) + ": " + cudaGetErrorString(e);
   return fail(s, e == cudaErrorMemoryAllocation ? DIRAC_ERR_OOM : DIRAC_ERR_CUDA, m);
 }
@@ -199,7 +208,7 @@ static void softcore_tables(const dirac_sim* s, std::vector<float2>& out) {
   double rmax = s->f.sc_a * s->f.sc_a;
   for (int a = 0; a < s->dims; ++a) {
     double m = 0.0;
-    for (long long X = 0; X < 2LL * s->N[a]; ++X) {
+    for (long long X = 0; X < 2LL * s->Nf[a]; ++X) {
       const double d = (double)X * s->dx[a] * 0.5 - s->f.sc_center[a];
       m = std::max(m, d * d);
     }
@@ -208,7 +217,7 @@ static void softcore_tables(const dirac_sim* s, std::vector<float2>& out) {
   const double q = std::ldexp(1.0, std::ilogb(rmax) + 1 - 22);
   out.clear();
   for (int a = 0; a < 3; ++a) {
-    for (long long X = 0; X < 2LL * s->N[a]; ++X) {
+    for (long long X = 0; X < 2LL * s->Nf[a]; ++X) {
       double v = 0.0;
       if (a < s->dims) {
         const double d = (double)X * s->dx[a] * 0.5 - s->f.sc_center[a];
@@ -250,7 +259,7 @@ static FieldDesc field_desc(const dirac_sim* s) {
   d.abs_W = s->f.abs_W;
   d.abs_width = s->f.abs_width;
   d.abs_axes = s->f.abs_axes;
-  for (int a = 0; a < 3; ++a) d.L[a] = s->N[a] * s->dx[a];
+  for (int a = 0; a < 3; ++a) d.L[a] = s->Nf[a] * s->dx[a];
   d.Alink = s->Alink;
   d.Alink_n = (long long)s->np * s->pstride;
   d.Alink_ps = s->pstride;
@@ -296,8 +305,9 @@ static HalfFields<P> half_fields(const dirac_sim* s, bool upper, double t) {
     long long off = 0;
     for (int a = 0; a < 3; ++a) {
       h.sc_sq[a] = s->sc_sq ? s->sc_sq + off : nullptr;
-      off += 2LL * s->N[a];
+      off += 2LL * s->Nf[a];
     }
+    h.sc_corr = s->sc_corr;
   }
   if (s->link_mode == LINK_TABLE) {
     h.larr = reinterpret_cast<const typename P::Link*>(s->larr);
@@ -354,6 +364,10 @@ static FusedArgs<P> fused_args(dirac_sim* s, double t) {
   a.hu = half_fields<P>(s, true, t);
   a.hl = half_fields<P>(s, false, t + s->dt / 2.0);
   a.f = field_desc(s);
+  a.zlo = s->zlo;
+  a.nzu = s->nzu;
+  a.zorg = s->zorg;
+  a.Nzg = s->Nzg;
   return a;
 }
 
@@ -414,9 +428,27 @@ static void apply_plan(dirac_sim* s, const dirac_plan& p) {
   s->plan_us = p.us_per_step;
 }
 
+// A slab of a grid decomposed along its marching axis ((3+1)D: z): the
+// simulation stores nz + 2 levels, updates levels 1 .. nz, and the fields live
+// on the whole grid (Nf) with its level 1 at global level z0.
+struct SlabSpec {
+  int z0 = 0, nz = 0, Nzg = 0;
+  bool on = false;
+};
+
+static dirac_status create_sim(dirac_sim** out, int dims, const int N[3], const double dx[3], double dt,
+                               double m, const dirac_fields* fields, dirac_precision precision, unsigned flags,
+                               void* stream, const SlabSpec& slab);
+
 extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], const double dx[3],
                                      double dt, double m, const dirac_fields* fields,
                                      dirac_precision precision, unsigned flags, void* stream) {
+  return create_sim(out, dims, N, dx, dt, m, fields, precision, flags, stream, SlabSpec{});
+}
+
+static dirac_status create_sim(dirac_sim** out, int dims, const int N[3], const double dx[3], double dt,
+                               double m, const dirac_fields* fields, dirac_precision precision, unsigned flags,
+                               void* stream, const SlabSpec& slab) {
   if (!out) return fail(nullptr, DIRAC_ERR_INVALID, "out is NULL");
   *out = nullptr;
   if (dims != 2 && dims != 3) return fail(nullptr, DIRAC_ERR_INVALID, "dims must be 2 or 3");
@@ -466,6 +498,18 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
   s->f.V_static = nullptr;
   s->f.A_links = nullptr;
   s->stream = static_cast<cudaStream_t>(stream);
+  for (int a = 0; a < 3; ++a) s->Nf[a] = s->N[a];
+  if (slab.on) {  // N is the whole grid: store the slab's levels and two halo levels
+    s->N[2] = slab.nz + 2;
+    s->zlo = 1;
+    s->nzu = slab.nz;
+    s->zorg = slab.z0 - 1;
+    s->Nzg = slab.Nzg;
+  } else {
+    s->zlo = 0;
+    s->nzu = s->Nzg = s->N[2];
+    s->zorg = 0;
+  }
   s->ncell = cells_of(dims, s->N);
   s->pstride = round_up(s->ncell, 64);
   s->np = dims == 3 ? 8 : 4;
@@ -478,8 +522,12 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
   // a real soft core (with V0 and a Klein step, nothing else): analytic per
   // value in the FP32 kernels, no per-site data
   const bool softcore = f.sc_Z != 0.0 && f.sc_a != 0.0 && !vstatic && !layers && f.V0_imag == 0.0;
-  if (precision == DIRAC_FP32 && softcore && std::getenv("DIRAC_SOFTCORE_TABLE") == nullptr)
-    s->coef_mode = COEF_SOFTCORE;
+  // DIRAC_SOFTCORE selects how the FP32 kernels evaluate it: "analytic"
+  // (default), "corrected" or "table"
+  const char* sc_env = std::getenv("DIRAC_SOFTCORE");
+  const std::string sc_how = sc_env ? sc_env : "analytic";
+  if (precision == DIRAC_FP32 && softcore && (slab.on || sc_how != "table"))
+    s->coef_mode = sc_how == "corrected" && !slab.on ? COEF_SOFTCORR : COEF_SOFTCORE;
   else if ((vstatic && f.Vmod_amp == 0.0) || (!vstatic && (f.sc_Z != 0.0 || layers)))
     s->coef_mode = precision == DIRAC_FP32 ? COEF_TABLE : COEF_GENERAL;
   else if (vstatic || f.sc_Z != 0.0) s->coef_mode = COEF_GENERAL;
@@ -501,7 +549,7 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
     if (count == 1 && along != f.Apw_pol && others_zero) {
       s->link_mode = LINK_PLANE;
       s->ltab_axis = along;
-      s->ltab_n = 2 * s->N[along];
+      s->ltab_n = 2 * s->Nf[along];
     }
   }
   // any other time-independent vector potential: its link factors are
@@ -568,7 +616,7 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
     if ((e = cudaGetLastError()) != cudaSuccess) return cleanup_fail(cuda_fail(s, e, "link factor table"));
     s->launches += 1;
   }
-  if (s->coef_mode == COEF_SOFTCORE) {
+  if (s->coef_mode == COEF_SOFTCORE || s->coef_mode == COEF_SOFTCORR) {
     std::vector<float2> sq;
     softcore_tables(s, sq);
     if ((e = cudaMalloc(&s->sc_sq, sq.size() * sizeof(float2))) != cudaSuccess)
@@ -576,6 +624,33 @@ extern "C" dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], 
     // synchronous: the host vector goes out of scope
     if ((e = cudaMemcpy(s->sc_sq, sq.data(), sq.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
       return cleanup_fail(cuda_fail(s, e, "cudaMemcpy(soft-core tables)"));
+  }
+  if (s->coef_mode == COEF_SOFTCORR) {
+    // the correction records, built on the device; if one does not fit its
+    // 16 bits the simulation evaluates the soft core analytically instead
+    const size_t cb = (size_t)s->np * s->ncell * sizeof(unsigned);
+    int* flag = nullptr;
+    if ((e = cudaMalloc(&s->sc_corr, cb)) != cudaSuccess)
+      return cleanup_fail(cuda_fail(s, e, "cudaMalloc(soft-core corrections)"));
+    if ((e = cudaMalloc(&flag, sizeof(int))) != cudaSuccess)
+      return cleanup_fail(cuda_fail(s, e, "cudaMalloc(flag)"));
+    int over = 0;
+    e = cudaMemsetAsync(flag, 0, sizeof(int), s->stream);
+    if (e == cudaSuccess) {
+      launch_softcore_corr(s->sc_corr, half_fields<F32>(s, true, 0.0), half_fields<F32>(s, false, 0.0),
+                           field_desc(s), dims, s->N, flag, s->stream);
+      e = cudaGetLastError();
+      s->launches += 1;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&over, flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaFree(flag);
+    if (e != cudaSuccess) return cleanup_fail(cuda_fail(s, e, "soft-core corrections"));
+    if (over) {
+      cudaFree(s->sc_corr);
+      s->sc_corr = nullptr;
+      s->coef_mode = COEF_SOFTCORE;
+    }
   }
   if (s->coef_mode == COEF_TABLE) {
     if ((e = cudaMalloc(&s->b_tab, (size_t)s->np * s->pstride * sizeof(float4))) != cudaSuccess)
@@ -631,6 +706,7 @@ extern "C" void dirac_destroy(dirac_sim* s) {
   cudaFree(s->Vstatic);
   cudaFree(s->b_tab);
   cudaFree(s->sc_sq);
+  cudaFree(s->sc_corr);
   cudaFree(s->Alink);
   cudaFree(s->larr);
   cudaFree(s->ltab);
@@ -1158,6 +1234,10 @@ static dirac_status observe_launch(dirac_sim* s, int dens_axis, int dens_X, doub
   a.dens_axis = dens_axis;
   a.dens_X = dens_X;
   a.partials = s->partials;
+  a.zlo = s->zlo;
+  a.nzu = s->nzu;
+  a.zorg = s->zorg;
+  a.Nzg = s->Nzg;
   if (s->dims == 3) launch_observables<P, 3>(a, s->red_blocks, s->stream);
   else launch_observables<P, 2>(a, s->red_blocks, s->stream);
   CK(s, cudaGetLastError());
@@ -1288,10 +1368,11 @@ extern "C" dirac_status dirac_autotune(dirac_sim* s, dirac_plan* out) {
   const int n1 = fused_candidates(s->dims, s->N, 0, c1, kCandidates);
   const bool tb_ok = s->dims == 2 && !time_dependent_fields(s) &&
                      (s->coef_mode == COEF_UNIFORM || s->coef_mode == COEF_STEP ||
-                      s->coef_mode == COEF_TABLE || s->coef_mode == COEF_SOFTCORE) &&
+                      s->coef_mode == COEF_TABLE || s->coef_mode == COEF_SOFTCORE ||
+                      s->coef_mode == COEF_SOFTCORR) &&
                      (s->link_mode == LINK_NONE || s->link_mode == LINK_CONST) &&
-                     !((s->coef_mode == COEF_TABLE || s->coef_mode == COEF_SOFTCORE) &&
-                       s->link_mode == LINK_CONST);
+                     !((s->coef_mode == COEF_TABLE || s->coef_mode == COEF_SOFTCORE ||
+                        s->coef_mode == COEF_SOFTCORR) && s->link_mode == LINK_CONST);
   const int n2 = tb_ok ? fused_candidates(2, s->N, 1, c2, kCandidates) : 0;
   link_table<F32>(s, sim_time(s), s->stream);  // plane-wave links of the current step, if any
   cudaEvent_t e0, e1;
@@ -1420,8 +1501,226 @@ extern "C" double dirac_algorithmic_bytes(const dirac_sim* s) {
   if (!s) return 0.0;
   double b = 2.0 * s->np * (double)s->elem;                    // every value read and written once
   if (s->coef_mode == COEF_TABLE) b += 16.0 * s->np;           // one coefficient per value read
+  if (s->coef_mode == COEF_SOFTCORR) b += 4.0 * s->np;         // one correction word per value read
   if (s->coef_mode == COEF_GENERAL && s->Vstatic) b += 8.0 * s->np;  // one real per value read
   if (s->link_mode == LINK_TABLE) b += 32.0 * s->dims * s->np;  // up and down link factor (hi + lo) per axis
   else if (s->Alink) b += 16.0 * s->dims * s->np;              // up and down link integral per axis
   return b;
+}
+
+// ------------------------------------------------------------------ sub-domains
+// The grid split along z into slabs of consecutive levels (the paper's
+// parallelisation: spatial sub-domains with boundary exchange, Sect. 6).
+// Every slab is a simulation of its own levels plus one halo level on either
+// side; after every time step each slab's first and last own levels are
+// copied into the halo levels of its neighbours (periodic: the last slab's
+// upper neighbour is the first).  All slabs live on the calling device here;
+// the same exchange between devices would copy peer to peer.
+struct dirac_slabs {
+  int n = 0;
+  int N[3] = {1, 1, 1};
+  std::vector<dirac_sim*> sim;
+  std::vector<int> z0, nz;
+  cudaStream_t stream = nullptr;
+  std::string err;
+};
+
+extern "C" void dirac_slab_partition(int Nz, int nslabs, int k, int* z0, int* nz) {
+  // nslabs nearly equal slabs, the first Nz mod nslabs one level longer
+  if (nslabs < 1 || k < 0 || k >= nslabs || Nz < 0) {
+    if (z0) *z0 = 0;
+    if (nz) *nz = 0;
+    return;
+  }
+  const int q = Nz / nslabs, r = Nz % nslabs;
+  if (z0) *z0 = k * q + (k < r ? k : r);
+  if (nz) *nz = q + (k < r ? 1 : 0);
+}
+
+static dirac_status slabs_fail(dirac_slabs* g, dirac_status st, const std::string& msg) {
+  if (st == DIRAC_ERR_CUDA) cudaGetLastError();  // as cuda_fail: no stale error for later calls
+  if (g) g->err = msg;
+  else g_create_error = msg;
+  return st;
+}
+
+extern "C" void dirac_slabs_destroy(dirac_slabs* g) {
+  if (!g) return;
+  for (dirac_sim* s : g->sim) dirac_destroy(s);
+  delete g;
+}
+
+extern "C" dirac_status dirac_slabs_create(dirac_slabs** out, int nslabs, int dims, const int N[3],
+                                           const double dx[3], double dt, double m, const dirac_fields* fields,
+                                           dirac_precision precision, unsigned flags, void* stream) {
+  if (!out) return slabs_fail(nullptr, DIRAC_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (dims != 3 || !N) return slabs_fail(nullptr, DIRAC_ERR_UNSUPPORTED, "slabs: (3+1)D grids only");
+  if (precision != DIRAC_FP32 || (flags & DIRAC_FLAG_REFERENCE_KERNELS))
+    return slabs_fail(nullptr, DIRAC_ERR_UNSUPPORTED, "slabs: the FP32 fused kernels only");
+  if (nslabs < 1 || N[2] < nslabs) return slabs_fail(nullptr, DIRAC_ERR_INVALID, "slabs: need 1 <= nslabs <= N[2]");
+  if (fields) {
+    if (fields->V_static || fields->A_links || fields->abs_W != 0.0)
+      return slabs_fail(nullptr, DIRAC_ERR_UNSUPPORTED,
+                        "slabs: fields given per site (V_static, A_links) or absorbing layers are not decomposed");
+    const bool any_other_A = fields->A_const[0] != 0.0 || fields->A_const[1] != 0.0 || fields->A_const[2] != 0.0;
+    const bool pw_z = fields->Apw_amp == 0.0 ||
+                      (fields->Apw_k[0] == 0.0 && fields->Apw_k[1] == 0.0 && fields->Apw_pol != 2);
+    if (!pw_z || (fields->Apw_amp != 0.0 && any_other_A))
+      return slabs_fail(nullptr, DIRAC_ERR_UNSUPPORTED,
+                        "slabs: a vector potential must be constant or a plane wave along z");
+  }
+  dirac_slabs* g = new (std::nothrow) dirac_slabs();
+  if (!g) return slabs_fail(nullptr, DIRAC_ERR_OOM, "host allocation failed");
+  g->n = nslabs;
+  for (int a = 0; a < 3; ++a) g->N[a] = N[a];
+  g->stream = static_cast<cudaStream_t>(stream);
+  for (int k = 0; k < nslabs; ++k) {
+    SlabSpec sp;
+    sp.on = true;
+    dirac_slab_partition(N[2], nslabs, k, &sp.z0, &sp.nz);
+    sp.Nzg = N[2];
+    dirac_sim* s = nullptr;
+    dirac_status st = create_sim(&s, dims, N, dx, dt, m, fields, precision, flags, stream, sp);
+    if (st != DIRAC_OK) {
+      dirac_slabs_destroy(g);
+      return st;  // the message is in dirac_last_error(NULL)
+    }
+    g->sim.push_back(s);
+    g->z0.push_back(sp.z0);
+    g->nz.push_back(sp.nz);
+  }
+  *out = g;
+  return DIRAC_OK;
+}
+
+extern "C" const char* dirac_slabs_last_error(const dirac_slabs* g) {
+  if (!g) return g_create_error.c_str();
+  if (!g->err.empty()) return g->err.c_str();
+  for (dirac_sim* s : g->sim)
+    if (!s->err.empty()) return s->err.c_str();
+  return "";
+}
+
+extern "C" dirac_status dirac_slabs_info(const dirac_slabs* g, int k, int* z0, int* nz) {
+  if (!g || k < 0 || k >= g->n) return DIRAC_ERR_INVALID;
+  if (z0) *z0 = g->z0[k];
+  if (nz) *nz = g->nz[k];
+  return DIRAC_OK;
+}
+
+// copy one stored level of every plane from slab a into slab b (device to
+// device on the group's stream)
+static dirac_status copy_level(dirac_slabs* g, dirac_sim* a, int la, dirac_sim* b, int lb) {
+  const size_t lvl = (size_t)a->N[0] * a->N[1];
+  for (int p = 0; p < a->np; ++p) {
+    const float2* src = static_cast<const float2*>(a->state) + (long long)p * a->pstride + (long long)la * lvl;
+    float2* dst = static_cast<float2*>(b->state) + (long long)p * b->pstride + (long long)lb * lvl;
+    cudaError_t e = cudaMemcpyAsync(dst, src, lvl * sizeof(float2), cudaMemcpyDeviceToDevice, g->stream);
+    if (e != cudaSuccess) return slabs_fail(g, DIRAC_ERR_CUDA, std::string("halo copy: ") + cudaGetErrorString(e));
+  }
+  return DIRAC_OK;
+}
+
+// every slab's halo levels from its neighbours' own boundary levels
+static dirac_status exchange_halos(dirac_slabs* g) {
+  for (int k = 0; k < g->n; ++k) {
+    dirac_sim* s = g->sim[k];
+    dirac_sim* up = g->sim[(k + 1) % g->n];
+    dirac_sim* dn = g->sim[(k + g->n - 1) % g->n];
+    dirac_status st = copy_level(g, s, g->nz[k], up, 0);          // last own level -> upper neighbour's lower halo
+    if (st == DIRAC_OK) st = copy_level(g, s, 1, dn, dn->N[2] - 1); // first own level -> lower neighbour's upper halo
+    if (st != DIRAC_OK) return st;
+  }
+  return DIRAC_OK;
+}
+
+extern "C" dirac_status dirac_slabs_set_spinor(dirac_slabs* g, const double* host) {
+  if (!g || !host) return slabs_fail(g, DIRAC_ERR_INVALID, "NULL argument");
+  const long long lvl = (long long)g->N[0] * g->N[1];
+  const long long ncell = lvl * g->N[2];
+  for (int k = 0; k < g->n; ++k) {
+    dirac_sim* s = g->sim[k];
+    s->e_valid_at = -1;
+    for (int p = 0; p < s->np; ++p) {
+      // the slab's stored levels (halos included) of this plane, from the global state
+      for (int l = 0; l < s->N[2]; ++l) {
+        int gzl = (g->z0[k] - 1 + l) % g->N[2];
+        if (gzl < 0) gzl += g->N[2];
+        const double* src = host + 2 * ((long long)p * ncell + gzl * lvl);
+        cudaError_t e = cudaMemcpyAsync(s->staging + l * lvl, src, lvl * sizeof(double2), cudaMemcpyHostToDevice,
+                                        s->stream);
+        if (e != cudaSuccess) return slabs_fail(g, DIRAC_ERR_CUDA, std::string("set: ") + cudaGetErrorString(e));
+      }
+      launch_convert_in(s->staging, static_cast<float2*>(s->state) + (long long)p * s->pstride, s->ncell, s->stream);
+      s->launches += 1;
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return slabs_fail(g, DIRAC_ERR_CUDA, std::string("set: ") + cudaGetErrorString(e));
+    }
+    dirac_status st = take_reference(s);
+    if (st != DIRAC_OK) return st;
+  }
+  return DIRAC_OK;
+}
+
+extern "C" dirac_status dirac_slabs_get_spinor(dirac_slabs* g, double* host) {
+  if (!g || !host) return slabs_fail(g, DIRAC_ERR_INVALID, "NULL argument");
+  const long long lvl = (long long)g->N[0] * g->N[1];
+  const long long ncell = lvl * g->N[2];
+  for (int k = 0; k < g->n; ++k) {
+    dirac_sim* s = g->sim[k];
+    for (int p = 0; p < s->np; ++p) {
+      launch_convert_out(static_cast<const float2*>(s->state) + (long long)p * s->pstride, s->staging, s->ncell,
+                         s->stream);
+      s->launches += 1;
+      cudaError_t e = cudaGetLastError();
+      // own levels 1 .. nz only
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host + 2 * ((long long)p * ncell + (long long)g->z0[k] * lvl), s->staging + lvl,
+                            (size_t)g->nz[k] * lvl * sizeof(double2), cudaMemcpyDeviceToHost, s->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // one staging plane per slab
+      if (e != cudaSuccess) return slabs_fail(g, DIRAC_ERR_CUDA, std::string("get: ") + cudaGetErrorString(e));
+    }
+  }
+  return DIRAC_OK;
+}
+
+extern "C" dirac_status dirac_slabs_step(dirac_slabs* g, long nsteps) {
+  if (!g || nsteps < 0) return slabs_fail(g, DIRAC_ERR_INVALID, "bad arguments");
+  for (long i = 0; i < nsteps; ++i) {
+    for (int k = 0; k < g->n; ++k) {
+      dirac_status st = steps_fused<F32>(g->sim[k], 1, g->stream, i == nsteps - 1);
+      if (st != DIRAC_OK) return st;
+    }
+    dirac_status st = exchange_halos(g);
+    if (st != DIRAC_OK) return st;
+  }
+  return DIRAC_OK;
+}
+
+extern "C" dirac_status dirac_slabs_norm(dirac_slabs* g, double* E, double* naive) {
+  if (!g || !E) return slabs_fail(g, DIRAC_ERR_INVALID, "NULL argument");
+  double e = 0.0, nv = 0.0;
+  for (dirac_sim* s : g->sim) {  // E and the naive norm are sums over the slabs' own values
+    double es = 0.0, ns = 0.0;
+    dirac_status st = dirac_norm(s, &es, &ns);
+    if (st != DIRAC_OK) return st;
+    e += es;
+    nv += ns;
+  }
+  *E = e;
+  if (naive) *naive = nv;
+  return DIRAC_OK;
+}
+
+extern "C" dirac_status dirac_slabs_get_time(const dirac_slabs* g, double* t) {
+  if (!g || !t || g->sim.empty()) return DIRAC_ERR_INVALID;
+  return dirac_get_time(g->sim[0], t);
+}
+
+extern "C" long long dirac_slabs_kernel_launches(const dirac_slabs* g) {
+  long long n = 0;
+  if (g)
+    for (const dirac_sim* s : g->sim) n += s->launches;
+  return n;
 }

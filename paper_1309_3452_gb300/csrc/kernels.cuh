@@ -37,6 +37,14 @@ struct FusedArgs {
   // non-null: accumulate the conserved functional of the new state (per block
   // [sum |psi|^2, Re sum_lower conj(G) S'_G]; E = first + r_x second)
   double* e_partials;
+  // levels along the marching axis ((3+1)D: z): the kernel updates the nzu
+  // levels zlo .. zlo + nzu - 1 of the N[2] stored ones; a level k lies at
+  // global level (zorg + k) mod Nzg, where every field is evaluated.  A whole
+  // grid: zlo = 0, nzu = Nzg = N[2], zorg = 0 (periodic wrap of the stored
+  // levels); a slab of a decomposed grid: its own levels between one halo
+  // level on either side (zlo = 1, nzu = N[2] - 2), zorg = its first global
+  // level - 1
+  int zlo, nzu, zorg, Nzg;
 };
 constexpr int kFusedEMaxBlocks = 4096;  // capacity of the per-block E partials
 // (2+1)D fused kernel geometry
@@ -93,6 +101,7 @@ struct ObsArgs {
   double t_links;           // time of the upper sheet (t - dt/2)
   int dens_axis, dens_X;    // partial density: half-lattice index >= dens_X along axis
   double* partials;         // [gridDim.x][5]
+  int zlo, nzu, zorg, Nzg;  // (3+1)D levels summed and their global position, as in FusedArgs
 };
 constexpr int kObsSums = 5;
 
@@ -117,6 +126,12 @@ void launch_link_table(void* tab, int n, const FieldDesc& f, int dims, int axis,
 // {re hi, im hi, re lo, im lo}
 void launch_coef_table(float4* tab, const FieldDesc& f, int dims, const int N[3], long long pstride,
                        cudaStream_t s);
+
+// COEF_SOFTCORR correction records of a soft-core potential (one 32-bit word
+// per value, softcore_corr_index's layout); *overflow (device) is or-ed with 1
+// if a correction does not fit
+void launch_softcore_corr(unsigned* out, const HalfFields<F32>& hu, const HalfFields<F32>& hl, const FieldDesc& f,
+                          int dims, const int N[3], int* overflow, cudaStream_t s);
 
 // link integrals of an arbitrary vector potential (Sect. 4): raw = the
 // caller's integrals [axis][plane][cell] (canonical layout, cells dense), out

@@ -85,6 +85,9 @@ void launch(int dims, const int N[3], const double dx[3], double dt, double t,
   a.t_links = t - dt / 2.0;
   a.dens_axis = -1;
   a.partials = scratch;
+  a.zlo = 0;
+  a.nzu = a.Nzg = a.N[2];
+  a.zorg = 0;
   if (dims == 3) launch_observables<P, 3>(a, blocks, s);
   else launch_observables<P, 2>(a, blocks, s);
 }

@@ -59,7 +59,11 @@ __global__ void __launch_bounds__(256) observables_kernel(const ObsArgs<P> a) {
   const long long nxy = (long long)Nx * Ny;
   double acc[kObsSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if (x < Nx && y < Ny) {
-    for (int z = blockIdx.z; z < Nz; z += gridDim.z) {
+    // the summed levels zlo .. zlo + nzu - 1; fields at their global level
+    for (int zz = blockIdx.z; zz < (DIMS == 3 ? a.nzu : 1); zz += gridDim.z) {
+      const int z = DIMS == 3 ? a.zlo + zz : 0;
+      int zg = DIMS == 3 ? (a.zorg + z) % a.Nzg : 0;
+      if (zg < 0) zg += a.Nzg;
       const long long cell = z * nxy + (long long)y * Nx + x;
       const int j[3] = {x, y, z};
       const int Nn[3] = {Nx, Ny, Nz};
@@ -72,7 +76,7 @@ __global__ void __launch_bounds__(256) observables_kernel(const ObsArgs<P> a) {
         cn += n2;
         long long H[3];
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax) H[ax] = 2 * j[ax] + plane_off<DIMS>(plane, ax);
+        for (int ax = 0; ax < 3; ++ax) H[ax] = 2 * (ax == 2 ? zg : j[ax]) + plane_off<DIMS>(plane, ax);
         const long long hd = a.dens_axis == 0 ? H[0] : (a.dens_axis == 1 ? H[1] : H[2]);
         if (a.dens_axis >= 0 && hd >= a.dens_X) cd += n2;
         if (is_upper<DIMS>(plane)) continue;
@@ -87,7 +91,22 @@ __global__ void __launch_bounds__(256) observables_kernel(const ObsArgs<P> a) {
           C up = nb[cell + (long long)(jp - j[ax]) * stride[ax]];
           C dn = nb[cell + (long long)(jm - j[ax]) * stride[ax]];
           R re, im;
-          if (a.link_mode == LINK_GENERAL || a.link_mode == LINK_PLANE || a.link_mode == LINK_TABLE) {
+          if (a.link_mode == LINK_PLANE) {
+            // a plane wave with its wave vector across the polarisation (and no
+            // constant A on other axes): a phase on the polarisation axis only,
+            // the same for both links of the value (k has no component along them)
+            if (ax == a.f.Apw_pol) {
+              double sn, cs;
+              sincos(link_phase(a.f, DIMS, H, ax, +1, a.t_links), &sn, &cs);
+              const double2 u = widen(up), v = widen(dn);
+              // exp(-i phi) up - exp(+i phi) dn = cos phi (up - dn) - i sin phi (up + dn)
+              re = (R)(cs * (u.x - v.x) + sn * (u.y + v.y));
+              im = (R)(cs * (u.y - v.y) - sn * (u.x + v.x));
+            } else {
+              re = up.x - dn.x;
+              im = up.y - dn.y;
+            }
+          } else if (a.link_mode == LINK_GENERAL || a.link_mode == LINK_TABLE) {
             double2 u = mul_expm(widen(up), link_phase_site(a.f, DIMS, H, ax, +1, a.t_links, plane, cell));
             double2 v = mul_expm(widen(dn), -link_phase_site(a.f, DIMS, H, ax, -1, a.t_links, plane, cell));
             re = (R)(u.x - v.x);
@@ -186,6 +205,53 @@ __global__ void coef_table_kernel(float4* __restrict__ tab, const FieldDesc f, i
     const float rh = __double2float_rn(re), ih = __double2float_rn(im);
     tab[plane * pstride + c] =
         make_float4(rh, ih, __double2float_rn(re - (double)rh), __double2float_rn(im - (double)ih));
+  }
+}
+
+// COEF_SOFTCORR: the correction records (softcore_corr_index's layout) of a
+// real soft-core potential: per value, (exact b) - (the kernels' FP32
+// estimate softcore_fast2), b = 1/(1 + i dt (beta m + V)/2) with V from the
+// same FP64 potential function as the per-site path, rounded to an integer
+// multiple of 2^-35 per component and stored as two 16-bit integers; a value
+// out of the 16-bit range sets *overflow (the estimate was off by more than
+// the table can hold; the library then evaluates the soft core otherwise)
+template <int DIMS>
+__global__ void softcore_corr_kernel(unsigned* __restrict__ out, const HalfFields<F32> hu,
+                                     const HalfFields<F32> hl, const FieldDesc f, int N0, int N1, int N2,
+                                     int* overflow) {
+  constexpr int np = nplanes<DIMS>();
+  const int N[3] = {N0, N1, N2};
+  const long long ncell = (long long)N0 * N1 * N2;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell * np;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / np;
+    const int plane = (int)(i - r * np);
+    const int x = (int)(r % N0), y = (int)((r / N0) % N1), zr = (int)(r / ((long long)N0 * N1));
+    int yy = y, zz = zr;
+    const bool shifted = DIMS == 3 ? plane < 2 : plane == 0;
+    if (shifted) {
+      if (DIMS == 3) zz = zr + 1 == N2 ? 0 : zr + 1;
+      else yy = y + 1 == N1 ? 0 : y + 1;
+    }
+    const int H[3] = {2 * x + plane_off<DIMS>(plane, 0), 2 * yy + plane_off<DIMS>(plane, 1),
+                      DIMS == 3 ? 2 * zz + plane_off<DIMS>(plane, 2) : 0};
+    const bool upper = is_upper<DIMS>(plane);
+    const HalfFields<F32>& h = upper ? hu : hl;
+    float Rh, Rl;
+    softcore_R<DIMS>(h, H, Rh, Rl);
+    float2 re, im;
+    softcore_fast2(f2(Rh), f2(Rl), f2(softcore_t0(h, H).x), h.sc_K_hi, re, im);
+    const double V = potential_at(f, DIMS, H[0], H[1], H[2], 0, 0, plane, 0.0);
+    const double th = f.dt * ((upper ? 1.0 : -1.0) * f.m + V) * 0.5;
+    const double k = 1.0 / (1.0 + th * th);
+    long long q[2] = {llrint((k - (double)re.x) * 34359738368.0), llrint((-th * k - (double)im.x) * 34359738368.0)};
+    for (int c = 0; c < 2; ++c) {
+      if (q[c] > 32767 || q[c] < -32767) {
+        atomicOr(overflow, 1);
+        q[c] = q[c] > 0 ? 32767 : -32767;
+      }
+    }
+    out[i] = (unsigned)(q[0] & 0xffff) | ((unsigned)(q[1] & 0xffff) << 16);
   }
 }
 
@@ -299,6 +365,17 @@ void launch_coef_table(float4* tab, const FieldDesc& f, int dims, const int N[3]
     coef_table_kernel<3><<<grid, 256, 0, s>>>(tab, f, N[0], N[1], N[2], pstride);
   else
     coef_table_kernel<2><<<grid, 256, 0, s>>>(tab, f, N[0], N[1], 1, pstride);
+}
+
+void launch_softcore_corr(unsigned* out, const HalfFields<F32>& hu, const HalfFields<F32>& hl, const FieldDesc& f,
+                          int dims, const int N[3], int* overflow, cudaStream_t s) {
+  const long long n = (long long)N[0] * N[1] * (dims == 3 ? N[2] : 1) * (dims == 3 ? 8 : 4);
+  long long bx = (n + 255) / 256;
+  if (bx > 152 * 32) bx = 152 * 32;
+  if (dims == 3)
+    softcore_corr_kernel<3><<<(unsigned)bx, 256, 0, s>>>(out, hu, hl, f, N[0], N[1], N[2], overflow);
+  else
+    softcore_corr_kernel<2><<<(unsigned)bx, 256, 0, s>>>(out, hu, hl, f, N[0], N[1], 1, overflow);
 }
 
 void launch_link_integral_table(double* out, const double* raw, int dims, const int N[3], long long pstride,

@@ -39,10 +39,18 @@ namespace dirac {
 
 namespace {
 
-constexpr int TW = 34, TH = 15;        // (3+1)D tile in threads
+// (3+1)D tile height in threads (build-time choice): 15 rows with 512 threads
+// and two blocks per SM, or 30 rows with 1024 threads and one block per SM
+#ifndef DIRAC_TILE_ROWS
+#define DIRAC_TILE_ROWS 15
+#endif
+constexpr int TW = 34, TH = DIRAC_TILE_ROWS;  // (3+1)D tile in threads
 constexpr int CX = TW - 2, CY = TH - 2; // interior
-constexpr int kThreads3d = 512;
-constexpr int kSmemRows = 16;           // TH rows + the spare threads' row
+constexpr int kThreads3d = TH == 15 ? 512 : 1024;
+constexpr int kBlocks3d = TH == 15 ? 2 : 1;  // resident blocks per SM the registers are planned for
+constexpr int kSmemRows = TH + 1;       // TH rows + the spare threads' row
+static_assert(32 * CY + 2 * TW + 2 * CY <= kThreads3d && kThreads3d - 32 * CY - 2 * TW - 2 * CY < TW,
+              "interior rows as warps, the halo ring and fewer than a row of spare threads");
 
 template <class T>
 __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
@@ -105,8 +113,9 @@ __device__ __forceinline__ Thread3d thread3d() {
   return th;
 }
 
-__host__ __device__ __forceinline__ long long items3d(const int (&N)[3], int chunk) {
-  return (long long)((N[0] + CX - 1) / CX) * ((N[1] + CY - 1) / CY) * ((N[2] + chunk - 1) / chunk);
+// work items of a (3+1)D launch: tiles x chunks of the `levels` updated levels
+__host__ __device__ __forceinline__ long long items3d(const int (&N)[3], int levels, int chunk) {
+  return (long long)((N[0] + CX - 1) / CX) * ((N[1] + CY - 1) / CY) * ((levels + chunk - 1) / chunk);
 }
 
 // One work item (one tile over one chunk of z levels) of one simulation.
@@ -123,6 +132,12 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
   const int t = th.slot, lx = th.lx, ly = th.ly;
   const int sxm = th.sxm, sxp = th.sxp, sym = th.sym, syp = th.syp;
   const int Nx = a.N[0], Ny = a.N[1], Nz = a.N[2];
+  // global level of the stored level k (wrapped on the global grid), for the fields
+  auto gz = [&](int k) {
+    int g = a.zorg + k;
+    g %= a.Nzg;
+    return g < 0 ? g + a.Nzg : g;
+  };
   const int tiles_x = (Nx + CX - 1) / CX;
   const long long tiles = (long long)tiles_x * ((Ny + CY - 1) / CY);
   const bool iso = a.iso != 0;
@@ -130,8 +145,8 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
   const bool want_e = a.e_partials != nullptr;
   {
     const long long chunk = item / tiles, tile = item - chunk * tiles;
-    const int z0 = (int)chunk * a.chunk;
-    const int z1 = min(Nz, z0 + a.chunk);
+    const int z0 = a.zlo + (int)chunk * a.chunk;
+    const int z1 = min(a.zlo + a.nzu, z0 + a.chunk);
     const int gx = (int)(tile % tiles_x) * CX + lx - 1;
     const int gy = (int)(tile / tiles_x) * CY + ly - 1;
     const int x = wrapi(gx, Nx), y = wrapi(gy, Ny);
@@ -143,8 +158,9 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
     // (hx+1, hy+1) and (B0/D0, B1/D1) at (hx+1, hy), (hx, hy+1)
     // (kept in shared memory, one slot per thread: sRxy[t] = {Rd_h, Rd_l},
     // {Ra_h, Ra_l}, so that they take no registers through the z-march)
-    __shared__ __align__(16) float4 sRxy[COEF == COEF_SOFTCORE ? kThreads3d : 1][2];
-    if constexpr (COEF == COEF_SOFTCORE) {
+    constexpr bool kSoft = COEF == COEF_SOFTCORE || COEF == COEF_SOFTCORR;
+    __shared__ __align__(16) float4 sRxy[kSoft ? kThreads3d : 1][2];
+    if constexpr (kSoft) {
       const float2 x0 = __ldg(a.hu.sc_sq[0] + hx), x1 = __ldg(a.hu.sc_sq[0] + hx + 1);
       const float2 y0 = __ldg(a.hu.sc_sq[1] + hy), y1 = __ldg(a.hu.sc_sq[1] + hy + 1);
       const float2 d00 = padd(x0, y0), d11 = padd(x1, y1), a10 = padd(x1, y0), a01 = padd(x0, y1);
@@ -170,8 +186,7 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
       const int tid = threadIdx.x;
       if (tid >= 7) return;
       const int p = k & 1;
-      const int zk = k < 0 ? k + Nz : (k >= Nz ? k - Nz : k);
-      const int zn = k + 1 >= Nz ? k + 1 - Nz : (k + 1 < 0 ? k + 1 + Nz : k + 1);
+      const int zk = gz(k), zn = gz(k + 1);  // global levels: the tables are indexed by global Z
       if constexpr (LINK == LINK_PLANE_ZX) {
         if (tid < 4) {
           const int Z = tid == 0 ? 2 * zn : (tid == 3 ? 2 * zk : 2 * zk + 1);
@@ -182,7 +197,7 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
                        reinterpret_cast<const char*>(tab + Z) + 16 * q);
         }
       }
-      if constexpr (COEF == COEF_SOFTCORE) {
+      if constexpr (kSoft) {
         if (tid >= 4) {
           const int Z = tid == 4 ? 2 * zn : (tid == 5 ? 2 * zk + 1 : 2 * zk);
           cp_async8(&sZq[p][tid - 4], a.hu.sc_sq[2] + Z);
@@ -204,7 +219,24 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
         b[1] = lane_b(bb, 1);
       }
     };
-    constexpr bool kPre = COEF == COEF_SOFTCORE;  // coefficients computed in pairs
+    // COEF_SOFTCORR: the FP32 estimates of a pair plus the two values' words w0, w1
+    // of the correction record (R summed in softcore_R's order)
+    auto pair_bc = [&](const HalfFields<P>& h, int which, float2 z, const int (&H0)[3], const int (&H1)[3],
+                       long long rec, int slot, float4 (&b)[2]) {
+      if constexpr (COEF == COEF_SOFTCORR) {
+        // the pair's two words of the level's correction record (read where used)
+        const uint2 w = __ldg(reinterpret_cast<const uint2*>(a.hu.sc_corr + 8 * rec + slot));
+        const unsigned w0 = w.x, w1 = w.y;
+        const float4 r = sRxy[threadIdx.x][which];
+        const float2 Rh = padd(make_float2(r.x, r.y), f2(z.x)), Rl = padd(make_float2(r.z, r.w), f2(z.y));
+        float2 re, im;
+        softcore_fast2(Rh, Rl, make_float2(softcore_t0(h, H0).x, softcore_t0(h, H1).x), h.sc_K_hi, re, im);
+        const float2 c0 = corr_decode(w0), c1 = corr_decode(w1);
+        b[0] = make_float4(re.x, c0.x, im.x, c0.y);
+        b[1] = make_float4(re.y, c1.x, im.y, c1.y);
+      }
+    };
+    constexpr bool kPre = kSoft;  // coefficients computed in pairs
 
     auto load = [&](int k) {
       const int zk = k < 0 ? k + Nz : k;
@@ -231,7 +263,7 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
       sD[p][1][t] = ld(a.in[7] + o);
     }
     LevelLoad<C> cur = load(z0 - 1);
-    constexpr bool kStage = LINK == LINK_PLANE_ZX || COEF == COEF_SOFTCORE;
+    constexpr bool kStage = LINK == LINK_PLANE_ZX || kSoft;
     if (kStage) stage_level(z0 - 1);
 
     for (int k = z0 - 1; k < z1; ++k) {
@@ -239,13 +271,14 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
       const int zn = k + 1 >= Nz ? k + 1 - Nz : k + 1;
       const long long ok = zk * nxy + cxy, on = zn * nxy + cxy;
       const int pk = k & 1, pn = (k + 1) & 1, pm = (k - 1) & 1;
+      const int Zk = 2 * gz(k), Zn = 2 * gz(k + 1);  // half-lattice z of levels k, k+1 (global)
       sC[pn][0][t] = cur.C0;  // old C(k+1), D(k+1): z+ / x,y neighbours now,
       sC[pn][1][t] = cur.C1;  // own old values at the next level
       sD[pn][0][t] = cur.D0;
       sD[pn][1][t] = cur.D1;
       // prefetch the next level while this one computes (the soft-core kernels,
       // short of registers, issue it after the upper half-step instead)
-      constexpr bool kLate = COEF == COEF_SOFTCORE;
+      constexpr bool kLate = kSoft;
       LevelLoad<C> nxt = cur;
       if (!kLate && k + 1 < z1) nxt = load(k + 1);
       if (kStage && threadIdx.x < 7) cp_async_wait_all();  // this level's staged constants
@@ -259,8 +292,9 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
       C nA0n, nA1n, nB0k, nB1k;
       float4 bv[2];
       {
-        const int H0[3] = {hx, hy, 2 * zn}, H1[3] = {hx + 1, hy + 1, 2 * zn};
-        if constexpr (kPre) pair_b(a.hu, 0, sZq[pk][0], H0, H1, bv);
+        const int H0[3] = {hx, hy, Zn}, H1[3] = {hx + 1, hy + 1, Zn};
+        if constexpr (COEF == COEF_SOFTCORE) pair_b(a.hu, 0, sZq[pk][0], H0, H1, bv);
+        if constexpr (COEF == COEF_SOFTCORR) pair_bc(a.hu, 0, sZq[pk][0], H0, H1, ok, 0, bv);
         C nb0[6] = {cur.D0, sD[pn][0][sxm], cur.D1, sD[pn][1][sym], cur.C0, oC0};
         nA0n = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 0, cur.A0, nb0, H0, on, a.pstride,
                                              nullptr, kPre ? &bv[0] : nullptr, lkA);
@@ -269,8 +303,9 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
                                              nullptr, kPre ? &bv[1] : nullptr, lkA);
       }
       {
-        const int H0[3] = {hx + 1, hy, 2 * zk + 1}, H1[3] = {hx, hy + 1, 2 * zk + 1};
-        if constexpr (kPre) pair_b(a.hu, 1, sZq[pk][1], H0, H1, bv);
+        const int H0[3] = {hx + 1, hy, Zk + 1}, H1[3] = {hx, hy + 1, Zk + 1};
+        if constexpr (COEF == COEF_SOFTCORE) pair_b(a.hu, 1, sZq[pk][1], H0, H1, bv);
+        if constexpr (COEF == COEF_SOFTCORR) pair_bc(a.hu, 1, sZq[pk][1], H0, H1, ok, 2, bv);
         C nb0[6] = {sC[pk][0][sxp], oC0, oC1, sC[pk][1][sym], cur.D0, sD[pk][0][t]};
         nB0k = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 2, cur.B0, nb0, H0, ok, a.pstride,
                                              nullptr, kPre ? &bv[0] : nullptr, lkB);
@@ -296,8 +331,9 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
           const bool acc = want_e && core;  // this cell's new values count towards E
           float lc = 0.0f;
           {
-            const int H0[3] = {hx, hy, 2 * zk + 1}, H1[3] = {hx + 1, hy + 1, 2 * zk + 1};
-            if constexpr (kPre) pair_b(a.hl, 0, sZq[pk][1], H0, H1, bv);
+            const int H0[3] = {hx, hy, Zk + 1}, H1[3] = {hx + 1, hy + 1, Zk + 1};
+            if constexpr (COEF == COEF_SOFTCORE) pair_b(a.hl, 0, sZq[pk][1], H0, H1, bv);
+            if constexpr (COEF == COEF_SOFTCORR) pair_bc(a.hl, 0, sZq[pk][1], H0, H1, ok, 4, bv);
             const PL* lkC = lk_z ? &sLk[pk][2] : nullptr;
             C nb0[6] = {nB0k, sB[pk][0][sxm], nB1k, sB[pk][1][sym], nA0n, nA0};
             nC0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 4, oC0, nb0, H0, ok, a.pstride, &S,
@@ -309,8 +345,9 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
             if (acc) lc = fmaf(nC1.x, S.x, fmaf(nC1.y, S.y, lc));
           }
           {
-            const int H0[3] = {hx + 1, hy, 2 * zk}, H1[3] = {hx, hy + 1, 2 * zk};
-            if constexpr (kPre) pair_b(a.hl, 1, sZq[pk][2], H0, H1, bv);
+            const int H0[3] = {hx + 1, hy, Zk}, H1[3] = {hx, hy + 1, Zk};
+            if constexpr (COEF == COEF_SOFTCORE) pair_b(a.hl, 1, sZq[pk][2], H0, H1, bv);
+            if constexpr (COEF == COEF_SOFTCORR) pair_bc(a.hl, 1, sZq[pk][2], H0, H1, ok, 6, bv);
             const PL* lkD = lk_z ? &sLk[pk][3] : nullptr;
             C nb0[6] = {sA[pk][0][sxp], nA0, nA1, sA[pk][1][sym], nB0k, sB[pm][0][t]};
             nD0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 6, sD[pk][0][t], nb0, H0, ok,
@@ -379,10 +416,10 @@ __device__ __forceinline__ void block_store_e(double e_n, double e_c, double* ou
 }
 
 template <class P, int COEF, int LINK>
-__global__ void __launch_bounds__(kThreads3d, 2) fused3d_kernel(const FusedArgs<P> a) {
+__global__ void __launch_bounds__(kThreads3d, kBlocks3d) fused3d_kernel(const FusedArgs<P> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Thread3d th = thread3d();
-  const long long items = items3d(a.N, a.chunk);
+  const long long items = items3d(a.N, a.nzu, a.chunk);
   // running sums of the functional, one FP64 pair per thread, kept in shared
   // memory so that they take no registers in the z-march
   __shared__ double e_acc[kThreads3d][2];
@@ -416,7 +453,7 @@ __device__ __forceinline__ void copy_args(FusedArgs<P>* dst, const FusedArgs<P>*
 // simulations' items back to back; each block copies the arguments of the
 // simulation its current item belongs to into shared memory.
 template <class P, int COEF, int LINK>
-__global__ void __launch_bounds__(kThreads3d, 2) fused3d_batch_kernel(const BatchArgs<P> b) {
+__global__ void __launch_bounds__(kThreads3d, kBlocks3d) fused3d_batch_kernel(const BatchArgs<P> b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ FusedArgs<P> sa;
   const Thread3d th = thread3d();
@@ -457,23 +494,27 @@ __device__ __forceinline__ void row2d(const FusedArgs<P>& a, bool iso, int hx, i
   {
     C nb[6] = {V0n, shfl_up1(V0n), V1n, oV1, V0n, V0n};
     const int H[3] = {hx, 2 * yn, 0};
-    nU0n = site_update<P, 2, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 0, U0, nb, H, on, a.pstride);
+    nU0n = site_update<P, 2, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 0, U0, nb, H, on, a.pstride, nullptr,
+                                         nullptr, nullptr, a.N);
   }
   {
     C nb[6] = {shfl_down1(oV1), oV1, V0n, oV0, oV1, oV1};
     const int H[3] = {hx + 1, 2 * yk + 1, 0};
-    nU1k = site_update<P, 2, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 1, U1, nb, H, ok, a.pstride);
+    nU1k = site_update<P, 2, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 1, U1, nb, H, ok, a.pstride, nullptr,
+                                         nullptr, nullptr, a.N);
   }
   // lower: v1(k) from u1(k) (x), u0(k+1), u0(k) (y); v0(k) from u0(k) (x), u1(k), u1(k-1) (y)
   {
     C nb[6] = {nU1k, shfl_up1(nU1k), nU0n, nU0, nU1k, nU1k};
     const int H[3] = {hx, 2 * yk + 1, 0};
-    nV1 = site_update<P, 2, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 3, oV1, nb, H, ok, a.pstride, SV1);
+    nV1 = site_update<P, 2, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 3, oV1, nb, H, ok, a.pstride, SV1, nullptr,
+                                        nullptr, a.N);
   }
   {
     C nb[6] = {shfl_down1(nU0), nU0, nU1k, nU1, nU0, nU0};
     const int H[3] = {hx + 1, 2 * yk, 0};
-    nV0 = site_update<P, 2, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 2, oV0, nb, H, ok, a.pstride, SV0);
+    nV0 = site_update<P, 2, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 2, oV0, nb, H, ok, a.pstride, SV0, nullptr,
+                                        nullptr, a.N);
   }
 }
 
@@ -774,8 +815,11 @@ template <int COEF, int LINK>
 int launch3d(FusedArgs<F32> a, cudaStream_t s) {
   auto k = fused3d_kernel<F32, COEF, LINK>;
   const int resident = workers3d<fused3d_kernel<F32, COEF, LINK>>();
-  if (a.chunk <= 0 || a.chunk > a.N[2]) a.chunk = fused_chunk(3, a.N);
-  const long long items = items3d(a.N, a.chunk);
+  if (a.chunk <= 0 || a.chunk > a.nzu) {
+    const int Np[3] = {a.N[0], a.N[1], a.nzu};
+    a.chunk = fused_chunk(3, Np);
+  }
+  const long long items = items3d(a.N, a.nzu, a.chunk);
   a.workers = (int)(items < resident ? items : resident);
   // one E partial per block: never more blocks than the partials hold
   if (a.e_partials && a.workers > kFusedEMaxBlocks) a.workers = kFusedEMaxBlocks;
@@ -848,11 +892,17 @@ int dispatch(const FusedArgs<F32>& a, cudaStream_t s) {
     if (c == COEF_STEP) return launch3d<COEF_STEP, LINK_PLANE_ZX>(a, s);
     if (c == COEF_TABLE) return launch3d<COEF_TABLE, LINK_PLANE_ZX>(a, s);
     if (c == COEF_SOFTCORE) return launch3d<COEF_SOFTCORE, LINK_PLANE_ZX>(a, s);
+    if (c == COEF_SOFTCORR) return launch3d<COEF_SOFTCORR, LINK_PLANE_ZX>(a, s);
     return launch3d<kAnyMode, kAnyMode>(a, s);
   }
   if (c == COEF_SOFTCORE) {
     if (l == LINK_NONE) return launch_dims<DIMS, COEF_SOFTCORE, LINK_NONE>(a, s);
     if (l == LINK_PLANE) return launch_dims<DIMS, COEF_SOFTCORE, LINK_PLANE>(a, s);
+    return launch_dims<DIMS, kAnyMode, kAnyMode>(a, s);
+  }
+  if (c == COEF_SOFTCORR) {
+    if (l == LINK_NONE) return launch_dims<DIMS, COEF_SOFTCORR, LINK_NONE>(a, s);
+    if (l == LINK_PLANE) return launch_dims<DIMS, COEF_SOFTCORR, LINK_PLANE>(a, s);
     return launch_dims<DIMS, kAnyMode, kAnyMode>(a, s);
   }
   if (l == LINK_TABLE) {
@@ -902,6 +952,7 @@ int launch_fused2d_tb2(const FusedArgs<F32>& a, cudaStream_t s) {
   if (c == COEF_STEP && l == LINK_CONST) return launch2d_tb2<COEF_STEP, LINK_CONST>(a, s);
   if (c == COEF_TABLE && l == LINK_NONE) return launch2d_tb2<COEF_TABLE, LINK_NONE>(a, s);
   if (c == COEF_SOFTCORE && l == LINK_NONE) return launch2d_tb2<COEF_SOFTCORE, LINK_NONE>(a, s);
+  if (c == COEF_SOFTCORR && l == LINK_NONE) return launch2d_tb2<COEF_SOFTCORR, LINK_NONE>(a, s);
   return 0;
 }
 
@@ -951,7 +1002,7 @@ int fused_candidates(int dims, const int N[3], int two_step, int* out, int max) 
 
 long long fused_items(int dims, const int N[3], int chunk) {
   const int n[3] = {N[0], N[1], N[2]};
-  return dims == 3 ? items3d(n, chunk) : items2d(n, chunk);
+  return dims == 3 ? items3d(n, n[2], chunk) : items2d(n, chunk);
 }
 
 template <>

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(128) half_step_kernel(const HalfStepArgs<P> a)
       }
     }
     self[cell] = site_update<P, DIMS, COEF, LINK>(a.h, a.f, a.iso != 0, a.ry, a.rz, plane, self[cell],
-                                               nb, H, cell, a.pstride);
+                                               nb, H, cell, a.pstride, nullptr, nullptr, nullptr, a.N);
   }
 }
 
@@ -64,6 +64,10 @@ void launch_one(const HalfStepArgs<P>& a, cudaStream_t s) {
     half_step_kernel<P, DIMS, UPPER, COEF_SOFTCORE, LINK_NONE><<<grid, block, 0, s>>>(a);
   else if (f32 && c == COEF_SOFTCORE && l == LINK_PLANE)
     half_step_kernel<P, DIMS, UPPER, COEF_SOFTCORE, LINK_PLANE><<<grid, block, 0, s>>>(a);
+  else if (f32 && c == COEF_SOFTCORR && l == LINK_NONE)
+    half_step_kernel<P, DIMS, UPPER, COEF_SOFTCORR, LINK_NONE><<<grid, block, 0, s>>>(a);
+  else if (f32 && c == COEF_SOFTCORR && l == LINK_PLANE)
+    half_step_kernel<P, DIMS, UPPER, COEF_SOFTCORR, LINK_PLANE><<<grid, block, 0, s>>>(a);
   else if (f32 && c == COEF_TABLE && l == LINK_PLANE)
     half_step_kernel<P, DIMS, UPPER, COEF_TABLE, LINK_PLANE><<<grid, block, 0, s>>>(a);
   else if (f32 && c == COEF_UNIFORM && l == LINK_PLANE)

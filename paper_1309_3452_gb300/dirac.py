@@ -111,8 +111,38 @@ for _name in ("dirac_create", "dirac_set_spinor", "dirac_get_spinor", "dirac_set
     getattr(_lib, _name).restype = C.c_int
 
 
+_lib.dirac_slab_partition.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+_lib.dirac_slab_partition.restype = None
+_lib.dirac_slabs_create.argtypes = [C.POINTER(_vp), C.c_int, C.c_int, C.POINTER(C.c_int), _dp, C.c_double,
+                                    C.c_double, C.POINTER(Fields), C.c_int, C.c_uint, _vp]
+_lib.dirac_slabs_set_spinor.argtypes = [_vp, _dp]
+_lib.dirac_slabs_get_spinor.argtypes = [_vp, _dp]
+_lib.dirac_slabs_step.argtypes = [_vp, C.c_long]
+_lib.dirac_slabs_norm.argtypes = [_vp, _dp, _dp]
+_lib.dirac_slabs_info.argtypes = [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+_lib.dirac_slabs_get_time.argtypes = [_vp, _dp]
+_lib.dirac_slabs_kernel_launches.argtypes = [_vp]
+_lib.dirac_slabs_kernel_launches.restype = C.c_longlong
+_lib.dirac_slabs_last_error.argtypes = [_vp]
+_lib.dirac_slabs_last_error.restype = C.c_char_p
+_lib.dirac_slabs_destroy.argtypes = [_vp]
+for _name in ("dirac_slabs_create", "dirac_slabs_set_spinor", "dirac_slabs_get_spinor", "dirac_slabs_step",
+              "dirac_slabs_norm", "dirac_slabs_info", "dirac_slabs_get_time"):
+    getattr(_lib, _name).restype = C.c_int
+
+
 def lib():
     return _lib
+
+
+def slab_partition(Nz, nslabs):
+    """[(z0, nz)] of the slabs dirac_slabs_create uses (host only)."""
+    out = []
+    for k in range(nslabs):
+        z0, nz = C.c_int(), C.c_int()
+        _lib.dirac_slab_partition(int(Nz), int(nslabs), k, C.byref(z0), C.byref(nz))
+        out.append((z0.value, nz.value))
+    return out
 
 
 def _fields_struct(f):
@@ -289,6 +319,80 @@ class Sim:
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             _lib.dirac_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Slabs:
+    """A (3+1)D grid split along z into slabs stepped as sub-domains with halo
+    exchange (dirac_slabs_*); the same calls as Sim for the whole grid."""
+
+    def __init__(self, prob, nslabs, precision=FP32, flags=0, stream=None):
+        self.prob = prob
+        n = (C.c_int * 3)(*[int(v) for v in (list(prob.N) + [1, 1, 1])[:3]])
+        dx = (C.c_double * 3)(*[float(v) for v in (list(prob.dx) + [1.0, 1.0, 1.0])[:3]])
+        fs, keep = _fields_struct(prob.fields)
+        self._h = _vp()
+        st = stream if stream is not None else _current_stream()
+        rc = _lib.dirac_slabs_create(C.byref(self._h), int(nslabs), int(prob.dims), n, dx, float(prob.dt),
+                                     float(prob.m), C.byref(fs), int(precision), int(flags), st)
+        if rc != OK:
+            raise DiracError(rc, _lib.dirac_slabs_last_error(None).decode())
+        self.nslabs = int(nslabs)
+        del keep
+
+    def _check(self, rc):
+        if rc != OK:
+            raise DiracError(rc, _lib.dirac_slabs_last_error(self._h).decode())
+
+    def set_spinor(self, psi):
+        a = np.ascontiguousarray(psi, dtype=np.complex128)
+        if a.size != int(np.prod(self.prob.shape)):
+            raise ValueError("state has the wrong number of values")
+        self._check(_lib.dirac_slabs_set_spinor(self._h, a.ctypes.data_as(_dp)))
+
+    def get_spinor(self):
+        out = np.empty(self.prob.shape, np.complex128)
+        self._check(_lib.dirac_slabs_get_spinor(self._h, out.ctypes.data_as(_dp)))
+        return out
+
+    def step(self, n):
+        self._check(_lib.dirac_slabs_step(self._h, int(n)))
+
+    def norm(self):
+        E, naive = C.c_double(), C.c_double()
+        self._check(_lib.dirac_slabs_norm(self._h, C.byref(E), C.byref(naive)))
+        return E.value, naive.value
+
+    def info(self, k):
+        z0, nz = C.c_int(), C.c_int()
+        self._check(_lib.dirac_slabs_info(self._h, int(k), C.byref(z0), C.byref(nz)))
+        return z0.value, nz.value
+
+    @property
+    def time(self):
+        t = C.c_double()
+        self._check(_lib.dirac_slabs_get_time(self._h, C.byref(t)))
+        return t.value
+
+    @property
+    def launches(self):
+        return int(_lib.dirac_slabs_kernel_launches(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.dirac_slabs_destroy(self._h)
             self._h = _vp()
 
     def __del__(self):

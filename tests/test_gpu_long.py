@@ -55,6 +55,7 @@ def fields3(name, prob):
         "softcore_offgrid_step": W.Fields(sc_Z=0.8, sc_a=1.3, sc_center=(c[0] - 0.37, c[1] + 0.61, 9.13),
                                           V0=-0.1, step_axis=0, step_x0=N[0] / 2 + 0.25, step_V=0.4),
         "softcore_table": W.Fields(sc_Z=1.0, sc_a=1.0, sc_center=c),
+        "softcore_corrected": W.Fields(sc_Z=1.0, sc_a=1.0, sc_center=c),
         "Vstatic": W.Fields(V_static=W.random_potential(prob, 6, 0.4)),
         "absorb": W.Fields(V0=0.05, V0_imag=-0.002, abs_W=0.3, abs_width=4.0, abs_axes=7),
         "A_const": W.Fields(q=1.0, A_const=(0.3, -0.25, 0.15)),
@@ -64,6 +65,8 @@ def fields3(name, prob):
                           Apw_omega=kz, Apw_pol=0),
         "laser_table": W.Fields(sc_Z=1.0, sc_a=1.0, sc_center=c, q=1.0, Apw_amp=0.5, Apw_k=(0.0, 0.0, kz),
                                 Apw_omega=kz, Apw_pol=0),
+        "laser_corrected": W.Fields(sc_Z=1.0, sc_a=1.0, sc_center=c, q=1.0, Apw_amp=0.5, Apw_k=(0.0, 0.0, kz),
+                                   Apw_omega=kz, Apw_pol=0),
     }[name]
 
 
@@ -74,6 +77,7 @@ def fields2(name, prob):
     return {
         "klein": W.Fields(step_axis=0, step_x0=N[0] / 2 + 0.25, step_V=0.9),
         "softcore": W.Fields(sc_Z=1.0, sc_a=1.0, sc_center=c),
+        "softcore_corrected": W.Fields(sc_Z=1.0, sc_a=1.0, sc_center=c),
         "Vstatic": W.Fields(V_static=W.random_potential(prob, 6, 0.4)),
         "absorb": W.Fields(V0_imag=-0.002, abs_W=0.3, abs_width=8.0, abs_axes=3),
         "A_const": W.Fields(q=1.0, A_const=(0.3, -0.25, 0.0)),
@@ -84,15 +88,18 @@ def fields2(name, prob):
     }[name]
 
 
-# what each case runs on in the FP32 library (for the reader; the modes are
-# chosen by dirac_create from the fields)
-CONSERVED = {"V0", "klein_z", "klein", "softcore", "softcore_offgrid_step", "softcore_table", "Vstatic",
-             "A_const", "links"}
+# the cases whose functional E is conserved (real potentials, static vector potentials)
+CONSERVED = {"V0", "klein_z", "klein", "softcore", "softcore_offgrid_step", "softcore_table",
+             "softcore_corrected", "Vstatic", "A_const", "links"}
 
 
 def check_long(D, prob, name, seed, monkeypatch):
+    # the soft core's three FP32 evaluations: compensated analytic (default),
+    # FP32 estimate plus tabulated correction, per-site coefficient table
     if name.endswith("_table"):
-        monkeypatch.setenv("DIRAC_SOFTCORE_TABLE", "1")  # the tabulated-coefficient path instead
+        monkeypatch.setenv("DIRAC_SOFTCORE", "table")
+    elif name.endswith("_corrected"):
+        monkeypatch.setenv("DIRAC_SOFTCORE", "corrected")
     c = [n / 2.0 for n in prob.N]
     sigma = 5.0 if prob.dims == 3 else 14.0
     k0 = W.random_k0(seed)
@@ -115,16 +122,16 @@ def check_long(D, prob, name, seed, monkeypatch):
 
 
 @pytest.mark.parametrize("name", ["V0", "klein_z", "softcore", "softcore_offgrid_step", "softcore_table",
-                                  "Vstatic", "absorb", "A_const", "A_wave", "links", "laser",
-                                  "laser_table"])
+                                  "softcore_corrected", "Vstatic", "absorb", "A_const", "A_wave", "links", "laser",
+                                  "laser_table", "laser_corrected"])
 def test_fp32_1000_steps_3d(D, name, monkeypatch):
     prob = W.Problem(3, N3, (1.0, 1.0, 1.0), 0.9 * W.stability_limit(3), 1.0)
     prob = prob.with_fields(**vars(fields3(name, prob)))
     check_long(D, prob, name, 11, monkeypatch)
 
 
-@pytest.mark.parametrize("name", ["klein", "softcore", "Vstatic", "absorb", "A_const", "A_wave", "links",
-                                  "laser"])
+@pytest.mark.parametrize("name", ["klein", "softcore", "softcore_corrected", "Vstatic", "absorb", "A_const",
+                                  "A_wave", "links", "laser"])
 def test_fp32_1000_steps_2d(D, name, monkeypatch):
     prob = W.Problem(2, N2, (1.0, 1.0, 1.0), 0.9 * W.stability_limit(2), 0.4)
     prob = prob.with_fields(**vars(fields2(name, prob)))

@@ -401,16 +401,13 @@ def test_klein_negative_refraction(D, precision):
 def test_algorithmic_bytes_per_path(D, monkeypatch):
     """dirac_algorithmic_bytes: the state read and written once per step,
     plus one 16-byte coefficient per value read with a tabulated potential,
-    or one FP64 potential value with the per-site FP64 path; the analytic
-    soft core (compensated per-value evaluation) reads nothing per site."""
+    or one FP64 potential value with the per-site FP64 path."""
     p3 = W.Problem(3, (12, 10, 8), (1.0, 1.0, 1.0), 0.5, 0.3)
     p2 = W.Problem(2, (20, 18, 1), (1.0, 1.0, 1.0), 0.5, 0.3)
     soft = W.Fields(sc_Z=1.0, sc_a=1.0, sc_center=(6.0, 5.0, 4.0))
     soft2 = W.Fields(sc_Z=1.0, sc_a=1.0, sc_center=(10.0, 9.0, 0.0))
     absorb = W.Fields(V0_imag=-0.01, abs_W=0.2, abs_width=2.0, abs_axes=1)
     cases = [(p3, D.FP32, 128.0), (p2, D.FP32, 64.0), (p3, D.FP64, 256.0),
-             (p3.with_fields(**vars(soft)), D.FP32, 128.0),
-             (p2.with_fields(**vars(soft2)), D.FP32, 64.0),
              (p3.with_fields(**vars(absorb)), D.FP32, 128.0 + 128.0),
              (p3.with_fields(step_axis=0, step_x0=6.25, step_V=0.5), D.FP32, 128.0)]
     vstat = p3.with_fields(V_static=W.random_potential(p3, 1, 0.3), Vmod_amp=0.2, Vmod_omega=0.5)
@@ -418,10 +415,13 @@ def test_algorithmic_bytes_per_path(D, monkeypatch):
     for prob, prec, want in cases:
         with D.Sim(prob, prec) as s:
             assert s.algorithmic_bytes == want, (prob.fields, prec)
-    monkeypatch.setenv("DIRAC_SOFTCORE_TABLE", "1")  # the tabulated soft core
-    for prob, want in ((p3.with_fields(**vars(soft)), 256.0), (p2.with_fields(**vars(soft2)), 128.0)):
-        with D.Sim(prob, D.FP32) as s:
-            assert s.algorithmic_bytes == want
+    # the soft core's evaluations: analytic (the default, nothing per site),
+    # FP32 estimate with a 4-byte correction per value, per-site table (16 bytes)
+    for how, extra in (("analytic", 0.0), ("corrected", 4.0), ("table", 16.0)):
+        monkeypatch.setenv("DIRAC_SOFTCORE", how)
+        for prob, np_ in ((p3.with_fields(**vars(soft)), 8), (p2.with_fields(**vars(soft2)), 4)):
+            with D.Sim(prob, D.FP32) as s:
+                assert s.algorithmic_bytes == 16.0 * np_ + extra * np_, how
 
 
 @pytest.mark.parametrize("dims", [2, 3])
