@@ -447,6 +447,12 @@ long long dirac_slabs_kernel_launches(const dirac_slabs* g);
 const char* dirac_slabs_last_error(const dirac_slabs* g);
 void dirac_slabs_destroy(dirac_slabs* g);
 
+/* The current device's FP64 fused multiply-add rate in TFLOP/s (2 flops per
+   FMA), measured by a kernel of independent FP64 FMA chains (a few ms; no
+   memory traffic): the arithmetic ceiling the FP64 validation path is held
+   against.  The paper has no counterpart.  Synchronises the device. */
+dirac_status dirac_fp64_fma_rate(double* tflops);
+
 /* ABI version: DIRAC_ABI_VERSION of the header the library was built with.
    A client checks it against the header it was compiled with; the version
    changes whenever a structure or a signature does (2: dirac_fields gained

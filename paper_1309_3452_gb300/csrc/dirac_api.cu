@@ -1724,3 +1724,14 @@ extern "C" long long dirac_slabs_kernel_launches(const dirac_slabs* g) {
     for (const dirac_sim* s : g->sim) n += s->launches;
   return n;
 }
+
+extern "C" dirac_status dirac_fp64_fma_rate(double* tflops) {
+  if (!tflops) return fail(nullptr, DIRAC_ERR_INVALID, "NULL argument");
+  const double r = measure_fp64_fma_tflops();
+  if (r < 0.0) {
+    cudaGetLastError();
+    return fail(nullptr, DIRAC_ERR_CUDA, "FP64 rate measurement failed");
+  }
+  *tflops = r;
+  return DIRAC_OK;
+}

@@ -146,6 +146,9 @@ void launch_link_integral_table(double* out, const double* raw, int dims, const 
 void launch_link_factor_table(F32::Link* out, const FieldDesc& f, int dims, const int N[3], long long pstride,
                               cudaStream_t s);
 
+// measured FP64 FMA rate of the current device (TFLOP/s), < 0 on a CUDA failure
+double measure_fp64_fma_tflops();
+
 // canonical complex128 plane <-> device plane of the simulation precision
 void launch_convert_in(const double2* src, float2* dst, long long n, cudaStream_t s);
 void launch_convert_out(const float2* src, double2* dst, long long n, cudaStream_t s);

@@ -62,8 +62,9 @@ __global__ void __launch_bounds__(256) observables_kernel(const ObsArgs<P> a) {
     // the summed levels zlo .. zlo + nzu - 1; fields at their global level
     for (int zz = blockIdx.z; zz < (DIMS == 3 ? a.nzu : 1); zz += gridDim.z) {
       const int z = DIMS == 3 ? a.zlo + zz : 0;
-      int zg = DIMS == 3 ? (a.zorg + z) % a.Nzg : 0;
+      int zg = DIMS == 3 ? a.zorg + z : 0;  // in [-1, 2 Nzg): one wrap at most
       if (zg < 0) zg += a.Nzg;
+      else if (zg >= a.Nzg) zg -= a.Nzg;
       const long long cell = z * nxy + (long long)y * Nx + x;
       const int j[3] = {x, y, z};
       const int Nn[3] = {Nx, Ny, Nz};
@@ -324,7 +325,56 @@ __global__ void convert_out_kernel(const float2* __restrict__ src, double2* __re
     dst[i] = make_double2(src[i].x, src[i].y);
 }
 
+// FP64 FMA throughput: eight independent dependency chains of fused
+// multiply-adds per thread (the FP64 pipe stays busy, nothing is read from
+// memory); the result is stored only if it matches an impossible value, so
+// the compiler keeps every operation
+__global__ void __launch_bounds__(256) fp64_fma_rate_kernel(double* out, int iters) {
+  const double m = 0.9999999999, c = 1e-12;
+  double a[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = 1e-3 * (threadIdx.x + 1) + j;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = fma(a[j], m, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += a[j];
+  if (s == -1.0) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace
+
+// measured FP64 FMA rate of the current device in FP64 TFLOP/s (2 flops per
+// FMA), or a negative value if a CUDA call failed
+double measure_fp64_fma_tflops() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return -1.0;
+  double* sink = nullptr;
+  const int blocks = 8 * sms, threads = 256, iters = 4096;
+  if (cudaMalloc(&sink, sizeof(double) * blocks * threads) != cudaSuccess) return -1.0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {  // the first launch warms up
+    cudaEventRecord(e0);
+    fp64_fma_rate_kernel<<<blocks, threads>>>(sink, iters);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  const bool ok = cudaGetLastError() == cudaSuccess;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (!ok || best <= 0.0f) return -1.0;
+  return 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e12;
+}
 
 int observables_blocks(const int N[3], int dims) {
   const int gx = (N[0] + 31) / 32, gy = (N[1] + 7) / 8;

@@ -132,11 +132,11 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
   const int t = th.slot, lx = th.lx, ly = th.ly;
   const int sxm = th.sxm, sxp = th.sxp, sym = th.sym, syp = th.syp;
   const int Nx = a.N[0], Ny = a.N[1], Nz = a.N[2];
-  // global level of the stored level k (wrapped on the global grid), for the fields
+  // global level of the stored level k (wrapped on the global grid), for the
+  // fields; zorg + k lies in [-1, 2 Nzg) (zorg in [-1, Nzg), k <= N[2] <= Nzg + 1)
   auto gz = [&](int k) {
-    int g = a.zorg + k;
-    g %= a.Nzg;
-    return g < 0 ? g + a.Nzg : g;
+    const int g = a.zorg + k;
+    return g < 0 ? g + a.Nzg : (g >= a.Nzg ? g - a.Nzg : g);
   };
   const int tiles_x = (Nx + CX - 1) / CX;
   const long long tiles = (long long)tiles_x * ((Ny + CY - 1) / CY);
@@ -276,11 +276,9 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
       sC[pn][1][t] = cur.C1;  // own old values at the next level
       sD[pn][0][t] = cur.D0;
       sD[pn][1][t] = cur.D1;
-      // prefetch the next level while this one computes (the soft-core kernels,
-      // short of registers, issue it after the upper half-step instead)
-      constexpr bool kLate = kSoft;
+      // prefetch the next level while this one computes
       LevelLoad<C> nxt = cur;
-      if (!kLate && k + 1 < z1) nxt = load(k + 1);
+      if (k + 1 < z1) nxt = load(k + 1);
       if (kStage && threadIdx.x < 7) cp_async_wait_all();  // this level's staged constants
       __syncthreads();
       if (kStage && k + 1 < z1) stage_level(k + 1);
@@ -317,7 +315,6 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
       sB[pk][1][t] = nB1k;
       sA[pn][0][t] = nA0n;
       sA[pn][1][t] = nA1n;
-      if (kLate && k + 1 < z1) nxt = load(k + 1);
       __syncthreads();
 
       // lower half-step: C(k) from A(k+1), A(k), B(k); D(k) from B(k), B(k-1), A(k)

@@ -131,8 +131,21 @@ for _name in ("dirac_slabs_create", "dirac_slabs_set_spinor", "dirac_slabs_get_s
     getattr(_lib, _name).restype = C.c_int
 
 
+_lib.dirac_fp64_fma_rate.argtypes = [_dp]
+_lib.dirac_fp64_fma_rate.restype = C.c_int
+
+
 def lib():
     return _lib
+
+
+def fp64_fma_rate():
+    """Measured FP64 FMA rate of the current device, TFLOP/s (dirac_fp64_fma_rate)."""
+    r = C.c_double()
+    rc = _lib.dirac_fp64_fma_rate(C.byref(r))
+    if rc != OK:
+        raise DiracError(rc, _lib.dirac_last_error(None).decode())
+    return r.value
 
 
 def slab_partition(Nz, nslabs):
