@@ -407,22 +407,25 @@ dirac_status dirac_norm_noalloc(int dims, const int N[3], const double dx[3], do
 
 /*
  * Sub-domain decomposition (Sect. 6: the scheme is parallelised by spatial
- * sub-domains that exchange their boundary values).  A (3+1)D grid is split
- * along z into nslabs slabs of consecutive levels (dirac_slab_partition);
- * every slab is stepped by the fused kernel as its own sub-domain, which
- * stores one halo level on either side, and after every time step each slab's
- * first and last own levels are copied into its neighbours' halo levels
- * (periodic along z).  Fields are evaluated at every value's position on the
+ * sub-domains that exchange their boundary values).  A grid is split along
+ * its marching axis (z in (3+1)D, y in (2+1)D) into nslabs slabs of
+ * consecutive levels (dirac_slab_partition); every slab is stepped by the
+ * fused one-step kernel as its own sub-domain, which stores one halo level on
+ * either side, and after every time step each slab's first and last own
+ * levels are copied into its neighbours' halo levels (periodic).  Fields are evaluated at every value's position on the
  * whole grid, so the stepped state equals, bit for bit, that of the whole
  * grid stepped as one simulation.  All slabs live on the calling device and
- * run on cuda_stream; the halo copies are device-to-device copies of Nx*Ny
- * values per plane and level, the data a multi-device split would exchange.
+ * run on cuda_stream; the halo copies are device-to-device copies of one
+ * level (Nx*Ny values in (3+1)D, Nx in (2+1)D) per plane and direction, the
+ * data a multi-device split would exchange.
  *
- * dirac_slabs_create: as dirac_create for the whole grid N (dims == 3, FP32
- *   only, 1 <= nslabs <= N[2]); fields given per site (V_static, A_links) and
- *   absorbing layers are not decomposed, and a vector potential must be
- *   constant or a plane wave with its wave vector along z
- *   (DIRAC_ERR_UNSUPPORTED); a soft core is evaluated analytically.
+ * dirac_slabs_create: as dirac_create for the whole grid N (FP32 only,
+ *   1 <= nslabs <= N[2] in (3+1)D, N[1] in (2+1)D); fields given per site
+ *   (V_static, A_links), absorbing layers and vector potentials that would
+ *   need a per-site table (static A other than a constant or a plane wave
+ *   across its polarisation) are not decomposed (DIRAC_ERR_UNSUPPORTED); a
+ *   soft core is evaluated analytically; (2+1)D slabs take one time step per
+ *   pass.
  * set/get_spinor: the whole grid in the canonical host layout (as
  *   dirac_set_spinor / dirac_get_spinor; get synchronises).
  * step: nsteps time steps of every slab, each followed by the halo exchange.

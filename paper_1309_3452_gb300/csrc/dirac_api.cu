@@ -499,15 +499,17 @@ static dirac_status create_sim(dirac_sim** out, int dims, const int N[3], const 
   s->f.A_links = nullptr;
   s->stream = static_cast<cudaStream_t>(stream);
   for (int a = 0; a < 3; ++a) s->Nf[a] = s->N[a];
+  const int march = dims == 3 ? 2 : 1;  // the fused kernels' marching axis
   if (slab.on) {  // N is the whole grid: store the slab's levels and two halo levels
-    s->N[2] = slab.nz + 2;
+    s->N[march] = slab.nz + 2;
     s->zlo = 1;
     s->nzu = slab.nz;
     s->zorg = slab.z0 - 1;
     s->Nzg = slab.Nzg;
+    s->tblock = 0;  // two-step passes would need two halo levels
   } else {
     s->zlo = 0;
-    s->nzu = s->Nzg = s->N[2];
+    s->nzu = s->Nzg = s->N[march];
     s->zorg = 0;
   }
   s->ncell = cells_of(dims, s->N);
@@ -848,7 +850,9 @@ static dirac_status steps_fused(dirac_sim* s, long n, cudaStream_t st, bool want
   want_e = want_e && n > 0 && std::getenv("DIRAC_NO_FUSED_NORM") == nullptr;
   int e_blocks = 0;
   // (2+1)D, time-independent fields: two steps per pass while pairs remain
-  const bool tb = s->dims == 2 && s->tblock && !time_dependent_fields(s) &&
+  // (the two-step kernel takes whole grids: never a slab of a decomposed one)
+  const bool whole = s->zlo == 0 && s->zorg == 0 && s->nzu == s->Nzg;
+  const bool tb = s->dims == 2 && s->tblock && whole && !time_dependent_fields(s) &&
                   std::getenv("DIRAC_NO_TEMPORAL_BLOCKING") == nullptr;
   while (tb && n >= 2) {
     FusedArgs<P> a = fused_args<P>(s, sim_time(s));
@@ -1366,7 +1370,7 @@ extern "C" dirac_status dirac_autotune(dirac_sim* s, dirac_plan* out) {
   constexpr int kCandidates = 6;
   int c1[kCandidates], c2[kCandidates];
   const int n1 = fused_candidates(s->dims, s->N, 0, c1, kCandidates);
-  const bool tb_ok = s->dims == 2 && !time_dependent_fields(s) &&
+  const bool tb_ok = s->dims == 2 && s->zlo == 0 && s->nzu == s->Nzg && !time_dependent_fields(s) &&
                      (s->coef_mode == COEF_UNIFORM || s->coef_mode == COEF_STEP ||
                       s->coef_mode == COEF_TABLE || s->coef_mode == COEF_SOFTCORE ||
                       s->coef_mode == COEF_SOFTCORR) &&
@@ -1518,6 +1522,8 @@ extern "C" double dirac_algorithmic_bytes(const dirac_sim* s) {
 // the same exchange between devices would copy peer to peer.
 struct dirac_slabs {
   int n = 0;
+  int dims = 3;
+  int march = 2;              // split axis: z in (3+1)D, y in (2+1)D
   int N[3] = {1, 1, 1};
   std::vector<dirac_sim*> sim;
   std::vector<int> z0, nz;
@@ -1555,36 +1561,40 @@ extern "C" dirac_status dirac_slabs_create(dirac_slabs** out, int nslabs, int di
                                            dirac_precision precision, unsigned flags, void* stream) {
   if (!out) return slabs_fail(nullptr, DIRAC_ERR_INVALID, "out is NULL");
   *out = nullptr;
-  if (dims != 3 || !N) return slabs_fail(nullptr, DIRAC_ERR_UNSUPPORTED, "slabs: (3+1)D grids only");
+  if ((dims != 2 && dims != 3) || !N) return slabs_fail(nullptr, DIRAC_ERR_INVALID, "slabs: dims must be 2 or 3");
   if (precision != DIRAC_FP32 || (flags & DIRAC_FLAG_REFERENCE_KERNELS))
     return slabs_fail(nullptr, DIRAC_ERR_UNSUPPORTED, "slabs: the FP32 fused kernels only");
-  if (nslabs < 1 || N[2] < nslabs) return slabs_fail(nullptr, DIRAC_ERR_INVALID, "slabs: need 1 <= nslabs <= N[2]");
-  if (fields) {
-    if (fields->V_static || fields->A_links || fields->abs_W != 0.0)
-      return slabs_fail(nullptr, DIRAC_ERR_UNSUPPORTED,
-                        "slabs: fields given per site (V_static, A_links) or absorbing layers are not decomposed");
-    const bool any_other_A = fields->A_const[0] != 0.0 || fields->A_const[1] != 0.0 || fields->A_const[2] != 0.0;
-    const bool pw_z = fields->Apw_amp == 0.0 ||
-                      (fields->Apw_k[0] == 0.0 && fields->Apw_k[1] == 0.0 && fields->Apw_pol != 2);
-    if (!pw_z || (fields->Apw_amp != 0.0 && any_other_A))
-      return slabs_fail(nullptr, DIRAC_ERR_UNSUPPORTED,
-                        "slabs: a vector potential must be constant or a plane wave along z");
-  }
+  const int march = dims == 3 ? 2 : 1;  // z in (3+1)D, y in (2+1)D
+  if (nslabs < 1 || N[march] < nslabs)
+    return slabs_fail(nullptr, DIRAC_ERR_INVALID, "slabs: need 1 <= nslabs <= the grid's extent along z (y in (2+1)D)");
+  if (fields && (fields->V_static || fields->A_links || fields->abs_W != 0.0))
+    return slabs_fail(nullptr, DIRAC_ERR_UNSUPPORTED,
+                      "slabs: fields given per site (V_static, A_links) or absorbing layers are not decomposed");
   dirac_slabs* g = new (std::nothrow) dirac_slabs();
   if (!g) return slabs_fail(nullptr, DIRAC_ERR_OOM, "host allocation failed");
   g->n = nslabs;
-  for (int a = 0; a < 3; ++a) g->N[a] = N[a];
+  g->dims = dims;
+  g->march = march;
+  for (int a = 0; a < 3; ++a) g->N[a] = a < dims ? N[a] : 1;
   g->stream = static_cast<cudaStream_t>(stream);
   for (int k = 0; k < nslabs; ++k) {
     SlabSpec sp;
     sp.on = true;
-    dirac_slab_partition(N[2], nslabs, k, &sp.z0, &sp.nz);
-    sp.Nzg = N[2];
+    dirac_slab_partition(N[march], nslabs, k, &sp.z0, &sp.nz);
+    sp.Nzg = N[march];
     dirac_sim* s = nullptr;
     dirac_status st = create_sim(&s, dims, N, dx, dt, m, fields, precision, flags, stream, sp);
     if (st != DIRAC_OK) {
       dirac_slabs_destroy(g);
       return st;  // the message is in dirac_last_error(NULL)
+    }
+    if (s->link_mode == LINK_TABLE || s->coef_mode == COEF_TABLE || s->coef_mode == COEF_GENERAL) {
+      // per-site tables are laid out on the stored cells: not decomposed
+      dirac_destroy(s);
+      dirac_slabs_destroy(g);
+      return slabs_fail(nullptr, DIRAC_ERR_UNSUPPORTED,
+                        "slabs: fields that need per-site tables (a static vector potential that is not a "
+                        "plane wave across its polarisation) are not decomposed");
     }
     g->sim.push_back(s);
     g->z0.push_back(sp.z0);
@@ -1612,7 +1622,7 @@ extern "C" dirac_status dirac_slabs_info(const dirac_slabs* g, int k, int* z0, i
 // copy one stored level of every plane from slab a into slab b (device to
 // device on the group's stream)
 static dirac_status copy_level(dirac_slabs* g, dirac_sim* a, int la, dirac_sim* b, int lb) {
-  const size_t lvl = (size_t)a->N[0] * a->N[1];
+  const size_t lvl = g->march == 2 ? (size_t)a->N[0] * a->N[1] : (size_t)a->N[0];  // values per level
   for (int p = 0; p < a->np; ++p) {
     const float2* src = static_cast<const float2*>(a->state) + (long long)p * a->pstride + (long long)la * lvl;
     float2* dst = static_cast<float2*>(b->state) + (long long)p * b->pstride + (long long)lb * lvl;
@@ -1628,8 +1638,9 @@ static dirac_status exchange_halos(dirac_slabs* g) {
     dirac_sim* s = g->sim[k];
     dirac_sim* up = g->sim[(k + 1) % g->n];
     dirac_sim* dn = g->sim[(k + g->n - 1) % g->n];
-    dirac_status st = copy_level(g, s, g->nz[k], up, 0);          // last own level -> upper neighbour's lower halo
-    if (st == DIRAC_OK) st = copy_level(g, s, 1, dn, dn->N[2] - 1); // first own level -> lower neighbour's upper halo
+    dirac_status st = copy_level(g, s, g->nz[k], up, 0);  // last own level -> upper neighbour's lower halo
+    if (st == DIRAC_OK)
+      st = copy_level(g, s, 1, dn, dn->N[g->march] - 1);  // first own level -> lower neighbour's upper halo
     if (st != DIRAC_OK) return st;
   }
   return DIRAC_OK;
@@ -1637,16 +1648,17 @@ static dirac_status exchange_halos(dirac_slabs* g) {
 
 extern "C" dirac_status dirac_slabs_set_spinor(dirac_slabs* g, const double* host) {
   if (!g || !host) return slabs_fail(g, DIRAC_ERR_INVALID, "NULL argument");
-  const long long lvl = (long long)g->N[0] * g->N[1];
-  const long long ncell = lvl * g->N[2];
+  const long long lvl = g->march == 2 ? (long long)g->N[0] * g->N[1] : (long long)g->N[0];
+  const long long ncell = (long long)g->N[0] * g->N[1] * g->N[2];
+  const int Ng = g->N[g->march];
   for (int k = 0; k < g->n; ++k) {
     dirac_sim* s = g->sim[k];
     s->e_valid_at = -1;
     for (int p = 0; p < s->np; ++p) {
       // the slab's stored levels (halos included) of this plane, from the global state
-      for (int l = 0; l < s->N[2]; ++l) {
-        int gzl = (g->z0[k] - 1 + l) % g->N[2];
-        if (gzl < 0) gzl += g->N[2];
+      for (int l = 0; l < s->N[g->march]; ++l) {
+        int gzl = (g->z0[k] - 1 + l) % Ng;
+        if (gzl < 0) gzl += Ng;
         const double* src = host + 2 * ((long long)p * ncell + gzl * lvl);
         cudaError_t e = cudaMemcpyAsync(s->staging + l * lvl, src, lvl * sizeof(double2), cudaMemcpyHostToDevice,
                                         s->stream);
@@ -1665,8 +1677,8 @@ extern "C" dirac_status dirac_slabs_set_spinor(dirac_slabs* g, const double* hos
 
 extern "C" dirac_status dirac_slabs_get_spinor(dirac_slabs* g, double* host) {
   if (!g || !host) return slabs_fail(g, DIRAC_ERR_INVALID, "NULL argument");
-  const long long lvl = (long long)g->N[0] * g->N[1];
-  const long long ncell = lvl * g->N[2];
+  const long long lvl = g->march == 2 ? (long long)g->N[0] * g->N[1] : (long long)g->N[0];
+  const long long ncell = (long long)g->N[0] * g->N[1] * g->N[2];
   for (int k = 0; k < g->n; ++k) {
     dirac_sim* s = g->sim[k];
     for (int p = 0; p < s->np; ++p) {

@@ -37,13 +37,14 @@ struct FusedArgs {
   // non-null: accumulate the conserved functional of the new state (per block
   // [sum |psi|^2, Re sum_lower conj(G) S'_G]; E = first + r_x second)
   double* e_partials;
-  // levels along the marching axis ((3+1)D: z): the kernel updates the nzu
-  // levels zlo .. zlo + nzu - 1 of the N[2] stored ones; a level k lies at
-  // global level (zorg + k) mod Nzg, where every field is evaluated.  A whole
-  // grid: zlo = 0, nzu = Nzg = N[2], zorg = 0 (periodic wrap of the stored
-  // levels); a slab of a decomposed grid: its own levels between one halo
-  // level on either side (zlo = 1, nzu = N[2] - 2), zorg = its first global
-  // level - 1
+  // levels along the marching axis ((3+1)D: z, (2+1)D: y): the kernel updates
+  // the nzu levels zlo .. zlo + nzu - 1 of the N[axis] stored ones; a level k
+  // lies at global level (zorg + k) mod Nzg, where every field is evaluated.
+  // A whole grid: zlo = 0, nzu = Nzg = N[axis], zorg = 0 (periodic wrap of
+  // the stored levels); a slab of a decomposed grid: its own levels between
+  // one halo level on either side (zlo = 1, nzu = N[axis] - 2), zorg = its
+  // first global level - 1.  (The two-step (2+1)D kernel and the batched
+  // kernels take whole grids only.)
   int zlo, nzu, zorg, Nzg;
 };
 constexpr int kFusedEMaxBlocks = 4096;  // capacity of the per-block E partials
@@ -101,7 +102,7 @@ struct ObsArgs {
   double t_links;           // time of the upper sheet (t - dt/2)
   int dens_axis, dens_X;    // partial density: half-lattice index >= dens_X along axis
   double* partials;         // [gridDim.x][5]
-  int zlo, nzu, zorg, Nzg;  // (3+1)D levels summed and their global position, as in FusedArgs
+  int zlo, nzu, zorg, Nzg;  // levels summed along the marching axis and their global position, as in FusedArgs
 };
 constexpr int kObsSums = 5;
 

@@ -86,7 +86,7 @@ void launch(int dims, const int N[3], const double dx[3], double dt, double t,
   a.dens_axis = -1;
   a.partials = scratch;
   a.zlo = 0;
-  a.nzu = a.Nzg = a.N[2];
+  a.nzu = a.Nzg = dims == 3 ? a.N[2] : a.N[1];  // every level of the marching axis
   a.zorg = 0;
   if (dims == 3) launch_observables<P, 3>(a, blocks, s);
   else launch_observables<P, 2>(a, blocks, s);

@@ -58,7 +58,15 @@ __global__ void __launch_bounds__(256) observables_kernel(const ObsArgs<P> a) {
   const int Nx = a.N[0], Ny = a.N[1], Nz = DIMS == 3 ? a.N[2] : 1;
   const long long nxy = (long long)Nx * Ny;
   double acc[kObsSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  if (x < Nx && y < Ny) {
+  // (2+1)D: the summed rows zlo .. zlo + nzu - 1, fields at the global row
+  const bool row_in = DIMS == 3 || (y >= a.zlo && y < a.zlo + a.nzu);
+  int yg = y;
+  if (DIMS == 2) {
+    yg = a.zorg + y;  // in [-1, 2 Nzg): one wrap at most
+    if (yg < 0) yg += a.Nzg;
+    else if (yg >= a.Nzg) yg -= a.Nzg;
+  }
+  if (x < Nx && y < Ny && row_in) {
     // the summed levels zlo .. zlo + nzu - 1; fields at their global level
     for (int zz = blockIdx.z; zz < (DIMS == 3 ? a.nzu : 1); zz += gridDim.z) {
       const int z = DIMS == 3 ? a.zlo + zz : 0;
@@ -77,7 +85,8 @@ __global__ void __launch_bounds__(256) observables_kernel(const ObsArgs<P> a) {
         cn += n2;
         long long H[3];
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax) H[ax] = 2 * (ax == 2 ? zg : j[ax]) + plane_off<DIMS>(plane, ax);
+        for (int ax = 0; ax < 3; ++ax)
+          H[ax] = 2 * (ax == 2 ? zg : (ax == 1 ? yg : j[ax])) + plane_off<DIMS>(plane, ax);
         const long long hd = a.dens_axis == 0 ? H[0] : (a.dens_axis == 1 ? H[1] : H[2]);
         if (a.dens_axis >= 0 && hd >= a.dens_X) cd += n2;
         if (is_upper<DIMS>(plane)) continue;

@@ -469,8 +469,9 @@ __global__ void __launch_bounds__(kThreads3d, kBlocks3d) fused3d_batch_kernel(co
   }
 }
 
-__host__ __device__ __forceinline__ long long items2d(const int (&N)[3], int chunk) {
-  return (long long)((N[0] + kCore - 1) / kCore) * ((N[1] + chunk - 1) / chunk);
+// work items of a (2+1)D one-step launch: strips x chunks of the `rows` updated rows
+__host__ __device__ __forceinline__ long long items2d(const int (&N)[3], int rows, int chunk) {
+  return (long long)((N[0] + kCore - 1) / kCore) * ((rows + chunk - 1) / chunk);
 }
 
 // One row of the (2+1)D pipeline at march position k.  In: the old u0, v0, v1
@@ -526,8 +527,14 @@ __device__ __forceinline__ void fused2d_item(const FusedArgs<P>& a, long long it
   const bool iso = a.iso != 0;
   const long long chunk = item / strips;
   const int strip = (int)(item - chunk * strips);
-  const int y0 = (int)chunk * a.chunk;
-  const int y1 = min(Ny, y0 + a.chunk);
+  // the updated rows zlo .. zlo + nzu - 1 (all rows of a whole grid, a slab's
+  // own rows); fields at the global row (zorg + k, wrapped: in [-1, 2 Nzg))
+  const int y0 = a.zlo + (int)chunk * a.chunk;
+  const int y1 = min(a.zlo + a.nzu, y0 + a.chunk);
+  auto gy = [&](int k) {
+    const int g = a.zorg + k;
+    return g < 0 ? g + a.Nzg : (g >= a.Nzg ? g - a.Nzg : g);
+  };
   const int gx = strip * kCore + lane - 1;
   const int x = wrapi(gx, Nx);
   const bool core = lane >= 1 && lane <= kCore && gx < Nx;
@@ -554,8 +561,8 @@ __device__ __forceinline__ void fused2d_item(const FusedArgs<P>& a, long long it
     C pU0 = U0, pV0 = V0n, pV1 = V1n, pU1 = U1;  // next row, loaded while this one computes
     if (k + 1 < y1) load(k + 1, pU0, pV0, pV1, pU1);
     C nU0n, nU1k, nV1, nV0, S1, S0;
-    row2d<P, COEF, LINK>(a, iso, hx, yk, yn, ok, on, U0, V0n, V1n, U1, oV0, oV1, nU0, nU1, nU0n, nU1k,
-                         nV1, nV0, &S1, &S0);
+    row2d<P, COEF, LINK>(a, iso, hx, gy(k), gy(k + 1), ok, on, U0, V0n, V1n, U1, oV0, oV1, nU0, nU1, nU0n,
+                         nU1k, nV1, nV0, &S1, &S0);
     if (core) {
       if (k >= y0) {
         a.out[1][ok] = nU1k;
@@ -673,7 +680,7 @@ template <class P, int COEF, int LINK>
 __global__ void __launch_bounds__(32 * kFused2dWarps) fused2d_kernel(const FusedArgs<P> a) {
   const int lane = threadIdx.x & 31;
   const long long worker = (long long)blockIdx.x * kFused2dWarps + (threadIdx.x >> 5);
-  const long long items = items2d(a.N, a.chunk);
+  const long long items = items2d(a.N, a.nzu, a.chunk);
   double e_n = 0.0, e_c = 0.0;
   for (long long item = worker; item < items; item += a.workers)  // uniform per warp
     fused2d_item<P, COEF, LINK>(a, item, lane, e_n, e_c);
@@ -828,8 +835,11 @@ template <int COEF, int LINK>
 int launch2d(FusedArgs<F32> a, cudaStream_t s) {
   auto k = fused2d_kernel<F32, COEF, LINK>;
   const int warps = workers2d<fused2d_kernel<F32, COEF, LINK>>();
-  if (a.chunk <= 0 || a.chunk > a.N[1]) a.chunk = fused_chunk(2, a.N);
-  const long long items = items2d(a.N, a.chunk);
+  if (a.chunk <= 0 || a.chunk > a.nzu) {
+    const int Np[3] = {a.N[0], a.nzu, 1};
+    a.chunk = fused_chunk(2, Np);
+  }
+  const long long items = items2d(a.N, a.nzu, a.chunk);
   long long w = items < warps ? items : warps;
   // one E partial per block: never more blocks than the partials hold
   if (a.e_partials && w > (long long)kFusedEMaxBlocks * kFused2dWarps) w = (long long)kFusedEMaxBlocks * kFused2dWarps;
@@ -999,7 +1009,7 @@ int fused_candidates(int dims, const int N[3], int two_step, int* out, int max) 
 
 long long fused_items(int dims, const int N[3], int chunk) {
   const int n[3] = {N[0], N[1], N[2]};
-  return dims == 3 ? items3d(n, n[2], chunk) : items2d(n, chunk);
+  return dims == 3 ? items3d(n, n[2], chunk) : items2d(n, n[1], chunk);
 }
 
 template <>

@@ -1,10 +1,11 @@
 """Halo exchange of the sub-domain decomposition (Sect. 6) between
 processes.
 
-The grid is split along z into slabs (dirac_slab_partition: slab k has nz_k
-consecutive levels from z0_k); a slab is stored as [planes][nz + 2][Ny][Nx]
-with one halo level below its own levels (index 0) and one above (index
-nz + 1).  After every time step each slab's last own level becomes its upper
+The grid is split along its marching axis (z in (3+1)D, y in (2+1)D) into
+slabs (dirac_slab_partition: slab k has n_k consecutive levels from z0_k); a
+slab is stored as [planes][n + 2][...] (the rest of a level: [Ny][Nx] or
+[Nx]) with one halo level below its own levels (index 0) and one above
+(index n + 1).  After every time step each slab's last own level becomes its upper
 neighbour's lower halo and its first own level its lower neighbour's upper
 halo, periodically (the last slab's upper neighbour is the first).  Within
 one device the library does this with device copies (dirac_slabs_step);
