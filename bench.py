@@ -335,8 +335,13 @@ def run_serve(args, rank, world):
         rule = ("0.8 x the sustainable rate of a sweep over prefixes of the stream "
                 f"({m} requests each; burst capacity {cap:.3f}/s)")
     reqs = serve.make_requests(args.requests, seed=args.seed, rate=rate)
+    log = None
+    if args.progress:
+        def log(msg):
+            print(msg, file=sys.stderr, flush=True)
+        log(f"rate {rate:.4f}/s ({rule}); sweep {sweep}")
     with Clocks(local) as clk:
-        out = srv.run(reqs)
+        out = srv.run(reqs, log=log)
     # the plain FP64 path (one simulation per launch sequence) on a subsample
     sub = []
     for r in reqs[:8]:
@@ -397,6 +402,7 @@ def main():
     ap.add_argument("--quantum", type=int, default=100, help="serve: steps per batching quantum")
     ap.add_argument("--seed", type=int, default=0, help="serve: request stream seed")
     ap.add_argument("--sweep-requests", type=int, default=40, help="serve: requests per rate-sweep point")
+    ap.add_argument("--progress", action="store_true", help="serve: log every retired request to stderr")
     ap.add_argument("--rate", type=float, default=0.0,
                     help="serve: arrival rate in requests/s (0: 0.8 x the sustainable rate, measured first)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
