@@ -53,6 +53,10 @@
  *   DIRAC_NO_GRAPHS             step loops as plain launches, no CUDA graphs
  *   DIRAC_NO_FUSED_NORM         dirac_norm always reduces the stored state
  *   DIRAC_NO_TEMPORAL_BLOCKING  (2+1)D FP32: one time step per pass
+ *   DIRAC_HOST_COPY=staged      dirac_set_spinor / dirac_get_spinor of FP32
+ *                               simulations copy page-locked buffers through a
+ *                               device staging plane instead of converting them
+ *                               in place
  *   DIRAC_SOFTCORE              (read by dirac_create) how the FP32 kernels
  *                               evaluate a soft-core potential's Cayley
  *                               coefficients: "analytic" (default; compensated
@@ -176,13 +180,18 @@ dirac_status dirac_create(dirac_sim** out, int dims, const int N[3], const doubl
    simulation (converted to the simulation's precision on the device).  The
    copies are enqueued on the simulation's stream: a pageable host buffer may
    be reused as soon as the call returns, a page-locked one only once the
-   stream has passed this point (any synchronising call).  The functional of
+   stream has passed this point (any synchronising call).  FP32: a
+   page-locked, device-mapped buffer (cudaHostAlloc / pinned memory; every
+   byte of the state's range page-locked, 16-byte aligned) is read in place
+   by the conversion kernels, without a copy-engine pass; anything else goes
+   through a device staging plane, one plane at a time.  The functional of
    the new state is reduced on the device as the reference of dirac_check
    (two more launches, no synchronisation). */
 dirac_status dirac_set_spinor(dirac_sim* sim, const double* host);
 
 /* Copy the current state out in the canonical host layout (complex128);
-   synchronises the stream. */
+   synchronises the stream.  FP32: a page-locked, device-mapped buffer (as for
+   dirac_set_spinor) is written in place by the conversion kernels. */
 dirac_status dirac_get_spinor(dirac_sim* sim, double* host);
 
 /* As dirac_set_spinor / dirac_get_spinor, but the canonical complex128

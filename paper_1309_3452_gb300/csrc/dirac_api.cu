@@ -1,6 +1,8 @@
 // Host side of libdirac: the C ABI declared in include/dirac.h.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -723,19 +725,54 @@ extern "C" void dirac_destroy(dirac_sim* s) {
 
 static dirac_status take_reference(dirac_sim* s);
 
+// The device address of a page-locked, mapped host buffer of `bytes` bytes
+// starting at p, or nullptr when the conversion kernels cannot access it in
+// place: pageable memory, a range whose last byte is not page-locked too, an
+// address not 16-byte aligned (the kernels move double2), or
+// DIRAC_HOST_COPY=staged.
+static const void* mapped_host(const void* p, size_t bytes) {
+  if (bytes == 0 || (reinterpret_cast<uintptr_t>(p) & 15) != 0) return nullptr;
+  if (const char* e = std::getenv("DIRAC_HOST_COPY"); e && std::strcmp(e, "staged") == 0) return nullptr;
+  cudaPointerAttributes a0, a1;
+  if (cudaPointerGetAttributes(&a0, p) != cudaSuccess) {
+    cudaGetLastError();  // not a CUDA pointer: not an error of this simulation
+    return nullptr;
+  }
+  if (a0.type != cudaMemoryTypeHost || a0.devicePointer == nullptr) return nullptr;
+  const char* last = static_cast<const char*>(p) + (bytes - 1);
+  if (cudaPointerGetAttributes(&a1, last) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a1.type != cudaMemoryTypeHost || a1.devicePointer == nullptr ||
+      static_cast<const char*>(a1.devicePointer) - static_cast<const char*>(a0.devicePointer) !=
+          static_cast<ptrdiff_t>(bytes - 1))
+    return nullptr;
+  return a0.devicePointer;
+}
+
 extern "C" dirac_status dirac_set_spinor(dirac_sim* s, const double* host) {
   if (!s || !host) return fail(s, DIRAC_ERR_INVALID, "NULL argument");
   s->e_valid_at = -1;
+  const size_t bytes = (size_t)s->ncell * sizeof(double2);
+  // FP32 from a page-locked buffer: the conversion kernels read the host
+  // memory in place (no copy-engine pass through the staging plane)
+  const double2* mapped = s->prec == DIRAC_FP32
+                              ? static_cast<const double2*>(mapped_host(host, bytes * (size_t)s->np))
+                              : nullptr;
   for (int k = 0; k < s->np; ++k) {
     const double* src = host + 2LL * k * s->ncell;
-    size_t bytes = (size_t)s->ncell * sizeof(double2);
     if (s->prec == DIRAC_FP64) {
       double2* dst = static_cast<double2*>(s->state) + (long long)k * s->pstride;
       CK(s, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream));
     } else {
       float2* dst = static_cast<float2*>(s->state) + (long long)k * s->pstride;
-      CK(s, cudaMemcpyAsync(s->staging, src, bytes, cudaMemcpyHostToDevice, s->stream));
-      launch_convert_in(s->staging, dst, s->ncell, s->stream);
+      if (mapped) {
+        launch_convert_in(mapped + (long long)k * s->ncell, dst, s->ncell, s->stream);
+      } else {
+        CK(s, cudaMemcpyAsync(s->staging, src, bytes, cudaMemcpyHostToDevice, s->stream));
+        launch_convert_in(s->staging, dst, s->ncell, s->stream);
+      }
       s->launches += 1;
       CK(s, cudaGetLastError());
     }
@@ -745,18 +782,25 @@ extern "C" dirac_status dirac_set_spinor(dirac_sim* s, const double* host) {
 
 extern "C" dirac_status dirac_get_spinor(dirac_sim* s, double* host) {
   if (!s || !host) return fail(s, DIRAC_ERR_INVALID, "NULL argument");
+  const size_t bytes = (size_t)s->ncell * sizeof(double2);
+  double2* mapped = s->prec == DIRAC_FP32
+                        ? static_cast<double2*>(const_cast<void*>(mapped_host(host, bytes * (size_t)s->np)))
+                        : nullptr;
   for (int k = 0; k < s->np; ++k) {
     double* dst = host + 2LL * k * s->ncell;
-    size_t bytes = (size_t)s->ncell * sizeof(double2);
     if (s->prec == DIRAC_FP64) {
       const double2* src = static_cast<double2*>(s->state) + (long long)k * s->pstride;
       CK(s, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s->stream));
     } else {
       const float2* src = static_cast<float2*>(s->state) + (long long)k * s->pstride;
-      launch_convert_out(src, s->staging, s->ncell, s->stream);
+      if (mapped) {
+        launch_convert_out(src, mapped + (long long)k * s->ncell, s->ncell, s->stream);
+      } else {
+        launch_convert_out(src, s->staging, s->ncell, s->stream);
+      }
       s->launches += 1;
       CK(s, cudaGetLastError());
-      CK(s, cudaMemcpyAsync(dst, s->staging, bytes, cudaMemcpyDeviceToHost, s->stream));
+      if (!mapped) CK(s, cudaMemcpyAsync(dst, s->staging, bytes, cudaMemcpyDeviceToHost, s->stream));
     }
   }
   CK(s, cudaStreamSynchronize(s->stream));
