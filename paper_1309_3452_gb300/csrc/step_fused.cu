@@ -39,11 +39,28 @@ namespace dirac {
 
 namespace {
 
-// (3+1)D tile height in threads (build-time choice): 15 rows with 512 threads
-// and two blocks per SM, or 30 rows with 1024 threads and one block per SM
+// (3+1)D tile geometry (build-time choice).  DIRAC_YPAIR=1 (default): every
+// thread updates two cells stacked in y, a 34 x 28 tile in 480 threads, one
+// block per SM.  DIRAC_YPAIR=0: one cell per thread, a 34 x DIRAC_TILE_ROWS
+// tile (15 rows: 512 threads, two blocks per SM; 30 rows: 1024 threads, one).
+#ifndef DIRAC_YPAIR
+#define DIRAC_YPAIR 1
+#endif
 #ifndef DIRAC_TILE_ROWS
 #define DIRAC_TILE_ROWS 15
 #endif
+#ifndef DIRAC_PAIRS
+#define DIRAC_PAIRS 14
+#endif
+#if DIRAC_YPAIR
+constexpr int kPairs = DIRAC_PAIRS;     // row pairs per tile
+constexpr int TW = 34, TH = 2 * kPairs;  // (3+1)D tile in cells
+constexpr int CX = TW - 2, CY = TH - 2;  // interior
+constexpr int kThreads3d = 32 * kPairs + 32;  // interior warps + one warp of halo columns and spares
+constexpr int kBlocks3d = kPairs <= 7 ? 2 : 1;  // resident blocks per SM the registers are planned for
+constexpr int kSmemRows = TH + 2;       // TH rows + the spare threads' pair of rows
+static_assert(2 * kPairs <= 32 && 2 * kPairs + 4 <= 32, "halo columns and spares fill one warp");
+#else
 constexpr int TW = 34, TH = DIRAC_TILE_ROWS;  // (3+1)D tile in threads
 constexpr int CX = TW - 2, CY = TH - 2; // interior
 constexpr int kThreads3d = TH == 15 ? 512 : 1024;
@@ -51,6 +68,7 @@ constexpr int kBlocks3d = TH == 15 ? 2 : 1;  // resident blocks per SM the regis
 constexpr int kSmemRows = TH + 1;       // TH rows + the spare threads' row
 static_assert(32 * CY + 2 * TW + 2 * CY <= kThreads3d && kThreads3d - 32 * CY - 2 * TW - 2 * CY < TW,
               "interior rows as warps, the halo ring and fewer than a row of spare threads");
+#endif
 
 template <class T>
 __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
@@ -77,6 +95,48 @@ struct LevelLoad {
   C A0, A1, B0, B1, C0, C1, D0, D1;
 };
 
+#if DIRAC_YPAIR
+// Thread geometry inside the (3+1)D tile (two cells per thread, rows ly and
+// ly + 1).  Warps 0..13 hold the columns 1..32 (lane -> x) of the row pairs
+// (0,1), (2,3), .., (26,27); rows 0 and 27 are halo rows, so warp 0's lower
+// cell and warp 13's upper cell are halo cells.  Warp 14 holds the halo
+// columns 0 and 33 of every row pair (28 threads) and four spare threads
+// (rows 28, 29 of shared memory, never stored).  Halo cells take part in the
+// upper half-step only, whose values the interior needs.
+struct Thread3d {
+  int slot;                // the lower cell's shared-memory slot, ly * TW + lx (upper: slot + TW)
+  int lx, ly;              // position of the lower cell in the 34 x 28 tile
+  int sym, syp;            // slots of the lower cell's y- and the upper cell's y+ neighbour
+                           // (clamped at the tile edge: halo cells then read their own slot)
+  int sxm, sxp;            // x- / x+ neighbour of the lower cell (clamped likewise; + TW: the upper cell's)
+  bool halo;               // warp-uniform: halo columns and spares (upper half-step only)
+  bool h0, h1;             // warp-uniform: the lower / upper cell is a halo cell
+};
+
+__device__ __forceinline__ Thread3d thread3d() {
+  Thread3d th;
+  const int t = threadIdx.x, w = t >> 5;
+  if (w < kPairs) {
+    th.lx = (t & 31) + 1;
+    th.ly = 2 * w;
+    th.halo = false;
+  } else {
+    const int h = t - 32 * kPairs;
+    th.halo = true;
+    if (h < kPairs) { th.lx = 0; th.ly = 2 * h; }
+    else if (h < 2 * kPairs) { th.lx = TW - 1; th.ly = 2 * (h - kPairs); }
+    else { th.lx = h - 2 * kPairs; th.ly = TH; }  // spare: rows of their own
+  }
+  th.h0 = th.halo || th.ly == 0;
+  th.h1 = th.halo || th.ly + 1 == TH - 1;
+  th.slot = th.ly * TW + th.lx;
+  th.sxm = th.lx > 0 ? th.slot - 1 : th.slot;
+  th.sxp = th.lx < TW - 1 ? th.slot + 1 : th.slot;
+  th.sym = th.ly > 0 ? th.slot - TW : th.slot;
+  th.syp = th.ly + 2 < kSmemRows ? th.slot + 2 * TW : th.slot + TW;
+  return th;
+}
+#else
 // Thread geometry inside the (3+1)D tile.  Warps 0..12 hold the 13 interior
 // rows, one aligned row of 32 cells each (lane -> x).  Warps 13..15 hold the
 // 94 halo cells (rows 0 and 14, columns 0 and 33) and two spare threads; they
@@ -113,11 +173,385 @@ __device__ __forceinline__ Thread3d thread3d() {
   return th;
 }
 
+#endif
+
 // work items of a (3+1)D launch: tiles x chunks of the `levels` updated levels
 __host__ __device__ __forceinline__ long long items3d(const int (&N)[3], int levels, int chunk) {
   return (long long)((N[0] + CX - 1) / CX) * ((N[1] + CY - 1) / CY) * ((levels + chunk - 1) / chunk);
 }
 
+#if DIRAC_YPAIR
+// One work item (one tile over one chunk of z levels) of one simulation, two
+// cells per thread stacked in y: cell 0 at row ly, cell 1 at row ly + 1.  The
+// y neighbour of a cell inside the pair comes from the other cell's registers;
+// the pair's outer y neighbours and all x neighbours come from shared memory.
+// `a` may live in the constant bank (kernel parameter) or in shared memory.
+template <class P, int COEF, int LINK>
+__device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long item, const Thread3d& th,
+                                             unsigned char* smem_raw, double* e_acc) {
+  using C = typename P::cplx;
+  // every tile is double-buffered by level parity: slot [k & 1] holds level k
+  C (*sC)[2][kSlots] = reinterpret_cast<C (*)[2][kSlots]>(smem_raw);  // old C(k)
+  C (*sD)[2][kSlots] = sC + 2;                                         // old D(k)
+  C (*sB)[2][kSlots] = sC + 4;                                         // new B(k)
+  C (*sA)[2][kSlots] = sC + 6;                                         // new A(k)
+  const int s0 = th.slot, s1 = th.slot + TW;  // the pair's slots
+  const int lx = th.lx, ly = th.ly;
+  const int xm0 = th.sxm, xp0 = th.sxp, xm1 = th.sxm + TW, xp1 = th.sxp + TW;
+  const int sym = th.sym, syp = th.syp;
+  const int Nx = a.N[0], Ny = a.N[1], Nz = a.N[2];
+  // global level of the stored level k (wrapped on the global grid), for the
+  // fields; zorg + k lies in [-1, 2 Nzg) (zorg in [-1, Nzg), k <= N[2] <= Nzg + 1)
+  auto gz = [&](int k) {
+    const int g = a.zorg + k;
+    return g < 0 ? g + a.Nzg : (g >= a.Nzg ? g - a.Nzg : g);
+  };
+  const int tiles_x = (Nx + CX - 1) / CX;
+  const long long tiles = (long long)tiles_x * ((Ny + CY - 1) / CY);
+  const bool iso = a.iso != 0;
+  const long long nxy = (long long)Nx * Ny;
+  const bool want_e = a.e_partials != nullptr;
+  {
+    const long long chunk = item / tiles, tile = item - chunk * tiles;
+    const int z0 = a.zlo + (int)chunk * a.chunk;
+    const int z1 = min(a.zlo + a.nzu, z0 + a.chunk);
+    const int gx = (int)(tile % tiles_x) * CX + lx - 1;
+    const int gy0 = (int)(tile / tiles_x) * CY + ly - 1, gy1 = gy0 + 1;
+    const int x = wrapi(gx, Nx), y0 = wrapi(gy0, Ny), y1 = wrapi(gy1, Ny);
+    const bool xin = lx >= 1 && lx <= CX && gx < Nx;
+    const bool core0 = xin && !th.h0 && gy0 < Ny;
+    const bool core1 = xin && !th.h1 && gy1 < Ny;
+    const long long cxy0 = (long long)y0 * Nx + x, cxy1 = (long long)y1 * Nx + x;
+    const int hx = 2 * x, hy0 = 2 * y0, hy1 = 2 * y1;
+    // COEF_SOFTCORE: the x-y part of R = |x - c|^2 + a^2 of each cell of the
+    // pair, as (hi, lo) pairs of two values: lanes (A0/C0, A1/C1) at (hx, hy),
+    // (hx+1, hy+1) and (B0/D0, B1/D1) at (hx+1, hy), (hx, hy+1), kept in
+    // shared memory (one record per thread and cell) so that they take no
+    // registers through the z-march
+    constexpr bool kSoft = COEF == COEF_SOFTCORE || COEF == COEF_SOFTCORR;
+    __shared__ __align__(16) float4 sRxy[kSoft ? kThreads3d : 1][2][2];
+    if constexpr (kSoft) {
+      const float2 x0 = __ldg(a.hu.sc_sq[0] + hx), x1 = __ldg(a.hu.sc_sq[0] + hx + 1);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int hy = c ? hy1 : hy0;
+        const float2 ya = __ldg(a.hu.sc_sq[1] + hy), yb = __ldg(a.hu.sc_sq[1] + hy + 1);
+        const float2 d00 = padd(x0, ya), d11 = padd(x1, yb), a10 = padd(x1, ya), a01 = padd(x0, yb);
+        sRxy[threadIdx.x][c][0] = make_float4(d00.x, d11.x, d00.y, d11.y);
+        sRxy[threadIdx.x][c][1] = make_float4(a10.x, a01.x, a10.y, a01.y);
+      }
+    }
+    // Per-level field constants, the same for the whole block, staged in
+    // shared memory by threads 0..6 with copies that bypass the registers,
+    // double-buffered by level parity (level k's copies are issued after the
+    // first barrier of level k-1, when no thread reads that parity any more,
+    // and waited for before the first barrier of level k):
+    //   sLk[p][0..3]: plane-wave link factors along z (LINK_PLANE, table axis z)
+    //                 of A (upper half, Z = 2zn), B (upper, 2zk+1), C (lower,
+    //                 2zk+1), D (lower, 2zk)
+    //   sZq[p][0..2]: soft-core z terms sc_sq[2][Z] of Z = 2zn, 2zk+1, 2zk
+    using PL = typename PlaneLinkOf<P>::type;
+    __shared__ __align__(16) PL sLk[2][4];
+    __shared__ __align__(16) float2 sZq[2][3];
+    // (the (3+1)D launchers run a plane wave along z polarised along x as
+    // LINK_PLANE_ZX and send other plane waves to the general path)
+    constexpr bool lk_z = LINK == LINK_PLANE_ZX;
+    auto stage_level = [&](int k) {
+      const int tid = threadIdx.x;
+      if (tid >= 7) return;
+      const int p = k & 1;
+      const int zk = gz(k), zn = gz(k + 1);  // global levels: the tables are indexed by global Z
+      if constexpr (LINK == LINK_PLANE_ZX) {
+        if (tid < 4) {
+          const int Z = tid == 0 ? 2 * zn : (tid == 3 ? 2 * zk : 2 * zk + 1);
+          const PL* tab = static_cast<const PL*>(tid < 2 ? a.hu.ltab : a.hl.ltab);
+          static_assert(sizeof(PL) % 16 == 0, "16-byte copies");
+          for (int q = 0; q < (int)(sizeof(PL) / 16); ++q)
+            cp_async16(reinterpret_cast<char*>(&sLk[p][tid]) + 16 * q,
+                       reinterpret_cast<const char*>(tab + Z) + 16 * q);
+        }
+      }
+      if constexpr (kSoft) {
+        if (tid >= 4) {
+          const int Z = tid == 4 ? 2 * zn : (tid == 5 ? 2 * zk + 1 : 2 * zk);
+          cp_async8(&sZq[p][tid - 4], a.hu.sc_sq[2] + Z);
+        }
+      }
+      cp_async_commit();
+    };
+    // the coefficients of a pair of values of cell c with the x-y parts
+    // (Rh, Rl), the z term z and positions H0, H1 (softcore_R's sums, same order)
+    auto pair_b = [&](const HalfFields<P>& h, int c, int which, float2 z, const int (&H0)[3],
+                      const int (&H1)[3], float4 (&b)[2]) {
+      if constexpr (COEF == COEF_SOFTCORE) {
+        const float4 r = sRxy[threadIdx.x][c][which];  // which: 0 = (A, C) pairs, 1 = (B, D) pairs
+        const float2 Rh = make_float2(r.x, r.y), Rl = make_float2(r.z, r.w);
+        const float2 t0 = softcore_t0(h, H0), t1 = softcore_t0(h, H1);
+        const SoftB2 bb = softcore_b2(padd(Rh, f2(z.x)), padd(Rl, f2(z.y)), make_float2(t0.x, t1.x),
+                                      make_float2(t0.y, t1.y), h.sc_K_hi, h.sc_K_lo);
+        b[0] = lane_b(bb, 0);
+        b[1] = lane_b(bb, 1);
+      }
+    };
+    // COEF_SOFTCORR: the FP32 estimates of a pair plus the two values' words w0, w1
+    // of the correction record (R summed in softcore_R's order)
+    auto pair_bc = [&](const HalfFields<P>& h, int c, int which, float2 z, const int (&H0)[3],
+                       const int (&H1)[3], long long rec, int slot, float4 (&b)[2]) {
+      if constexpr (COEF == COEF_SOFTCORR) {
+        // the pair's two words of the level's correction record (read where used)
+        const uint2 w = __ldg(reinterpret_cast<const uint2*>(a.hu.sc_corr + 8 * rec + slot));
+        const float4 r = sRxy[threadIdx.x][c][which];
+        const float2 Rh = padd(make_float2(r.x, r.y), f2(z.x)), Rl = padd(make_float2(r.z, r.w), f2(z.y));
+        float2 re, im;
+        softcore_fast2(Rh, Rl, make_float2(softcore_t0(h, H0).x, softcore_t0(h, H1).x), h.sc_K_hi, re, im);
+        const float2 c0 = corr_decode(w.x), c1 = corr_decode(w.y);
+        b[0] = make_float4(re.x, c0.x, im.x, c0.y);
+        b[1] = make_float4(re.y, c1.x, im.y, c1.y);
+      }
+    };
+    constexpr bool kPre = kSoft;  // coefficients computed in pairs
+
+    auto load = [&](int k, LevelLoad<C>& l0, LevelLoad<C>& l1) {
+      const int zk = k < 0 ? k + Nz : k;
+      const int zn = k + 1 >= Nz ? k + 1 - Nz : k + 1;
+      const long long ok0 = zk * nxy + cxy0, on0 = zn * nxy + cxy0;
+      const long long ok1 = zk * nxy + cxy1, on1 = zn * nxy + cxy1;
+      l0.A0 = ld(a.in[0] + on0);
+      l1.A0 = ld(a.in[0] + on1);
+      l0.A1 = ld(a.in[1] + on0);
+      l1.A1 = ld(a.in[1] + on1);
+      l0.B0 = ld(a.in[2] + ok0);
+      l1.B0 = ld(a.in[2] + ok1);
+      l0.B1 = ld(a.in[3] + ok0);
+      l1.B1 = ld(a.in[3] + ok1);
+      l0.C0 = ld(a.in[4] + on0);
+      l1.C0 = ld(a.in[4] + on1);
+      l0.C1 = ld(a.in[5] + on0);
+      l1.C1 = ld(a.in[5] + on1);
+      l0.D0 = ld(a.in[6] + on0);
+      l1.D0 = ld(a.in[6] + on1);
+      l0.D1 = ld(a.in[7] + on0);
+      l1.D1 = ld(a.in[7] + on1);
+    };
+
+    {  // old C, D of level z0-1 (the z- neighbours of the first level)
+      const int p = (z0 - 1) & 1;
+      const long long zo = (long long)wrapi(z0 - 1, Nz) * nxy;
+      const long long o0 = zo + cxy0, o1 = zo + cxy1;
+      sC[p][0][s0] = ld(a.in[4] + o0);
+      sC[p][1][s0] = ld(a.in[5] + o0);
+      sD[p][0][s0] = ld(a.in[6] + o0);
+      sD[p][1][s0] = ld(a.in[7] + o0);
+      sC[p][0][s1] = ld(a.in[4] + o1);
+      sC[p][1][s1] = ld(a.in[5] + o1);
+      sD[p][0][s1] = ld(a.in[6] + o1);
+      sD[p][1][s1] = ld(a.in[7] + o1);
+    }
+    LevelLoad<C> c0, c1;  // the level loads of the two cells
+    load(z0 - 1, c0, c1);
+    constexpr bool kStage = LINK == LINK_PLANE_ZX || kSoft;
+    if (kStage) stage_level(z0 - 1);
+
+    for (int k = z0 - 1; k < z1; ++k) {
+      const int zk = k < 0 ? k + Nz : k;
+      const int zn = k + 1 >= Nz ? k + 1 - Nz : k + 1;
+      const long long ok0 = zk * nxy + cxy0, on0 = zn * nxy + cxy0;
+      const long long ok1 = zk * nxy + cxy1, on1 = zn * nxy + cxy1;
+      const int pk = k & 1, pn = (k + 1) & 1, pm = (k - 1) & 1;
+      const int Zk = 2 * gz(k), Zn = 2 * gz(k + 1);  // half-lattice z of levels k, k+1 (global)
+      sC[pn][0][s0] = c0.C0;  // old C(k+1), D(k+1): z+ / x,y neighbours now,
+      sC[pn][1][s0] = c0.C1;  // own old values at the next level
+      sD[pn][0][s0] = c0.D0;
+      sD[pn][1][s0] = c0.D1;
+      sC[pn][0][s1] = c1.C0;
+      sC[pn][1][s1] = c1.C1;
+      sD[pn][0][s1] = c1.D0;
+      sD[pn][1][s1] = c1.D1;
+      // prefetch the next level while this one computes
+      LevelLoad<C> n0 = c0, n1 = c1;
+      if (k + 1 < z1) load(k + 1, n0, n1);
+      if (kStage && threadIdx.x < 7) cp_async_wait_all();  // this level's staged constants
+      __syncthreads();
+      if (kStage && k + 1 < z1) stage_level(k + 1);
+      const PL* lkA = lk_z ? &sLk[pk][0] : nullptr;  // compile-time choice: a shared-memory address
+      const PL* lkB = lk_z ? &sLk[pk][1] : nullptr;
+
+      // upper half-step: A(k+1) from C(k+1), C(k), D(k+1); B(k) from D(k+1), D(k), C(k)
+      const C oC00 = sC[pk][0][s0], oC10 = sC[pk][1][s0];  // old C(k) of cell 0
+      const C oC01 = sC[pk][0][s1], oC11 = sC[pk][1][s1];  // and of cell 1
+      C nA0n0, nA1n0, nB0k0, nB1k0, nA0n1, nA1n1, nB0k1, nB1k1;
+      float4 bv[2];
+      {  // cell 0
+        const int H0[3] = {hx, hy0, Zn}, H1[3] = {hx + 1, hy0 + 1, Zn};
+        if constexpr (COEF == COEF_SOFTCORE) pair_b(a.hu, 0, 0, sZq[pk][0], H0, H1, bv);
+        if constexpr (COEF == COEF_SOFTCORR) pair_bc(a.hu, 0, 0, sZq[pk][0], H0, H1, ok0, 0, bv);
+        C nb0[6] = {c0.D0, sD[pn][0][xm0], c0.D1, sD[pn][1][sym], c0.C0, oC00};
+        nA0n0 = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 0, c0.A0, nb0, H0, on0, a.pstride,
+                                              nullptr, kPre ? &bv[0] : nullptr, lkA);
+        C nb1[6] = {sD[pn][1][xp0], c0.D1, c1.D0, c0.D0, c0.C1, oC10};
+        nA1n0 = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 1, c0.A1, nb1, H1, on0, a.pstride,
+                                              nullptr, kPre ? &bv[1] : nullptr, lkA);
+      }
+      {  // cell 1
+        const int H0[3] = {hx, hy1, Zn}, H1[3] = {hx + 1, hy1 + 1, Zn};
+        if constexpr (COEF == COEF_SOFTCORE) pair_b(a.hu, 1, 0, sZq[pk][0], H0, H1, bv);
+        if constexpr (COEF == COEF_SOFTCORR) pair_bc(a.hu, 1, 0, sZq[pk][0], H0, H1, ok1, 0, bv);
+        C nb0[6] = {c1.D0, sD[pn][0][xm1], c1.D1, c0.D1, c1.C0, oC01};
+        nA0n1 = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 0, c1.A0, nb0, H0, on1, a.pstride,
+                                              nullptr, kPre ? &bv[0] : nullptr, lkA);
+        C nb1[6] = {sD[pn][1][xp1], c1.D1, sD[pn][0][syp], c1.D0, c1.C1, oC11};
+        nA1n1 = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 1, c1.A1, nb1, H1, on1, a.pstride,
+                                              nullptr, kPre ? &bv[1] : nullptr, lkA);
+      }
+      {  // cell 0
+        const int H0[3] = {hx + 1, hy0, Zk + 1}, H1[3] = {hx, hy0 + 1, Zk + 1};
+        if constexpr (COEF == COEF_SOFTCORE) pair_b(a.hu, 0, 1, sZq[pk][1], H0, H1, bv);
+        if constexpr (COEF == COEF_SOFTCORR) pair_bc(a.hu, 0, 1, sZq[pk][1], H0, H1, ok0, 2, bv);
+        C nb0[6] = {sC[pk][0][xp0], oC00, oC10, sC[pk][1][sym], c0.D0, sD[pk][0][s0]};
+        nB0k0 = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 2, c0.B0, nb0, H0, ok0, a.pstride,
+                                              nullptr, kPre ? &bv[0] : nullptr, lkB);
+        C nb1[6] = {oC10, sC[pk][1][xm0], oC01, oC00, c0.D1, sD[pk][1][s0]};
+        nB1k0 = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 3, c0.B1, nb1, H1, ok0, a.pstride,
+                                              nullptr, kPre ? &bv[1] : nullptr, lkB);
+      }
+      {  // cell 1
+        const int H0[3] = {hx + 1, hy1, Zk + 1}, H1[3] = {hx, hy1 + 1, Zk + 1};
+        if constexpr (COEF == COEF_SOFTCORE) pair_b(a.hu, 1, 1, sZq[pk][1], H0, H1, bv);
+        if constexpr (COEF == COEF_SOFTCORR) pair_bc(a.hu, 1, 1, sZq[pk][1], H0, H1, ok1, 2, bv);
+        C nb0[6] = {sC[pk][0][xp1], oC01, oC11, oC10, c1.D0, sD[pk][0][s1]};
+        nB0k1 = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 2, c1.B0, nb0, H0, ok1, a.pstride,
+                                              nullptr, kPre ? &bv[0] : nullptr, lkB);
+        C nb1[6] = {oC11, sC[pk][1][xm1], sC[pk][0][syp], oC01, c1.D1, sD[pk][1][s1]};
+        nB1k1 = site_update<P, 3, COEF, LINK>(a.hu, a.f, iso, a.ry, a.rz, 3, c1.B1, nb1, H1, ok1, a.pstride,
+                                              nullptr, kPre ? &bv[1] : nullptr, lkB);
+      }
+      sB[pk][0][s0] = nB0k0;
+      sB[pk][1][s0] = nB1k0;
+      sA[pn][0][s0] = nA0n0;
+      sA[pn][1][s0] = nA1n0;
+      sB[pk][0][s1] = nB0k1;
+      sB[pk][1][s1] = nB1k1;
+      sA[pn][0][s1] = nA0n1;
+      sA[pn][1][s1] = nA1n1;
+      __syncthreads();
+
+      // lower half-step: C(k) from A(k+1), A(k), B(k); D(k) from B(k), B(k-1), A(k)
+      // (interior cells only: nothing needs the halo's lower values; the
+      // first level of a run only rebuilds A(z0) and B(z0-1))
+      if (!th.halo) {
+        auto n2 = [](C v) { return fmaf(v.x, v.x, v.y * v.y); };
+        if (k >= z0) {
+          const C nA00 = sA[pk][0][s0], nA10 = sA[pk][1][s0];  // new A(k) of cell 0
+          const C nA01 = sA[pk][0][s1], nA11 = sA[pk][1][s1];  // and of cell 1
+          const PL* lkC = lk_z ? &sLk[pk][2] : nullptr;
+          const PL* lkD = lk_z ? &sLk[pk][3] : nullptr;
+          if (!th.h0) {  // cell 0 (warp-uniform)
+            C nC0, nC1, nD0, nD1, S;
+            const bool acc = want_e && core0;  // this cell's new values count towards E
+            float lc = 0.0f;
+            {
+              const int H0[3] = {hx, hy0, Zk + 1}, H1[3] = {hx + 1, hy0 + 1, Zk + 1};
+              if constexpr (COEF == COEF_SOFTCORE) pair_b(a.hl, 0, 0, sZq[pk][1], H0, H1, bv);
+              if constexpr (COEF == COEF_SOFTCORR) pair_bc(a.hl, 0, 0, sZq[pk][1], H0, H1, ok0, 4, bv);
+              C nb0[6] = {nB0k0, sB[pk][0][xm0], nB1k0, sB[pk][1][sym], nA0n0, nA00};
+              nC0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 4, oC00, nb0, H0, ok0, a.pstride,
+                                                  &S, kPre ? &bv[0] : nullptr, lkC);
+              if (acc) lc = fmaf(nC0.x, S.x, fmaf(nC0.y, S.y, lc));
+              C nb1[6] = {sB[pk][1][xp0], nB1k0, nB0k1, nB0k0, nA1n0, nA10};
+              nC1 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 5, oC10, nb1, H1, ok0, a.pstride,
+                                                  &S, kPre ? &bv[1] : nullptr, lkC);
+              if (acc) lc = fmaf(nC1.x, S.x, fmaf(nC1.y, S.y, lc));
+            }
+            {
+              const int H0[3] = {hx + 1, hy0, Zk}, H1[3] = {hx, hy0 + 1, Zk};
+              if constexpr (COEF == COEF_SOFTCORE) pair_b(a.hl, 0, 1, sZq[pk][2], H0, H1, bv);
+              if constexpr (COEF == COEF_SOFTCORR) pair_bc(a.hl, 0, 1, sZq[pk][2], H0, H1, ok0, 6, bv);
+              C nb0[6] = {sA[pk][0][xp0], nA00, nA10, sA[pk][1][sym], nB0k0, sB[pm][0][s0]};
+              nD0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 6, sD[pk][0][s0], nb0, H0, ok0,
+                                                  a.pstride, &S, kPre ? &bv[0] : nullptr, lkD);
+              if (acc) lc = fmaf(nD0.x, S.x, fmaf(nD0.y, S.y, lc));
+              C nb1[6] = {nA10, sA[pk][1][xm0], nA01, nA00, nB1k0, sB[pm][1][s0]};
+              nD1 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 7, sD[pk][1][s0], nb1, H1, ok0,
+                                                  a.pstride, &S, kPre ? &bv[1] : nullptr, lkD);
+              if (acc) lc = fmaf(nD1.x, S.x, fmaf(nD1.y, S.y, lc));
+            }
+            if (acc) {  // this level's few terms in FP32, the running sums in FP64 (shared memory)
+              e_acc[1] += lc;
+              e_acc[0] += ((n2(nB0k0) + n2(nB1k0)) + (n2(nC0) + n2(nC1))) + (n2(nD0) + n2(nD1));
+            }
+            if (core0) {
+              a.out[2][ok0] = nB0k0;
+              a.out[3][ok0] = nB1k0;
+              a.out[4][ok0] = nC0;
+              a.out[5][ok0] = nC1;
+              a.out[6][ok0] = nD0;
+              a.out[7][ok0] = nD1;
+            }
+          }
+          if (!th.h1) {  // cell 1 (warp-uniform)
+            C nC0, nC1, nD0, nD1, S;
+            const bool acc = want_e && core1;
+            float lc = 0.0f;
+            {
+              const int H0[3] = {hx, hy1, Zk + 1}, H1[3] = {hx + 1, hy1 + 1, Zk + 1};
+              if constexpr (COEF == COEF_SOFTCORE) pair_b(a.hl, 1, 0, sZq[pk][1], H0, H1, bv);
+              if constexpr (COEF == COEF_SOFTCORR) pair_bc(a.hl, 1, 0, sZq[pk][1], H0, H1, ok1, 4, bv);
+              C nb0[6] = {nB0k1, sB[pk][0][xm1], nB1k1, nB1k0, nA0n1, nA01};
+              nC0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 4, oC01, nb0, H0, ok1, a.pstride,
+                                                  &S, kPre ? &bv[0] : nullptr, lkC);
+              if (acc) lc = fmaf(nC0.x, S.x, fmaf(nC0.y, S.y, lc));
+              C nb1[6] = {sB[pk][1][xp1], nB1k1, sB[pk][0][syp], nB0k1, nA1n1, nA11};
+              nC1 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 5, oC11, nb1, H1, ok1, a.pstride,
+                                                  &S, kPre ? &bv[1] : nullptr, lkC);
+              if (acc) lc = fmaf(nC1.x, S.x, fmaf(nC1.y, S.y, lc));
+            }
+            {
+              const int H0[3] = {hx + 1, hy1, Zk}, H1[3] = {hx, hy1 + 1, Zk};
+              if constexpr (COEF == COEF_SOFTCORE) pair_b(a.hl, 1, 1, sZq[pk][2], H0, H1, bv);
+              if constexpr (COEF == COEF_SOFTCORR) pair_bc(a.hl, 1, 1, sZq[pk][2], H0, H1, ok1, 6, bv);
+              C nb0[6] = {sA[pk][0][xp1], nA01, nA11, nA10, nB0k1, sB[pm][0][s1]};
+              nD0 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 6, sD[pk][0][s1], nb0, H0, ok1,
+                                                  a.pstride, &S, kPre ? &bv[0] : nullptr, lkD);
+              if (acc) lc = fmaf(nD0.x, S.x, fmaf(nD0.y, S.y, lc));
+              C nb1[6] = {nA11, sA[pk][1][xm1], sA[pk][0][syp], nA01, nB1k1, sB[pm][1][s1]};
+              nD1 = site_update<P, 3, COEF, LINK>(a.hl, a.f, iso, a.ry, a.rz, 7, sD[pk][1][s1], nb1, H1, ok1,
+                                                  a.pstride, &S, kPre ? &bv[1] : nullptr, lkD);
+              if (acc) lc = fmaf(nD1.x, S.x, fmaf(nD1.y, S.y, lc));
+            }
+            if (acc) {
+              e_acc[1] += lc;
+              e_acc[0] += ((n2(nB0k1) + n2(nB1k1)) + (n2(nC0) + n2(nC1))) + (n2(nD0) + n2(nD1));
+            }
+            if (core1) {
+              a.out[2][ok1] = nB0k1;
+              a.out[3][ok1] = nB1k1;
+              a.out[4][ok1] = nC0;
+              a.out[5][ok1] = nC1;
+              a.out[6][ok1] = nD0;
+              a.out[7][ok1] = nD1;
+            }
+          }
+        }
+        if (k + 1 < z1) {
+          if (core0) {
+            if (want_e) e_acc[0] += n2(nA0n0) + n2(nA1n0);
+            a.out[0][on0] = nA0n0;
+            a.out[1][on0] = nA1n0;
+          }
+          if (core1) {
+            if (want_e) e_acc[0] += n2(nA0n1) + n2(nA1n1);
+            a.out[0][on1] = nA0n1;
+            a.out[1][on1] = nA1n1;
+          }
+        }
+      }
+      c0 = n0;
+      c1 = n1;
+    }
+    __syncthreads();  // the next item rewrites the shared tiles
+  }
+}
+#else
 // One work item (one tile over one chunk of z levels) of one simulation.
 // `a` may live in the constant bank (kernel parameter) or in shared memory.
 template <class P, int COEF, int LINK>
@@ -379,6 +813,8 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
     __syncthreads();  // the next item rewrites the shared tiles
   }
 }
+
+#endif
 
 // FP64 block reduction of the two conserved-functional accumulators into
 // out[blockIdx.x][2] (all threads of the block call it)
