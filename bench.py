@@ -27,6 +27,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import math
 import os
 import statistics
@@ -210,10 +211,16 @@ def whole_job_glups(lups_per_rank, world, seconds):
 
 
 def kernel_source_hash(kernel):
+    """The first 12 hex digits of the SHA-1 of the kernel's source files with
+    comments and white space removed: an edited comment keeps a capture's
+    counters valid, any change of the code does not."""
     h = hashlib.sha1()
     for name in KERNEL_SOURCES[kernel]:
-        with open(os.path.join(ROOT, "paper_1309_3452_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1309_3452_gb300", "csrc", name)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:12]
 
 

@@ -2,12 +2,13 @@
 // scheme2Deq ff.), out of place: every value is read once from HBM and
 // written once, neighbours come from registers, shuffles and shared memory.
 //
-// (3+1)D: a block of 512 threads covers a 34 x 15 tile of cells in (x, y)
-// (thread t sits at lx = t % 34, ly = t / 34; the last two threads are spare)
-// and marches along z.  Columns 0, 33 and rows 0, 14 are a one-cell halo:
-// they load and compute like every other thread, so the new upper values the
-// 32 x 13 interior needs from outside the tile exist in shared memory, but
-// they store nothing.  Per z level k the block
+// (3+1)D: a block of 480 threads covers a 34 x 28 tile of cells in (x, y)
+// and marches along z; every thread updates two cells stacked in y (rows ly,
+// ly + 1), so the y neighbour inside the pair comes from registers.  Columns
+// 0, 33 and rows 0, 27 are a one-cell halo: they load and compute the upper
+// half-step like every other cell, so the new upper values the 32 x 26
+// interior needs from outside the tile exist in shared memory, but they store
+// nothing.  Per z level k the block
 //   1. holds the old A(k+1), C(k+1), D(k+1) and B(k) (B, C sit at z+1/2) in
 //      registers, loaded while level k-1 was computed, publishes C(k+1) and
 //      D(k+1) in shared memory and starts the loads of level k+1,
@@ -17,7 +18,8 @@
 //   4. publishes them,
 //   5. computes the new C(k) and D(k)        (lower half-step, t -> t+dt),
 // A run of levels starts one level early to rebuild that state (the upper
-// half-step of that level only).
+// half-step of that level only).  (Build option DIRAC_YPAIR=0: one cell per
+// thread, 34 x 15 tiles of 512 threads, two blocks per SM.)
 //
 // (2+1)D: each warp owns a strip of 32 cells in x (30 interior) and marches
 // along y with the same pipeline (u0 ~ A, u1 ~ B, v1 ~ C, v0 ~ D with y as the
