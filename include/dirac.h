@@ -99,7 +99,9 @@ typedef enum {
 #define DIRAC_FLAG_ALLOW_UNSTABLE 0x1u   /* accept r beyond the stability bound */
 #define DIRAC_FLAG_REFERENCE_KERNELS 0x2u /* FP32: use the plain one-kernel-per-half-step
                                              path instead of the fused time-step kernel
-                                             (same per-value arithmetic, same results) */
+                                             (same per-value arithmetic, same results);
+                                             (3+1)D grids of 2^31 cells or more always
+                                             take this path */
 
 /*
  * External fields (Sect. 2: V in Eq. 3+3D; Sect. 4: vector potential).

@@ -576,7 +576,10 @@ static dirac_status create_sim(dirac_sim** out, int dims, const int N[3], const 
     if ((e = cudaMalloc(&s->staging, (size_t)s->pstride * sizeof(double2))) != cudaSuccess)
       return cleanup_fail(cuda_fail(s, e, "cudaMalloc(staging)"));
   }
-  s->fused = precision == DIRAC_FP32 && !(flags & DIRAC_FLAG_REFERENCE_KERNELS);
+  // the fused (3+1)D kernel addresses values inside a plane with 32-bit
+  // offsets: larger grids take the split kernels
+  s->fused = precision == DIRAC_FP32 && !(flags & DIRAC_FLAG_REFERENCE_KERNELS) &&
+             (dims == 2 || s->pstride < (1LL << 31));
   if (s->fused) {
     if ((e = cudaMalloc(&s->state_alt, sbytes)) != cudaSuccess)
       return cleanup_fail(cuda_fail(s, e, "cudaMalloc(state_alt)"));

@@ -211,7 +211,11 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
   const int tiles_x = (Nx + CX - 1) / CX;
   const long long tiles = (long long)tiles_x * ((Ny + CY - 1) / CY);
   const bool iso = a.iso != 0;
-  const long long nxy = (long long)Nx * Ny;
+  // value offsets inside a plane: 32-bit (the host runs the fused kernels
+  // only on grids of fewer than 2^31 cells), so an address is one wide
+  // multiply-add
+  using Off = unsigned;
+  const Off nxy = (Off)Nx * (Off)Ny;
   const bool want_e = a.e_partials != nullptr;
   {
     const long long chunk = item / tiles, tile = item - chunk * tiles;
@@ -223,7 +227,7 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
     const bool xin = lx >= 1 && lx <= CX && gx < Nx;
     const bool core0 = xin && !th.h0 && gy0 < Ny;
     const bool core1 = xin && !th.h1 && gy1 < Ny;
-    const long long cxy0 = (long long)y0 * Nx + x, cxy1 = (long long)y1 * Nx + x;
+    const Off cxy0 = (Off)y0 * (Off)Nx + (Off)x, cxy1 = (Off)y1 * (Off)Nx + (Off)x;
     const int hx = 2 * x, hy0 = 2 * y0, hy1 = 2 * y1;
     // COEF_SOFTCORE: the x-y part of R = |x - c|^2 + a^2 of each cell of the
     // pair, as (hi, lo) pairs of two values: lanes (A0/C0, A1/C1) at (hx, hy),
@@ -316,8 +320,8 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
     auto load = [&](int k, LevelLoad<C>& l0, LevelLoad<C>& l1) {
       const int zk = k < 0 ? k + Nz : k;
       const int zn = k + 1 >= Nz ? k + 1 - Nz : k + 1;
-      const long long ok0 = zk * nxy + cxy0, on0 = zn * nxy + cxy0;
-      const long long ok1 = zk * nxy + cxy1, on1 = zn * nxy + cxy1;
+      const Off ok0 = (Off)zk * nxy + cxy0, on0 = (Off)zn * nxy + cxy0;
+      const Off ok1 = (Off)zk * nxy + cxy1, on1 = (Off)zn * nxy + cxy1;
       l0.A0 = ld(a.in[0] + on0);
       l1.A0 = ld(a.in[0] + on1);
       l0.A1 = ld(a.in[1] + on0);
@@ -338,8 +342,8 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
 
     {  // old C, D of level z0-1 (the z- neighbours of the first level)
       const int p = (z0 - 1) & 1;
-      const long long zo = (long long)wrapi(z0 - 1, Nz) * nxy;
-      const long long o0 = zo + cxy0, o1 = zo + cxy1;
+      const Off zo = (Off)wrapi(z0 - 1, Nz) * nxy;
+      const Off o0 = zo + cxy0, o1 = zo + cxy1;
       sC[p][0][s0] = ld(a.in[4] + o0);
       sC[p][1][s0] = ld(a.in[5] + o0);
       sD[p][0][s0] = ld(a.in[6] + o0);
@@ -357,8 +361,8 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
     for (int k = z0 - 1; k < z1; ++k) {
       const int zk = k < 0 ? k + Nz : k;
       const int zn = k + 1 >= Nz ? k + 1 - Nz : k + 1;
-      const long long ok0 = zk * nxy + cxy0, on0 = zn * nxy + cxy0;
-      const long long ok1 = zk * nxy + cxy1, on1 = zn * nxy + cxy1;
+      const Off ok0 = (Off)zk * nxy + cxy0, on0 = (Off)zn * nxy + cxy0;
+      const Off ok1 = (Off)zk * nxy + cxy1, on1 = (Off)zn * nxy + cxy1;
       const int pk = k & 1, pn = (k + 1) & 1, pm = (k - 1) & 1;
       const int Zk = 2 * gz(k), Zn = 2 * gz(k + 1);  // half-lattice z of levels k, k+1 (global)
       sC[pn][0][s0] = c0.C0;  // old C(k+1), D(k+1): z+ / x,y neighbours now,
