@@ -54,6 +54,7 @@ namespace {
 #ifndef DIRAC_PAIRS
 #define DIRAC_PAIRS 14
 #endif
+
 #if DIRAC_YPAIR
 constexpr int kPairs = DIRAC_PAIRS;     // row pairs per tile
 constexpr int TW = 34, TH = 2 * kPairs;  // (3+1)D tile in cells
@@ -294,7 +295,7 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
         const float2 Rh = make_float2(r.x, r.y), Rl = make_float2(r.z, r.w);
         const float2 t0 = softcore_t0(h, H0), t1 = softcore_t0(h, H1);
         const SoftB2 bb = softcore_b2(padd(Rh, f2(z.x)), padd(Rl, f2(z.y)), make_float2(t0.x, t1.x),
-                                      make_float2(t0.y, t1.y), h.sc_K_hi, h.sc_K_lo);
+                                      make_float2(t0.y, t1.y), h.sc_K_hi, h.sc_K_lo, h.sc_small != 0);
         b[0] = lane_b(bb, 0);
         b[1] = lane_b(bb, 1);
       }
@@ -451,7 +452,8 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
           const C nA01 = sA[pk][0][s1], nA11 = sA[pk][1][s1];  // and of cell 1
           const PL* lkC = lk_z ? &sLk[pk][2] : nullptr;
           const PL* lkD = lk_z ? &sLk[pk][3] : nullptr;
-          if (!th.h0) {  // cell 0 (warp-uniform)
+          if (!th.h0) {  // cell 0 (warp-uniform; one block of code per cell: computing
+                         // the halo cells too, to interleave the two cells, was slower)
             C nC0, nC1, nD0, nD1, S;
             const bool acc = want_e && core0;  // this cell's new values count towards E
             float lc = 0.0f;
@@ -654,7 +656,7 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
         const float2 Rh = make_float2(r.x, r.y), Rl = make_float2(r.z, r.w);
         const float2 t0 = softcore_t0(h, H0), t1 = softcore_t0(h, H1);
         const SoftB2 bb = softcore_b2(padd(Rh, f2(z.x)), padd(Rl, f2(z.y)), make_float2(t0.x, t1.x),
-                                      make_float2(t0.y, t1.y), h.sc_K_hi, h.sc_K_lo);
+                                      make_float2(t0.y, t1.y), h.sc_K_hi, h.sc_K_lo, h.sc_small != 0);
         b[0] = lane_b(bb, 0);
         b[1] = lane_b(bb, 1);
       }

@@ -9,7 +9,7 @@ rounded FP32 coefficient biases every step the same way, so its error grows
 linearly with the number of steps; 1000 steps is where such a bias would
 show (the compensated hi + lo coefficients keep it out).
 
-Grids: (3+1)D 40 x 36 x 34 (2 x 3 tiles of 32 x 13 interior cells, ragged in
+Grids: (3+1)D 40 x 36 x 34 (2 x 2 tiles of 32 x 26 interior cells, ragged in
 x and y, 34 z levels in several work items) and (2+1)D 300 x 260 (ten
 30-lane strips with a ragged last one).  Inputs: Gaussian packets (the
 workloads' shape) with seeded momenta, positive-energy spinors.
@@ -54,6 +54,7 @@ def fields3(name, prob):
         "softcore": W.Fields(sc_Z=1.0, sc_a=1.0, sc_center=c),
         "softcore_offgrid_step": W.Fields(sc_Z=0.8, sc_a=1.3, sc_center=(c[0] - 0.37, c[1] + 0.61, 9.13),
                                           V0=-0.1, step_axis=0, step_x0=N[0] / 2 + 0.25, step_V=0.4),
+        "softcore_deep": W.Fields(sc_Z=4.0, sc_a=0.5, sc_center=c),  # |theta| > 1 at the centre
         "softcore_table": W.Fields(sc_Z=1.0, sc_a=1.0, sc_center=c),
         "softcore_corrected": W.Fields(sc_Z=1.0, sc_a=1.0, sc_center=c),
         "Vstatic": W.Fields(V_static=W.random_potential(prob, 6, 0.4)),
@@ -89,7 +90,7 @@ def fields2(name, prob):
 
 
 # the cases whose functional E is conserved (real potentials, static vector potentials)
-CONSERVED = {"V0", "klein_z", "klein", "softcore", "softcore_offgrid_step", "softcore_table",
+CONSERVED = {"V0", "klein_z", "klein", "softcore", "softcore_deep", "softcore_offgrid_step", "softcore_table",
              "softcore_corrected", "Vstatic", "A_const", "links"}
 
 
@@ -121,7 +122,7 @@ def check_long(D, prob, name, seed, monkeypatch):
         assert abs(E1 - E0) < FP32_EDRIFT * abs(E0), (name, abs(E1 - E0) / abs(E0))
 
 
-@pytest.mark.parametrize("name", ["V0", "klein_z", "softcore", "softcore_offgrid_step", "softcore_table",
+@pytest.mark.parametrize("name", ["V0", "klein_z", "softcore", "softcore_deep", "softcore_offgrid_step", "softcore_table",
                                   "softcore_corrected", "Vstatic", "absorb", "A_const", "A_wave", "links", "laser",
                                   "laser_table", "laser_corrected"])
 def test_fp32_1000_steps_3d(D, name, monkeypatch):

@@ -66,6 +66,9 @@ def field_cases(dims, N):
         # soft core off the half lattice, with a Klein step
         "softcore_offgrid": W.Fields(sc_Z=0.8, sc_a=1.3, sc_center=(c[0] - 0.37, c[1] + 0.61, 2.13),
                                      V0=-0.1, step_axis=1, step_x0=N[1] / 2 + 0.25, step_V=0.3),
+        # a deep soft core: |theta| > 1 near the centre (the FP32 kernels then
+        # split 1 + theta^2 by TwoSum instead of the FMA form used when |theta| <= 1)
+        "softcore_deep": W.Fields(sc_Z=4.0, sc_a=0.5, sc_center=tuple(c)),
         # absorbing layers on every face plus a uniform imaginary part (Sect. 3)
         "absorb": W.Fields(V0=0.05, V0_imag=-0.02, abs_W=0.7, abs_width=3.0, abs_axes=(1 << dims) - 1),
         # the laser workload's fields: soft core plus a moving plane wave
@@ -78,8 +81,8 @@ def field_cases(dims, N):
 
 @pytest.mark.parametrize("dims,N", [(2, (37, 29)), (3, (13, 11, 9))])
 @pytest.mark.parametrize("case", ["free", "V0", "klein", "klein_y", "softcore", "A_const", "A_wave",
-                                  "A_wave_long", "Vstatic", "Vstatic_mod", "softcore_offgrid", "laser",
-                                  "absorb"])
+                                  "A_wave_long", "Vstatic", "Vstatic_mod", "softcore_offgrid", "softcore_deep",
+                                  "laser", "absorb"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_parity_fields(D, dims, N, case, precision):
     full = tuple(N) + ((1,) if dims == 2 else ())
@@ -220,15 +223,16 @@ def test_unstable_is_rejected_and_diverges_when_forced(D):
 
 
 @pytest.mark.parametrize("dims,N", [(2, (37, 29)), (2, (64, 70)), (3, (13, 11, 9)), (3, (33, 17, 20)),
-                                    (3, (2, 3, 2))])
+                                    (3, (2, 3, 2)), (3, (33, 27, 5)), (3, (40, 53, 3))])
 @pytest.mark.parametrize("case", ["free", "klein", "klein_y", "softcore", "A_const", "A_wave",
-                                  "A_wave_long", "Vstatic", "Vstatic_mod", "softcore_offgrid", "laser",
-                                  "absorb"])
+                                  "A_wave_long", "Vstatic", "Vstatic_mod", "softcore_offgrid", "softcore_deep",
+                                  "laser", "absorb"])
 def test_fused_kernel_bit_identical_to_reference_kernels(D, dims, N, case):
     """The fused time-step kernel (out of place, tiles with recomputed halos,
     z/y marching) uses the same per-value arithmetic as the one-kernel-per-
     half-step path, so the FP32 states agree bit for bit, for every field
-    path, ragged tiles and grids smaller than one tile."""
+    path, ragged tiles and grids smaller than one tile (the (3+1)D tiles hold
+    32 x 26 interior cells: 27 and 53 rows leave a last tile of one row)."""
     full = tuple(N) + ((1,) if dims == 2 else ())
     prob = W.Problem(dims, full, (1.0, 1.0, 1.0), 0.9 * W.stability_limit(dims), 0.45)
     if case == "Vstatic_mod":
