@@ -427,16 +427,15 @@ __device__ __forceinline__ float2 rcp2(float2 v) {
 // dt (beta m + V0 [+ V_step])/2).  1/sqrt(R) is the hardware estimate refined
 // by one Newton step y0 + y0 (1 - R y0^2)/2 whose residual is formed with y0^2
 // split exactly (TwoProduct) and 1 - Rh y0^2 in one FMA rounding; theta =
-// th0 + K y by TwoSum; 1 + theta^2 split into hi + lo by an FMA when `small`
-// (|theta| <= 1 at every site, so the hi part lies in [1, 2]), else by
-// TwoSum; b = (1 - i theta)/(1 + theta^2) with the reciprocal refined like
-// the square root.  Result: b = (re_hi + re_lo) + i (im_hi + im_lo), relative
+// th0 + K y by TwoSum; 1 + theta^2 split into hi + lo by an FMA; b =
+// (1 - i theta)/(1 + theta^2) with the reciprocal refined like the square
+// root.  Result: b = (re_hi + re_lo) + i (im_hi + im_lo), relative
 // error ~1e-13 for |theta| < 1, so |2b - 1| = 1 to that accuracy.
 struct SoftB2 {
   float2 re_hi, re_lo, im_hi, im_lo;
 };
 __device__ __forceinline__ SoftB2 softcore_b2(float2 Rh, float2 Rl, float2 t0h, float2 t0l, float Kh,
-                                              float Kl, bool small) {
+                                              float Kl) {
   // y = 1/sqrt(R) as y0 + yl
   const float2 y0 = rsqrt2(Rh);
   const float2 ph = pmul(y0, y0);
@@ -456,22 +455,12 @@ __device__ __forceinline__ SoftB2 softcore_b2(float2 Rh, float2 Rl, float2 t0h, 
   float2 ah, ae;
   two_sum2(t0h, th, ah, ae);
   const float2 al = padd(ae, padd(t0l, tl));
-  // D = 1 + theta^2 as dh + dl
-  float2 dh, dl;
-  if (small) {
-    // |theta| <= 1: dh = fl(1 + ah^2) lies in [1, 2], so 1 - dh is exact
-    // (Sterbenz) and ah^2 + (1 - dh) is the rounding error of dh
-    dh = pfma(ah, ah, f2(1.0f));
-    dl = pfma(ah, ah, psub(f2(1.0f), dh));
-    dl = pfma(padd(ah, ah), al, dl);
-  } else {
-    const float2 sh = pmul(ah, ah);
-    float2 sl = pfma(ah, ah, pneg(sh));
-    sl = pfma(padd(ah, ah), al, sl);
-    float2 de;
-    two_sum2(f2(1.0f), sh, dh, de);
-    dl = padd(de, sl);
-  }
+  // D = 1 + theta^2 as dh + dl: dh = fl(1 + ah^2) >= 1 is a multiple of its
+  // own ulp, and so is 1, so 1 - dh is exact; ah^2 + (1 - dh), rounded once,
+  // is the rounding error of dh
+  const float2 dh = pfma(ah, ah, f2(1.0f));
+  float2 dl = pfma(ah, ah, psub(f2(1.0f), dh));
+  dl = pfma(padd(ah, ah), al, dl);
   // 1/D as r0 + rl
   const float2 r0 = rcp2(dh);
   float2 g = pfma(pneg(dh), r0, f2(1.0f));
@@ -585,7 +574,6 @@ struct HalfFields {
   // that sums of hi parts are exact in FP32
   float2 sc_t0[2];
   int sc_step;              // a Klein step is present (else sc_t0[0] everywhere)
-  int sc_small;             // |theta| <= 1 at every site (softcore_b2 may form 1 + theta^2 by FMA)
   float sc_K_hi, sc_K_lo;
   const float2* sc_sq[3];
   // COEF_SOFTCORR: the correction records (softcore_corr_index), 32-bit words
@@ -706,7 +694,7 @@ __device__ __forceinline__ float2 apply_softcore_f32(const HalfFields<F32>& h, f
     float Rh, Rl;
     softcore_R<DIMS>(h, H, Rh, Rl);
     const float2 t0 = softcore_t0(h, H);
-    b = lane_b(softcore_b2(f2(Rh), f2(Rl), f2(t0.x), f2(t0.y), h.sc_K_hi, h.sc_K_lo, h.sc_small != 0), 0);
+    b = lane_b(softcore_b2(f2(Rh), f2(Rl), f2(t0.x), f2(t0.y), h.sc_K_hi, h.sc_K_lo), 0);
   }
   return apply_b(b, h.rx_hi, h.rx_lo, F, S);
 }

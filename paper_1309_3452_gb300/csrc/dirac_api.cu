@@ -304,12 +304,6 @@ static HalfFields<P> half_fields(const dirac_sim* s, bool upper, double t) {
     split(t_out, h.sc_t0[1].x, h.sc_t0[1].y);
     h.sc_step = s->f.step_axis >= 0;
     split(-s->dt * s->f.sc_Z / 2.0, h.sc_K_hi, h.sc_K_lo);
-    // |theta| = dt |beta m + V|/2 with |V| <= |V0| + |V_step| + |Z|/|a| (R >= a^2)
-    {
-      const double vmax = std::fabs(s->f.V0) + (s->f.step_axis >= 0 ? std::fabs(s->f.step_V) : 0.0) +
-                          (s->f.sc_a != 0.0 ? std::fabs(s->f.sc_Z / s->f.sc_a) : INFINITY);
-      h.sc_small = s->dt * (std::fabs(s->m) + vmax) / 2.0 <= 0.99;
-    }
     long long off = 0;
     for (int a = 0; a < 3; ++a) {
       h.sc_sq[a] = s->sc_sq ? s->sc_sq + off : nullptr;

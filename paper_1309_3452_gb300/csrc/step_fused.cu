@@ -295,7 +295,7 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
         const float2 Rh = make_float2(r.x, r.y), Rl = make_float2(r.z, r.w);
         const float2 t0 = softcore_t0(h, H0), t1 = softcore_t0(h, H1);
         const SoftB2 bb = softcore_b2(padd(Rh, f2(z.x)), padd(Rl, f2(z.y)), make_float2(t0.x, t1.x),
-                                      make_float2(t0.y, t1.y), h.sc_K_hi, h.sc_K_lo, h.sc_small != 0);
+                                      make_float2(t0.y, t1.y), h.sc_K_hi, h.sc_K_lo);
         b[0] = lane_b(bb, 0);
         b[1] = lane_b(bb, 1);
       }
@@ -656,7 +656,7 @@ __device__ __forceinline__ void fused3d_item(const FusedArgs<P>& a, long long it
         const float2 Rh = make_float2(r.x, r.y), Rl = make_float2(r.z, r.w);
         const float2 t0 = softcore_t0(h, H0), t1 = softcore_t0(h, H1);
         const SoftB2 bb = softcore_b2(padd(Rh, f2(z.x)), padd(Rl, f2(z.y)), make_float2(t0.x, t1.x),
-                                      make_float2(t0.y, t1.y), h.sc_K_hi, h.sc_K_lo, h.sc_small != 0);
+                                      make_float2(t0.y, t1.y), h.sc_K_hi, h.sc_K_lo);
         b[0] = lane_b(bb, 0);
         b[1] = lane_b(bb, 1);
       }

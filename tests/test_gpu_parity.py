@@ -66,8 +66,7 @@ def field_cases(dims, N):
         # soft core off the half lattice, with a Klein step
         "softcore_offgrid": W.Fields(sc_Z=0.8, sc_a=1.3, sc_center=(c[0] - 0.37, c[1] + 0.61, 2.13),
                                      V0=-0.1, step_axis=1, step_x0=N[1] / 2 + 0.25, step_V=0.3),
-        # a deep soft core: |theta| > 1 near the centre (the FP32 kernels then
-        # split 1 + theta^2 by TwoSum instead of the FMA form used when |theta| <= 1)
+        # a deep soft core: |theta| > 1 near the centre
         "softcore_deep": W.Fields(sc_Z=4.0, sc_a=0.5, sc_center=tuple(c)),
         # absorbing layers on every face plus a uniform imaginary part (Sect. 3)
         "absorb": W.Fields(V0=0.05, V0_imag=-0.02, abs_W=0.7, abs_width=3.0, abs_axes=(1 << dims) - 1),
