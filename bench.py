@@ -544,7 +544,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         e2e_ms = []
-        for i in range(max(1, min(2, args.steps))):
+        for i in range(max(1, min(3, args.steps))):
             flush.fill_(float(i))
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
