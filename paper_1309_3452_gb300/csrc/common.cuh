@@ -505,10 +505,12 @@ __device__ __forceinline__ float2 apply_b(float4 b, float rxh, float rxl, float2
   // w = 2F - r_x S'  (small product first)
   const float2 w = pfma(f2(-rxh), S, pfma(f2(-rxl), S, padd(F, F)));
   // b w = re(b) (wx, wy) + im(b) (-wy, wx), small (lo) products first
-  const float2 ws = make_float2(w.y, w.x);
+  // (the rotated w is formed once; each product has the value of im(b) times
+  // the rotated lane, so the result does not depend on where the sign sits)
+  const float2 wr = make_float2(-w.y, w.x);
   float2 t = pmul(f2(b.y), w);
-  t = pfma(make_float2(-b.w, b.w), ws, t);
-  t = pfma(make_float2(-b.z, b.z), ws, t);
+  t = pfma(f2(b.w), wr, t);
+  t = pfma(f2(b.z), wr, t);
   t = pfma(f2(b.x), w, t);
   return psub(t, F);
 }
