@@ -314,7 +314,7 @@ def run_serve(args, rank, world):
     torch.cuda.set_device(local)
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.6 * free)
-    srv = serve.Server(budget, quantum=args.quantum)
+    srv = serve.Server(budget, quantum=args.quantum, policy=args.serve_policy)
     stream = serve.make_requests(args.requests, seed=args.seed, rate=1.0)
     mean_lups = sum(r.lups for r in stream) / len(stream)
     sweep = []
@@ -381,7 +381,7 @@ def run_serve(args, rank, world):
                                   "p = 1/2, 100..5000 steps, FP32; admitted by free HBM, continuously "
                                   "batched in quanta",
                       "requests": out["requests"], "seed": args.seed, "rate_per_s": rate, "rate_rule": rule,
-                      "rate_sweep": sweep, "burst_glups": glups_sat, "quantum_steps": args.quantum,
+                      "rate_sweep": sweep, "burst_glups": glups_sat, "quantum_steps": args.quantum, "policy": args.serve_policy,
                       "hbm_budget_bytes": budget, "parallelism": f"replicas x{world}"},
            "serving": {"p50_latency_s": out["p50_s"], "p99_latency_s": out["p99_s"],
                        "mean_latency_s": out["mean_s"], "makespan_s": out["makespan_s"],
@@ -418,6 +418,8 @@ def main():
                          "the JSON line then names the count)")
     ap.add_argument("--requests", type=int, default=40, help="serve: requests in the stream")
     ap.add_argument("--quantum", type=int, default=100, help="serve: steps per batching quantum")
+    ap.add_argument("--serve-policy", default="lockstep", choices=["lockstep", "work"],
+                    help="serve: every resident the same steps per round, or the same work")
     ap.add_argument("--seed", type=int, default=0, help="serve: request stream seed")
     ap.add_argument("--sweep-requests", type=int, default=40, help="serve: requests per rate-sweep point")
     ap.add_argument("--progress", action="store_true", help="serve: log every retired request to stderr")

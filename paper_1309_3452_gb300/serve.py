@@ -5,8 +5,11 @@ number of time steps) arrive over time.  The server admits a request as soon
 as it has arrived and its device state fits the HBM budget next to the
 simulations already resident, keeps every admitted state resident until its
 steps are done, and advances all resident simulations together with
-dirac_batch_step in quanta of at most `quantum` steps (shortened so the
-request that finishes first finishes exactly).  Between quanta finished
+dirac_batch_step in rounds: under the "lockstep" policy every resident
+advances by at most `quantum` steps per round (shortened so the request that
+finishes first finishes exactly); under "work" a resident with 2^k times fewer
+cells than the largest advances 2^k times as many steps (capped, never past
+its last step), so the residents share the device by work.  Between quanta finished
 requests leave (their conserved functional is read and checked against the
 value reduced when their state was set) and waiting ones join.  Latency =
 finish - arrival on the wall clock.
@@ -108,11 +111,16 @@ class Result:
 
 class Server:
     def __init__(self, hbm_budget: int, quantum: int = 100, stream=None, device="cuda",
-                 keep_states: bool = False, drift_tol: float = 1e-6):
+                 keep_states: bool = False, drift_tol: float = 1e-6, policy: str = "lockstep",
+                 max_boost: int = 64):
         import torch
+        if policy not in ("lockstep", "work"):
+            raise ValueError(f"unknown policy {policy}")
         self.torch = torch
         self.budget = int(hbm_budget)
         self.quantum = int(quantum)
+        self.policy = policy
+        self.max_boost = int(max_boost)
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.device = device
         self.keep_states = keep_states
@@ -142,6 +150,26 @@ class Server:
         _, r = sim.check(self.drift_tol)
         state = sim.get_spinor() if self.keep_states else None
         return r["E_ref"], r["E"], state
+
+    def _round(self, resident):
+        """[(steps, members)]: the batch_step calls of one round.  "lockstep":
+        every resident advances the same number of steps, at most `quantum`
+        and no more than the nearest finish needs, so a request's latency
+        follows its number of steps.  "work": a resident with 2^k times fewer
+        cells than the largest one advances 2^k times further (k at most
+        log2(max_boost), never past its last step), so the residents receive
+        about equal work per round and a request's latency follows its own
+        work (cells x steps)."""
+        if self.policy == "lockstep":
+            return [(min(self.quantum, min(r[2] for r in resident)), list(resident))]
+        cmax = max(r[0].prob.cells for r in resident)
+        groups = collections.OrderedDict()
+        for r in resident:
+            boost = 1
+            while boost < self.max_boost and r[0].prob.cells * boost * 2 <= cmax:
+                boost *= 2
+            groups.setdefault(min(self.quantum * boost, r[2]), []).append(r)
+        return list(groups.items())
 
     def run(self, requests: List[Request], log=None) -> dict:
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
@@ -197,13 +225,13 @@ class Server:
                 if pending:
                     time.sleep(max(0.0, min(0.05, pending[0].arrival - now())))
                 continue
-            q = min(self.quantum, min(r[2] for r in resident))
-            sims = [r[1] for r in resident]
-            before = sum(s.launches for s in sims)
-            D.batch_step(sims, q)
-            launches += sum(s.launches for s in sims) - before
-            for r in resident:
-                r[2] -= q
+            for n, members in self._round(resident):
+                sims = [r[1] for r in members]
+                before = sum(s.launches for s in sims)
+                D.batch_step(sims, n)
+                launches += sum(s.launches for s in sims) - before
+                for r in members:
+                    r[2] -= n
             leaving = [r for r in resident if r[2] == 0 or gone(r[0], now())]
             if leaving:
                 for r in leaving:

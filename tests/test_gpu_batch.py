@@ -164,16 +164,17 @@ def test_batch_graph_replay_and_membership_changes(D, monkeypatch):
             assert np.array_equal(s.get_spinor(), with_graphs[i])
 
 
-def test_serving_results_equal_stepping_alone(D, monkeypatch):
-    """Each request served in the mix (admitted and retired between quanta,
-    batched with whatever else is resident, loops replayed as graphs) ends
-    in the same state as when stepped alone: its functional, from the same
-    reduction, is identical to the last bit."""
+@pytest.mark.parametrize("policy", ["lockstep", "work"])
+def test_serving_results_equal_stepping_alone(D, monkeypatch, policy):
+    """Each request served in the mix (admitted and retired between rounds,
+    batched with whatever else is resident, loops replayed as graphs, under
+    either scheduling policy) ends in the same state as when stepped alone:
+    its functional, from the same reduction, is identical to the last bit."""
     from paper_1309_3452_gb300 import serve
     monkeypatch.setenv("DIRAC_NO_FUSED_NORM", "1")  # both sides reduce the stored state
     reqs = serve.make_requests(24, seed=5, rate=40.0, max_side_3d=40, max_side_2d=192,
                                min_steps=30, max_steps=700)
-    srv = serve.Server(hbm_budget=3 << 30, quantum=50, keep_states=True)
+    srv = serve.Server(hbm_budget=3 << 30, quantum=50, keep_states=True, policy=policy)
     out = srv.run(reqs)
     assert out["served"] == len(reqs)
     byid = {r.rid: r for r in reqs}

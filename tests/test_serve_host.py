@@ -205,3 +205,53 @@ def test_cancelled_and_timed_out_requests_free_their_slots(monkeypatch):
     assert all(st[r.rid].status == "ok" for r in reqs[3:])
     assert not FakeSim.alive
     assert out["served"] == len(reqs) - 3 and out["status_counts"]["cancelled"] == 2
+
+
+def test_work_policy_shares_by_work(monkeypatch):
+    """Under the "work" policy a resident with 2^k times fewer cells than the
+    largest advances 2^k times as many steps per round (at most max_boost
+    times the quantum, never past its last step); every request still gets
+    exactly its steps, and a small request next to a large one finishes in
+    fewer rounds than under "lockstep"."""
+    import numpy as np
+    from paper_1309_3452_gb300 import workloads as W
+
+    def two_requests():
+        big = W.Problem(3, (64, 64, 64), (1.0, 1.0, 1.0), 0.5, 0.5)
+        small = W.Problem(3, (16, 16, 16), (1.0, 1.0, 1.0), 0.5, 0.5)  # 64 x fewer cells
+        return [serve.Request(0, 0.0, big, 4.0, (0.0, 0.0, 0.0), (32.0, 32.0, 32.0), 1000),
+                serve.Request(1, 0.0, small, 2.0, (0.0, 0.0, 0.0), (8.0, 8.0, 8.0), 1000)]
+
+    rounds = {}
+    for policy in ("lockstep", "work"):
+        FakeSim.alive = []
+        reqs = two_requests()
+        sims, calls = {}, []
+
+        def admit(self, req):
+            sims[req.rid] = FakeSim(req, 1)
+            return sims[req.rid]
+
+        def batch_step(group, n):
+            calls.append((sorted(s.req.rid for s in group), n))
+            for s in group:
+                s.steps += n
+                s.launches += 1
+                assert s.steps <= s.req.steps
+
+        monkeypatch.setattr(serve.Server, "_admit", admit)
+        monkeypatch.setattr(serve.D, "batch_step", batch_step)
+        srv = serve.Server(hbm_budget=1 << 40, quantum=50, stream=FakeStream(), policy=policy, max_boost=8)
+        out = srv.run(reqs)
+        assert all(sims[r.rid].steps == r.steps for r in reqs)
+        assert out["served"] == 2
+        # the round in which the small request received its last steps
+        rounds[policy] = next(i for i, (ids, _) in enumerate(calls)
+                              if 1 in ids and sum(n for j, n in calls[:i + 1] if 1 in j) == 1000)
+        if policy == "work":
+            first = dict((tuple(ids), n) for ids, n in calls[:2])
+            assert first[(0,)] == 50 and first[(1,)] == 400  # boost capped at 8 (64 x fewer cells)
+    assert rounds["work"] < rounds["lockstep"]
+    with pytest.raises(ValueError):
+        serve.Server(hbm_budget=1, stream=FakeStream(), policy="fifo")
+    del np
