@@ -418,7 +418,7 @@ def main():
                          "the JSON line then names the count)")
     ap.add_argument("--requests", type=int, default=40, help="serve: requests in the stream")
     ap.add_argument("--quantum", type=int, default=100, help="serve: steps per batching quantum")
-    ap.add_argument("--serve-policy", default="lockstep", choices=["lockstep", "work"],
+    ap.add_argument("--serve-policy", default="work", choices=["lockstep", "work"],
                     help="serve: every resident the same steps per round, or the same work")
     ap.add_argument("--seed", type=int, default=0, help="serve: request stream seed")
     ap.add_argument("--sweep-requests", type=int, default=40, help="serve: requests per rate-sweep point")

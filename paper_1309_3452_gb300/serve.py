@@ -111,7 +111,7 @@ class Result:
 
 class Server:
     def __init__(self, hbm_budget: int, quantum: int = 100, stream=None, device="cuda",
-                 keep_states: bool = False, drift_tol: float = 1e-6, policy: str = "lockstep",
+                 keep_states: bool = False, drift_tol: float = 1e-6, policy: str = "work",
                  max_boost: int = 64):
         import torch
         if policy not in ("lockstep", "work"):
