@@ -68,7 +68,7 @@ def test_serving_schedule(monkeypatch):
 
     monkeypatch.setattr(serve.Server, "_admit", admit)
     monkeypatch.setattr(serve.D, "batch_step", batch_step)
-    srv = serve.Server(hbm_budget=budget, quantum=64, stream=FakeStream())
+    srv = serve.Server(hbm_budget=budget, quantum=64, stream=FakeStream(), policy="lockstep")
     out = srv.run(reqs)
 
     assert out["requests"] == len(reqs)
