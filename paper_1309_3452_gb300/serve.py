@@ -9,7 +9,7 @@ dirac_batch_step in rounds: under the "lockstep" policy every resident
 advances by at most `quantum` steps per round (shortened so the request that
 finishes first finishes exactly); under "work" a resident with 2^k times fewer
 cells than the largest advances 2^k times as many steps (capped, never past
-its last step), so the residents share the device by work.  Between quanta finished
+its last step), so the residents share the device by work.  Between rounds finished
 requests leave (their conserved functional is read and checked against the
 value reduced when their state was set) and waiting ones join.  Latency =
 finish - arrival on the wall clock.
@@ -21,7 +21,7 @@ can never fit the budget is rejected; one whose creation fails with
 DIRAC_ERR_OOM (the device has less free memory than the budget assumed) waits
 until a resident request has retired and is then tried again (rejected if
 nothing else is resident); a request may be cancelled by its client or time
-out, before or after admission, and then leaves between quanta, freeing its
+out, before or after admission, and then leaves between rounds, freeing its
 memory.
 
 The stepping, the norms and the state set-up all run in libdirac; this

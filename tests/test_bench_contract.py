@@ -49,3 +49,28 @@ def test_own_arm_needs_a_device():
     r = run("--workload", "2d64", "--steps", "1", "--warmup", "3")
     assert r.returncode != 0
     assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_traffic_counters_follow_the_kernel_code(tmp_path, monkeypatch):
+    """profiles/ncu_traffic.json is valid only for the kernel code it was
+    captured on: the hash ignores comments and white space but changes with
+    any code token."""
+    sys.path.insert(0, ROOT)
+    import bench
+    src = tmp_path / "paper_1309_3452_gb300" / "csrc"
+    src.mkdir(parents=True)
+    code = "int f(int a) {\n  return a + 1;  // one more\n}\n/* block */\n"
+    for name in bench.KERNEL_SOURCES["step_fp32"]:
+        (src / name).write_text(code)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_source_hash("step_fp32")
+    for name in bench.KERNEL_SOURCES["step_fp32"]:
+        (src / name).write_text("int f(int a)   {\n\n  return a + 1;  // more than one\n}\n/* another */\n")
+    assert bench.kernel_source_hash("step_fp32") == h0
+    (src / bench.KERNEL_SOURCES["step_fp32"][0]).write_text(code.replace("+ 1", "+ 2"))
+    assert bench.kernel_source_hash("step_fp32") != h0
+    # and the committed counters carry the hash of the committed sources
+    monkeypatch.setattr(bench, "ROOT", ROOT)
+    d = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+    h = bench.kernel_source_hash("step_fp32")
+    assert all(e["source_hash"] == h for k, e in d.items() if k.startswith("step_fp32@"))
